@@ -1,0 +1,345 @@
+"""Seeded synthetic PUSCH slots and seeded NRX weights.
+
+This module is the transmitter and channel side of the link: random bits,
+Gray QAM (3GPP TS 38.211 Sec. 5.1 mapping formulas), DMRS insertion with the
+type-1 comb and frequency-domain OCC, a tapped-delay-line channel with an
+exponential power-delay profile and Doppler, and AWGN, producing the received
+resource grid of the system model (Eq. 1).  It also draws the seeded network
+weights and serialises them into the flat weight blob that ``nrx_create``
+consumes (format documented in ``include/nrx.h``).
+
+It holds none of the receiver's arithmetic (no LS estimation, interpolation,
+network layers, equalisation or demapping): both the CUDA path and the CPU
+oracle consume what it produces, and nothing here depends on either of them.
+
+Randomness: every draw comes from ``numpy.random.Generator(PCG64(seed))``.
+Slot ``i`` of a workload uses seed ``1000 * workload.seed_base + i``; weights
+use seed 42.
+"""
+from __future__ import annotations
+
+import dataclasses
+import struct
+from typing import Dict, List, Sequence
+
+import numpy as np
+
+SUBCARRIER_SPACING_HZ = 30e3
+NUM_SYMBOLS = 14
+SLOT_DURATION_S = 0.5e-3
+
+# ----------------------------------------------------------------------------
+# Configuration records
+# ----------------------------------------------------------------------------
+
+
+@dataclasses.dataclass(frozen=True)
+class NetConfig:
+    """Hyper-parameters of the network: Rx antennas B, state depth C (d_S in
+    Sec. II-A), residual conv blocks R per CGNN iteration, iterations N_it,
+    and LLR head width m_max (bits of the highest supported modulation)."""
+
+    num_rx_ant: int
+    channels: int
+    res_blocks: int
+    iterations: int
+    m_max: int = 6
+
+    @property
+    def in_features(self) -> int:
+        # [Re/Im y per antenna, Re/Im LS estimate per antenna, 2 PE channels]
+        return 4 * self.num_rx_ant + 2
+
+
+@dataclasses.dataclass(frozen=True)
+class SlotConfig:
+    """One slot's transmission: geometry, DMRS positions, modulation orders
+    (bits per symbol per user) and channel/SNR draws."""
+
+    num_prb: int
+    num_users: int
+    num_rx_ant: int
+    dmrs_symbols: tuple
+    bits_per_symbol: tuple  # one entry per user, each 2, 4 or 6
+    snr_db: float
+    num_taps: int
+    delay_spread_s: float
+    doppler_hz: float
+    ula: bool
+
+    @property
+    def num_subcarriers(self) -> int:
+        return 12 * self.num_prb
+
+    @property
+    def num_data_symbols(self) -> int:
+        return NUM_SYMBOLS - len(self.dmrs_symbols)
+
+    @property
+    def noise_var(self) -> float:
+        return float(10.0 ** (-self.snr_db / 10.0))
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """A named family of slots (shape + the distributions of the random draws)
+    and the network it is run with."""
+
+    name: str
+    seed_base: int
+    batch: int
+    num_prb: int
+    num_users: int
+    num_rx_ant: int
+    dmrs_symbols: tuple
+    mcs_choices: tuple  # modulation orders drawn per user (uniformly)
+    snr_db_range: tuple  # (lo, hi); lo == hi means fixed
+    num_taps: int
+    delay_spread_range_s: tuple
+    doppler_range_hz: tuple
+    ula: bool
+    net: NetConfig
+
+
+# The three workloads.  Shapes follow the paper's evaluation setting (Sec. III-B:
+# 2 users x 4 Rx antennas, 30 kHz SCS, DMRS type A with one additional position)
+# scaled to a tiny single-user case, a 24-PRB two-user case and the full
+# 273-PRB four-user slot.
+WORKLOADS: Dict[str, Workload] = {
+    "su_2rx_4prb": Workload(
+        name="su_2rx_4prb", seed_base=1, batch=1, num_prb=4, num_users=1,
+        num_rx_ant=2, dmrs_symbols=(2,), mcs_choices=(2,), snr_db_range=(10.0, 10.0),
+        num_taps=6, delay_spread_range_s=(100e-9, 100e-9), doppler_range_hz=(0.0, 0.0),
+        ula=False, net=NetConfig(num_rx_ant=2, channels=32, res_blocks=2, iterations=1, m_max=2)),
+    "mu2_4rx_24prb": Workload(
+        name="mu2_4rx_24prb", seed_base=2, batch=16, num_prb=24, num_users=2,
+        num_rx_ant=4, dmrs_symbols=(2, 11), mcs_choices=(4,), snr_db_range=(-2.0, 20.0),
+        num_taps=12, delay_spread_range_s=(10e-9, 300e-9), doppler_range_hz=(0.0, 400.0),
+        ula=True, net=NetConfig(num_rx_ant=4, channels=64, res_blocks=2, iterations=2, m_max=4)),
+    "mu4_4rx_273prb": Workload(
+        name="mu4_4rx_273prb", seed_base=3, batch=8, num_prb=273, num_users=4,
+        num_rx_ant=4, dmrs_symbols=(2, 11), mcs_choices=(2, 4, 6), snr_db_range=(-2.0, 20.0),
+        num_taps=12, delay_spread_range_s=(10e-9, 300e-9), doppler_range_hz=(0.0, 400.0),
+        ula=True, net=NetConfig(num_rx_ant=4, channels=64, res_blocks=2, iterations=2, m_max=6)),
+}
+
+
+def draw_slot_config(w: Workload, rng: np.random.Generator) -> SlotConfig:
+    """Draw one slot's per-slot parameters from the workload's distributions."""
+    bits = tuple(int(rng.choice(w.mcs_choices)) for _ in range(w.num_users))
+    snr = float(rng.uniform(*w.snr_db_range)) if w.snr_db_range[0] != w.snr_db_range[1] \
+        else float(w.snr_db_range[0])
+    ds = float(rng.uniform(*w.delay_spread_range_s))
+    fd = float(rng.uniform(*w.doppler_range_hz))
+    return SlotConfig(num_prb=w.num_prb, num_users=w.num_users, num_rx_ant=w.num_rx_ant,
+                      dmrs_symbols=tuple(w.dmrs_symbols), bits_per_symbol=bits, snr_db=snr,
+                      num_taps=w.num_taps, delay_spread_s=ds, doppler_hz=fd, ula=w.ula)
+
+
+# ----------------------------------------------------------------------------
+# Transmitter
+# ----------------------------------------------------------------------------
+
+
+def qam_modulate(bits: np.ndarray, m: int) -> np.ndarray:
+    """Map bit vectors [..., m] to unit-energy Gray QAM symbols with the
+    TS 38.211 Sec. 5.1.3-5.1.5 formulas (b0/b1 are the I/Q sign bits)."""
+    b = 1.0 - 2.0 * bits.astype(np.float64)
+    if m == 2:
+        return (b[..., 0] + 1j * b[..., 1]) / np.sqrt(2.0)
+    if m == 4:
+        re = b[..., 0] * (2.0 - b[..., 2])
+        im = b[..., 1] * (2.0 - b[..., 3])
+        return (re + 1j * im) / np.sqrt(10.0)
+    if m == 6:
+        re = b[..., 0] * (4.0 - b[..., 2] * (2.0 - b[..., 4]))
+        im = b[..., 1] * (4.0 - b[..., 3] * (2.0 - b[..., 5]))
+        return (re + 1j * im) / np.sqrt(42.0)
+    raise ValueError(f"unsupported bits per symbol {m}")
+
+
+def dmrs_port_values(base: np.ndarray, port: int) -> np.ndarray:
+    """Values a DMRS port transmits on its comb: port p in {0,1,2,3} uses CDM
+    group p//2 and frequency OCC [+1,+1] (even p) or [+1,-1] (odd p) over each
+    pair of consecutive comb positions.  ``base`` is the base sequence r(m) of
+    one DMRS symbol, m = 0..S/2-1, placed on subcarrier 2m + p//2."""
+    m = np.arange(base.shape[-1])
+    occ = np.ones_like(m, dtype=np.float64) if port % 2 == 0 else (-1.0) ** m
+    return base * occ
+
+
+def transmit_grid(cfg: SlotConfig, dmrs: np.ndarray, bits: List[np.ndarray]) -> np.ndarray:
+    """Resource grids x_u[t, s] of all users (complex128 [U, 14, S]).  DMRS
+    symbols carry only pilots (both CDM groups reserved, no data)."""
+    S = cfg.num_subcarriers
+    x = np.zeros((cfg.num_users, NUM_SYMBOLS, S), dtype=np.complex128)
+    data_syms = [t for t in range(NUM_SYMBOLS) if t not in cfg.dmrs_symbols]
+    for u in range(cfg.num_users):
+        sym = qam_modulate(bits[u], cfg.bits_per_symbol[u]).reshape(len(data_syms), S)
+        for i, t in enumerate(data_syms):
+            x[u, t, :] = sym[i]
+        for d, t in enumerate(cfg.dmrs_symbols):
+            x[u, t, (u // 2)::2] = dmrs_port_values(dmrs[d].astype(np.complex128), u)
+    return x
+
+
+# ----------------------------------------------------------------------------
+# Channel
+# ----------------------------------------------------------------------------
+
+
+def tdl_channel(cfg: SlotConfig, rng: np.random.Generator) -> np.ndarray:
+    """Frequency response h[u, b, t, s] (complex128) of an exponential-PDP
+    tapped delay line per user.
+
+    Taps: tau_l = l * 4 * DS / (L-1), power ~ exp(-tau_l / DS), normalised to 1.
+    Time variation: a sum of M = 16 complex sinusoids per tap with equally
+    spaced, randomly rotated arrival angles (Clarke's model), unit power; a
+    static channel (zero Doppler) draws CN(0, 1) gains instead.  Antennas: a
+    half-wavelength ULA (one arrival angle in [-60, 60] degrees per tap) or
+    independent gains per antenna.
+    """
+    U, B, S, L = cfg.num_users, cfg.num_rx_ant, cfg.num_subcarriers, cfg.num_taps
+    tau = np.arange(L) * (4.0 * cfg.delay_spread_s / max(L - 1, 1))
+    pdp = np.exp(-tau / cfg.delay_spread_s)
+    pdp /= pdp.sum()
+    t_n = np.arange(NUM_SYMBOLS) * (SLOT_DURATION_S / NUM_SYMBOLS)
+    f_s = (np.arange(S) - S / 2) * SUBCARRIER_SPACING_HZ
+    n_ant_draws = 1 if cfg.ula else B
+    M = 16
+    h = np.zeros((U, B, NUM_SYMBOLS, S), dtype=np.complex128)
+    for u in range(U):
+        # gains a[l, b', t]
+        if cfg.doppler_hz == 0.0:
+            g = (rng.standard_normal((L, n_ant_draws)) + 1j * rng.standard_normal((L, n_ant_draws))) / np.sqrt(2.0)
+            a = np.repeat(g[:, :, None], NUM_SYMBOLS, axis=2)
+        else:
+            theta = rng.uniform(-np.pi, np.pi, size=(L, n_ant_draws, 1))
+            phi = rng.uniform(0.0, 2.0 * np.pi, size=(L, n_ant_draws, M))
+            alpha = (2.0 * np.pi * np.arange(1, M + 1) - np.pi + theta) / M  # [L, b', M]
+            ph = 2.0 * np.pi * cfg.doppler_hz * np.cos(alpha)[..., None] * t_n + phi[..., None]
+            a = np.exp(1j * ph).sum(axis=2) / np.sqrt(M)  # [L, b', T]
+        a = a * np.sqrt(pdp)[:, None, None]
+        if cfg.ula:
+            aoa = rng.uniform(-np.pi / 3.0, np.pi / 3.0, size=L)
+            steer = np.exp(1j * np.pi * np.arange(B)[None, :] * np.sin(aoa)[:, None])  # [L, B]
+            a = a[:, 0:1, :] * steer[:, :, None]  # [L, B, T]
+        phase = np.exp(-2j * np.pi * f_s[None, :] * tau[:, None])  # [L, S]
+        h[u] = np.einsum("lbt,ls->bts", a, phase)
+    return h
+
+
+# ----------------------------------------------------------------------------
+# Slots
+# ----------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class Slot:
+    cfg: SlotConfig
+    y: np.ndarray          # complex64 [B, 14, S]: the received grid
+    dmrs: np.ndarray       # complex64 [n_dmrs, S/2]: DMRS base sequence per DMRS symbol
+    bits: List[np.ndarray]  # per user uint8 [n_data_RE, m_u], RE order t-major then s
+    h: np.ndarray          # complex128 [U, B, 14, S]: true channel
+    x: np.ndarray          # complex128 [U, 14, S]: transmitted grid
+
+
+def make_slot(cfg: SlotConfig, rng: np.random.Generator, channel: np.ndarray | None = None) -> Slot:
+    """Generate one received slot (Eq. 1).  ``channel`` overrides the TDL draw
+    (shape [U, B, 14, S]); used by tests that need e.g. a flat channel."""
+    S = cfg.num_subcarriers
+    n_dmrs = len(cfg.dmrs_symbols)
+    qpsk = (1.0 - 2.0 * rng.integers(0, 2, size=(n_dmrs, S // 2, 2))) / np.sqrt(2.0)
+    dmrs = (qpsk[..., 0] + 1j * qpsk[..., 1]).astype(np.complex64)
+    n_data = cfg.num_data_symbols * S
+    bits = [rng.integers(0, 2, size=(n_data, m), dtype=np.uint8) for m in cfg.bits_per_symbol]
+    x = transmit_grid(cfg, dmrs, bits)
+    h = tdl_channel(cfg, rng) if channel is None else np.asarray(channel, dtype=np.complex128)
+    n0 = cfg.noise_var
+    noise = np.sqrt(n0 / 2.0) * (rng.standard_normal((cfg.num_rx_ant, NUM_SYMBOLS, S))
+                                + 1j * rng.standard_normal((cfg.num_rx_ant, NUM_SYMBOLS, S)))
+    y = np.einsum("ubts,uts->bts", h, x) + noise
+    return Slot(cfg=cfg, y=y.astype(np.complex64), dmrs=dmrs, bits=bits, h=h, x=x)
+
+
+def workload_slots(w: Workload, n: int | None = None, start: int = 0) -> List[Slot]:
+    """Slots ``start .. start+n-1`` of a workload (seed 1000*seed_base + i)."""
+    n = w.batch if n is None else n
+    out = []
+    for i in range(start, start + n):
+        rng = np.random.Generator(np.random.PCG64(1000 * w.seed_base + i))
+        out.append(make_slot(draw_slot_config(w, rng), rng))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Weights
+# ----------------------------------------------------------------------------
+
+WEIGHT_MAGIC = 0x5758524E  # "NRXW" little-endian
+WEIGHT_VERSION = 1
+
+
+def weight_layout(net: NetConfig) -> List[tuple]:
+    """(name, shape) of every tensor in blob order.  Dense weights are
+    [out, in] row-major (y = W x + b); depthwise kernels are [C, 3, 3] indexed
+    [channel, symbol offset + 1, subcarrier offset + 1]."""
+    C, F, m = net.channels, net.in_features, net.m_max
+    lay = [("init.pw.w", (C, F)), ("init.pw.b", (C,)), ("init.dw", (C, 3, 3))]
+    for k in range(net.iterations):
+        p = f"it{k}."
+        lay += [(p + "mp1.w", (C, C)), (p + "mp1.b", (C,)),
+                (p + "mp2.w", (C, C)), (p + "mp2.b", (C,)),
+                (p + "in.w", (C, 2 * C + 2)), (p + "in.b", (C,))]
+        for r in range(net.res_blocks):
+            q = f"{p}blk{r}."
+            lay += [(q + "dw1", (C, 3, 3)), (q + "pw1.w", (C, C)), (q + "pw1.b", (C,)),
+                    (q + "dw2", (C, 3, 3)), (q + "pw2.w", (C, C)), (q + "pw2.b", (C,))]
+    lay += [("ro1.w", (C, C)), ("ro1.b", (C,)), ("ro2.w", (m, C)), ("ro2.b", (m,))]
+    return lay
+
+
+def make_weights(net: NetConfig, seed: int = 42) -> Dict[str, np.ndarray]:
+    """Seeded Gaussian initialisation (float32): He-normal N(0, 2/fan_in) for
+    dense layers, N(0, 2/9) for depthwise taps, N(0, 0.01^2) biases; the last
+    dense layer of each residual branch is scaled by 1/sqrt(R * N_it)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    scale_last = 1.0 / np.sqrt(net.res_blocks * net.iterations)
+    out = {}
+    for name, shape in weight_layout(net):
+        if name.endswith(".b"):
+            v = 0.01 * rng.standard_normal(shape)
+        elif name.endswith("dw") or name.endswith("dw1") or name.endswith("dw2"):
+            v = np.sqrt(2.0 / 9.0) * rng.standard_normal(shape)
+        else:
+            v = np.sqrt(2.0 / shape[1]) * rng.standard_normal(shape)
+            if name.endswith("pw2.w"):
+                v = v * scale_last
+        out[name] = v.astype(np.float32)
+    return out
+
+
+def pack_weights(net: NetConfig, weights: Dict[str, np.ndarray]) -> bytes:
+    """Serialise to the flat blob: a 32-byte header of eight little-endian
+    int32 (magic, version, B, C, R, N_it, m_max, total float count) followed by
+    the float32 tensors in ``weight_layout`` order."""
+    arrs = [np.ascontiguousarray(weights[n], dtype=np.float32).reshape(-1) for n, _ in weight_layout(net)]
+    total = int(sum(a.size for a in arrs))
+    hdr = struct.pack("<8i", WEIGHT_MAGIC, WEIGHT_VERSION, net.num_rx_ant, net.channels,
+                      net.res_blocks, net.iterations, net.m_max, total)
+    return hdr + b"".join(a.tobytes() for a in arrs)
+
+
+def zero_like_residual(net: NetConfig, weights: Dict[str, np.ndarray]) -> Dict[str, np.ndarray]:
+    """Copy of ``weights`` with every message-MLP output layer, CNN-update input
+    layer and residual branch output layer zeroed (used by composition tests)."""
+    w = {k: v.copy() for k, v in weights.items()}
+    for k in w:
+        if any(k.endswith(s) for s in ("mp2.w", "mp2.b", "in.w", "in.b", "pw2.w", "pw2.b")):
+            w[k][...] = 0.0
+    return w
+
+
+def stack_batch(slots: Sequence[Slot]) -> np.ndarray:
+    """Contiguous complex64 [n_slots, B, 14, S] grid of same-shaped slots."""
+    return np.stack([s.y for s in slots]).astype(np.complex64)
