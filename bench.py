@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the NRX forward pass on the 273-PRB, 4-user, 4-Rx slot
+(batch of 8 slots, C=64, R=2, N_it=2), through the C ABI.
+
+One step = one nrx_detect_batch over the batch (DMRS LS + interpolation,
+StateInit, 2 CGNN iterations, ReadoutLLRs with masking), inputs resident in
+HBM; the L2 is flushed (a 256 MB write) before every timed step.  Prints one
+JSON line (rank 0).  Under torchrun each rank runs an independent replica on
+its own slots (weak scaling, no data-path collective).
+
+--impl reference times the FP64 CPU oracle on the host cores instead (one slot
+of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2409_02912_b300 import synth  # noqa: E402
+
+WORKLOAD = "mu4_4rx_273prb"
+METRIC = "NRX REs/s and p99 slot latency on 1 B300, BF16/FP8 vs FP32 at matched BLER"
+UNIT = "REs/s"
+FP32_CORE_FLOP_PER_CLK_PER_SM = 256  # 128 FP32 lanes x FMA
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["auto", "fp32", "bf16"], default="auto")
+    ap.add_argument("--no-extras", action="store_true", help="skip latency/compare/e2e/cpu legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0}, \
+            "fallback"
+
+
+def nrx_flops_per_re_ue(net: synth.NetConfig) -> dict:
+    """Algorithmic FLOPs per RE and user of each kernel kind (2 per MAC)."""
+    C, F, R, m = net.channels, net.in_features, net.res_blocks, net.m_max
+    return {
+        "state_init": 2 * (F * C + 9 * C),
+        "message_passing": 2 * (2 * C * C + (2 * C + 2) * C),
+        "residual_block": 2 * (2 * 9 * C + 2 * C * C),
+        "readout": 2 * (C * C + C * m),
+    }
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_slot_seconds(slots, W64, net):
+    from oracle import nrx_oracle as O
+    t0 = time.perf_counter()
+    for s in slots:
+        c = s.cfg
+        O.nrx_forward(s.y, s.dmrs, c.num_users, c.dmrs_symbols, c.bits_per_symbol, W64, net.iterations,
+                      net.res_blocks)
+    return time.perf_counter() - t0
+
+
+def blas_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        return max(n) if n else 1
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def res_per_slot(w: synth.Workload) -> int:
+    return synth.NUM_SYMBOLS * 12 * w.num_prb
+
+
+def run_reference(args, rank, world):
+    """FP64 CPU oracle on the host cores, one slot of the workload per step."""
+    if rank != 0:
+        return
+    w = synth.WORKLOADS[WORKLOAD]
+    W64 = {k: v.astype(np.float64) for k, v in synth.make_weights(w.net).items()}
+    slots = synth.workload_slots(w, w.batch)
+    for i in range(args.warmup):
+        oracle_slot_seconds([slots[i % len(slots)]], W64, w.net)
+    secs = [oracle_slot_seconds([slots[i % len(slots)]], W64, w.net) for i in range(args.steps)]
+    total = sum(secs)
+    value = args.steps * res_per_slot(w) / total
+    cores = blas_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "slots_per_step": 1, "users": w.num_users,
+                                        "num_rx_ant": w.num_rx_ant, "num_prb": w.num_prb,
+                                        "net": "C64 R2 N_it2 m_max6"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} slots of {WORKLOAD}, one per step, FP64 numpy oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def traffic_for(kernel: str, precision: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
+    kernel source has not changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[f"{kernel}/{precision}"]
+    except (OSError, KeyError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_2409_02912_b300", "csrc", rec["source"])
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return rec["bytes_per_launch"] if sha == rec["sha256"] else None
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_2409_02912_b300 import nrx
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    w = synth.WORKLOADS[WORKLOAD]
+    net = w.net
+    blob = synth.pack_weights(net, synth.make_weights(net))
+    slots = synth.workload_slots(w, w.batch, start=rank * w.batch)
+    n = len(slots)
+    S = 12 * w.num_prb
+    y = torch.from_numpy(synth.stack_batch(slots)).to(dev)
+    dmrs = torch.from_numpy(np.stack([s.dmrs for s in slots])).to(dev)
+    bits = [list(s.cfg.bits_per_symbol) for s in slots]
+    nv = [s.cfg.noise_var for s in slots]
+
+    precision = args.precision
+    if precision == "auto":
+        try:
+            nrx.Receiver(blob, net.num_rx_ant, w.num_users, w.num_prb, n, "bf16").close()
+            precision = "bf16"
+        except nrx.NrxError:
+            precision = "fp32"
+    rx = nrx.Receiver(blob, net.num_rx_ant, w.num_users, w.num_prb, n, precision)
+    n_llr = sum(rx.llr_count(nrx.make_cfgs(1, w.num_prb, w.num_users, w.dmrs_symbols, [0], [1.0])[0], b)
+                for b in bits)
+    llr = torch.empty(n_llr, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits, out=llr, stream=stream)
+
+    def timed(fn, k):
+        ts = []
+        for _ in range(k):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ts.append((a, b))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ts]
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = rx.last_launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    rx.nrx_profile(True)
+    rx.nrx_profile_read(reset=True)
+    times = timed(step, args.steps)
+    rx.nrx_profile(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = rx.nrx_profile_read(reset=True)
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    res_step = n * res_per_slot(w)
+    value = world * args.steps * res_step / (total_ms * 1e-3)
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # per-slot latency at batch 1 and batch-8 latency percentiles
+        y1, d1, b1 = y[:1], dmrs[:1], bits[:1]
+        lat1 = timed(lambda: rx.nrx_detect_batch(y1, d1, w.dmrs_symbols, b1, out=llr, stream=stream), 50)
+        extras["latency_us"] = {
+            "slot_batch1_p50": 1e3 * float(np.percentile(lat1, 50)),
+            "slot_batch1_p99": 1e3 * float(np.percentile(lat1, 99)),
+            "batch8_p50": 1e3 * float(np.percentile(times, 50)),
+            "batch8_p99": 1e3 * float(np.percentile(times, 99)),
+        }
+        # the other receivers on the same slots
+        cmp = {}
+        for other in ("fp32", "bf16"):
+            if other == precision:
+                continue
+            try:
+                rx2 = nrx.Receiver(blob, net.num_rx_ant, w.num_users, w.num_prb, n, other)
+            except nrx.NrxError:
+                continue
+            f = lambda: rx2.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits, out=llr, stream=stream)
+            for _ in range(3):
+                f()
+            ts = timed(f, max(5, args.steps // 2))
+            cmp[f"nrx_{other}"] = {"value": res_step / (1e-3 * statistics.mean(ts)), "unit": UNIT,
+                                   "ms_per_step": statistics.mean(ts)}
+            rx2.close()
+        f = lambda: rx.lmmse_detect_batch(y, dmrs, w.dmrs_symbols, bits, nv, out=llr, stream=stream)
+        for _ in range(3):
+            f()
+        ts = timed(f, max(5, args.steps // 2))
+        cmp["lmmse_fp32"] = {"value": res_step / (1e-3 * statistics.mean(ts)), "unit": UNIT,
+                             "ms_per_step": statistics.mean(ts)}
+        extras["compare"] = cmp
+        # end to end through the host-buffer entry point
+        y_h = torch.from_numpy(synth.stack_batch(slots)).pin_memory()
+        d_h = torch.from_numpy(np.stack([s.dmrs for s in slots])).pin_memory()
+        l_h = torch.empty(n_llr, dtype=torch.float32).pin_memory()
+        for _ in range(3):
+            rx.nrx_detect_batch_host(y_h, d_h, w.dmrs_symbols, bits, l_h, stream=stream)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            rx.nrx_detect_batch_host(y_h, d_h, w.dmrs_symbols, bits, l_h, stream=stream)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        extras["e2e"] = {"value": res_step / e2e_s, "unit": UNIT,
+                         "h2d_bytes_per_step": int(y_h.numel() * 8 + d_h.numel() * 8),
+                         "d2h_bytes_per_step": int(n_llr * 4)}
+        # CPU baseline: the FP64 oracle on one slot of the same workload
+        W64 = {k: v.astype(np.float64) for k, v in synth.make_weights(net).items()}
+        secs = oracle_slot_seconds(slots[:1], W64, net)
+        extras["cpu_baseline"] = {"value": res_per_slot(w) / secs, "unit": UNIT, "cores": blas_threads(),
+                                  "kind": "oracle", "sample": f"1 slot of {WORKLOAD} (45864 REs), FP64 numpy oracle"}
+
+    # roofline of the dominant kernel
+    pk, src = peaks()
+    kern = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+    k_ms, k_n = prof[kern]
+    per_launch_ms = k_ms / max(k_n, 1)
+    flops = nrx_flops_per_re_ue(net)[kern] * n * w.num_users * res_per_slot(w)
+    if precision == "fp32":
+        peak = pk["sm_max_mhz"] * 1e6 * 148 * FP32_CORE_FLOP_PER_CLK_PER_SM / 1e12
+        bound, unit = "alu", "TFLOP/s"
+    else:
+        peak = pk["bf16_tflops_sustained"]
+        bound, unit = "tensor", "TFLOP/s"
+    achieved = flops / (per_launch_ms * 1e-3) / 1e12
+    roofline = {"bound": bound, "kernel": kern, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "peak_source": src, "traffic": traffic_for(kern, precision),
+                "flop_per_launch": flops, "launch_ms": per_launch_ms,
+                "kernel_share": {k: prof[k][0] / max(sum(v[0] for v in prof.values()), 1e-12) for k in prof
+                                 if prof[k][1] > 0}}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": precision, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch": n, "users": w.num_users, "num_rx_ant": w.num_rx_ant,
+                       "num_prb": w.num_prb, "net": "C64 R2 N_it2 m_max6", "l2": "flushed before each step",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "roofline": roofline,
+        }
+        line.update(extras)
+        if "e2e" not in line:
+            line["e2e"] = None
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,414 @@
+// Front end of both receivers: DMRS LS estimation, linear interpolation and
+// positional encoding, fused into (a) the NRX StateInit kernel and (b) the
+// per-RE LMMSE + max-log kernel (the "LS + LMMSE" baseline of Fig. 3).
+#include "common.cuh"
+#include "kernels.h"
+
+// ---------------------------------------------------------------------------
+// StateInit (Sec. II-A): S0 = ReLU(DW(PW(x_u))), x_u = [y, h_u, PE].
+// One CTA per (subcarrier tile of TW, user, slot), all 14 symbols.  The PW
+// output is formed on the tile plus a one-subcarrier halo (zero outside the
+// grid, i.e. the depthwise input's zero padding), then the 3x3 depthwise and
+// ReLU produce the tile.  FP32 CUDA-core arithmetic; output FP32 or BF16.
+// ---------------------------------------------------------------------------
+template <int C, typename OutT>
+__global__ void __launch_bounds__(256) k_state_init(Geometry g, SlotTable tab, const float2* __restrict__ y,
+                                                    const float* __restrict__ w_pw,  // [C][F]
+                                                    const float* __restrict__ b_pw,  // [C]
+                                                    const float* __restrict__ k_dw,  // [C][9]
+                                                    OutT* __restrict__ s_out) {
+  constexpr int TW = kStateInitTile;
+  constexpr int EW = TW + 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* hf = reinterpret_cast<float2*>(smem_raw);          // [2][B][EW]
+  float* wt = reinterpret_cast<float*>(hf + 2 * NRX_MAX_RX * EW);  // [F][C]
+  float* feat = wt + (4 * NRX_MAX_RX + 2) * C;              // [14][EW][F]
+  float* h = feat + NRX_SYMBOLS * EW * (4 * NRX_MAX_RX + 2);  // [14][EW][C]
+
+  const int tile = blockIdx.x, u = blockIdx.y, sl = blockIdx.z;
+  const int S = g.S, B = g.B, F = g.F;
+  const int s0 = tile * TW - 1;
+  const float2* ys = y + (size_t)sl * B * NRX_SYMBOLS * S;
+
+  for (int i = threadIdx.x; i < F * C; i += blockDim.x) {
+    const int c = i % C, f = i / C;
+    wt[f * C + c] = __ldg(w_pw + c * F + f);
+  }
+  for (int i = threadIdx.x; i < g.n_dmrs * B * EW; i += blockDim.x) {
+    const int e = i % EW, b = (i / EW) % B, d = i / (EW * B);
+    const int s = s0 + e;
+    float2 v = make_float2(0.f, 0.f);
+    if (s >= 0 && s < S) {
+      const int td = d == 0 ? g.td0 : g.td1;
+      v = ls_interp_freq(ys + ((size_t)b * NRX_SYMBOLS + td) * S, tab.dmrs[sl] + (size_t)d * (S / 2), u, g.U, S, s);
+    }
+    hf[(d * B + b) * EW + e] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NRX_SYMBOLS * EW; i += blockDim.x) {
+    const int t = i / EW, e = i % EW, s = s0 + e;
+    float* f = feat + i * F;
+    if (s < 0 || s >= S) {
+      for (int k = 0; k < F; ++k) f[k] = 0.f;
+      continue;
+    }
+    for (int b = 0; b < B; ++b) {
+      const float2 v = __ldg(ys + ((size_t)b * NRX_SYMBOLS + t) * S + s);
+      f[2 * b] = v.x;
+      f[2 * b + 1] = v.y;
+    }
+    for (int b = 0; b < B; ++b) {
+      const float2 hv = interp_time(g, t, hf[b * EW + e], hf[((g.n_dmrs - 1) * B + b) * EW + e]);
+      f[2 * B + 2 * b] = hv.x;
+      f[2 * B + 2 * b + 1] = hv.y;
+    }
+    f[4 * B] = pe_time(g, t);
+    f[4 * B + 1] = pe_freq(u, s);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NRX_SYMBOLS * EW * C; i += blockDim.x) {
+    const int c = i % C, re = i / C;
+    const int s = s0 + re % EW;
+    float acc = 0.f;
+    if (s >= 0 && s < S) {
+      acc = __ldg(b_pw + c);
+      const float* f = feat + re * F;
+      for (int k = 0; k < F; ++k) acc = fmaf(wt[k * C + c], f[k], acc);
+    }
+    h[re * C + c] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NRX_SYMBOLS * TW * C; i += blockDim.x) {
+    const int c = i % C, re = i / C;
+    const int t = re / TW, x = re % TW, s = tile * TW + x;
+    if (s >= S) continue;
+    float acc = 0.f;
+#pragma unroll
+    for (int dt = -1; dt <= 1; ++dt) {
+      const int tt = t + dt;
+      if (tt < 0 || tt >= NRX_SYMBOLS) continue;
+#pragma unroll
+      for (int ds = -1; ds <= 1; ++ds)
+        acc = fmaf(__ldg(k_dw + c * 9 + (dt + 1) * 3 + (ds + 1)), h[(tt * EW + x + 1 + ds) * C + c], acc);
+    }
+    s_out[((((size_t)sl * g.U + u) * NRX_SYMBOLS + t) * S + s) * C + c] = store_cast<OutT>(fmaxf(acc, 0.f));
+  }
+}
+
+size_t state_init_smem_bytes(int C) {
+  constexpr int EW = kStateInitTile + 2;
+  return sizeof(float2) * 2 * NRX_MAX_RX * EW + sizeof(float) * (4 * NRX_MAX_RX + 2) * C +
+         sizeof(float) * NRX_SYMBOLS * EW * (4 * NRX_MAX_RX + 2) + sizeof(float) * NRX_SYMBOLS * EW * C;
+}
+
+template <typename OutT>
+cudaError_t launch_state_init(const Geometry& g, const SlotTable& tab, const float2* y, const float* w_pw,
+                              const float* b_pw, const float* k_dw, OutT* s_out, cudaStream_t st) {
+  dim3 grid((g.S + kStateInitTile - 1) / kStateInitTile, g.U, g.n_slots);
+  const size_t smem = state_init_smem_bytes(g.C);
+  if (g.C == 64) {
+    cudaFuncSetAttribute(k_state_init<64, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_state_init<64, OutT><<<grid, 256, smem, st>>>(g, tab, y, w_pw, b_pw, k_dw, s_out);
+  } else if (g.C == 32) {
+    cudaFuncSetAttribute(k_state_init<32, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_state_init<32, OutT><<<grid, 256, smem, st>>>(g, tab, y, w_pw, b_pw, k_dw, s_out);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_state_init<float>(const Geometry&, const SlotTable&, const float2*, const float*,
+                                              const float*, const float*, float*, cudaStream_t);
+template cudaError_t launch_state_init<__nv_bfloat16>(const Geometry&, const SlotTable&, const float2*,
+                                                      const float*, const float*, const float*, __nv_bfloat16*,
+                                                      cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// LS + LMMSE + max-log.  Per data RE: H = interpolated LS estimates [B x U],
+// G = H^H H + N0 I, Cholesky G = L L^H, xhat = G^-1 H^H y,
+// d_u = [G^-1 H^H H]_uu, xt_u = xhat_u / d_u, var_u = 1/d_u - 1, then max-log
+// over the user's Gray QAM (per I/Q PAM dimension).  FP32; a RE whose
+// Cholesky pivots spread by more than 1e6 (or is not positive) is redone in
+// FP64.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Cx {
+  T re, im;
+};
+template <typename T>
+__device__ __forceinline__ Cx<T> cx_mul(Cx<T> a, Cx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> cx_mulc(Cx<T> a, Cx<T> b) {  // conj(a) * b
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+
+// Per-RE LMMSE solve for U users and B antennas (compile-time).  Returns false
+// if a Cholesky pivot is not positive or the pivots spread by more than 1e6.
+// Outputs xhat = G^-1 H^H y, d_u = Re [G^-1 H^H H]_uu and e_u = N0 [G^-1]_uu;
+// since G^-1 H^H H = I - N0 G^-1, the post-equalisation variance 1/d_u - 1
+// equals e_u / d_u, which callers use to avoid the cancellation of 1/d - 1
+// near d = 1 (high SNR).
+template <typename T, int U, int B>
+__device__ __forceinline__ bool lmmse_solve(const Cx<T> (&H)[U][B], const Cx<T> (&yv)[B], T n0, Cx<T> (&xhat)[U],
+                                            T (&d)[U], T (&e)[U]) {
+  Cx<T> A[U][U], rhs[U];
+#pragma unroll
+  for (int i = 0; i < U; ++i) {
+    rhs[i] = {0, 0};
+#pragma unroll
+    for (int j = 0; j < U; ++j) A[i][j] = {0, 0};
+  }
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const Cx<T> c = cx_mulc(H[i][b], yv[b]);
+      rhs[i].re += c.re;
+      rhs[i].im += c.im;
+#pragma unroll
+      for (int j = 0; j <= i; ++j) {
+        const Cx<T> a = cx_mulc(H[i][b], H[j][b]);
+        A[i][j].re += a.re;
+        A[i][j].im += a.im;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < U; ++i)
+#pragma unroll
+    for (int j = i + 1; j < U; ++j) A[i][j] = {A[j][i].re, -A[j][i].im};
+  // Cholesky of G = A + n0 I (lower, real diagonal)
+  Cx<T> L[U][U];
+  T piv_min = (T)1e30, piv_max = (T)0;
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < U; ++i) {
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      Cx<T> s = A[i][j];
+      if (i == j) s.re += n0;
+#pragma unroll
+      for (int k = 0; k < j; ++k) {
+        s.re -= L[i][k].re * L[j][k].re + L[i][k].im * L[j][k].im;  // L[i][k] conj(L[j][k])
+        s.im -= L[i][k].im * L[j][k].re - L[i][k].re * L[j][k].im;
+      }
+      if (i == j) {
+        if (!(s.re > (T)0)) ok = false;
+        piv_min = s.re < piv_min ? s.re : piv_min;
+        piv_max = s.re > piv_max ? s.re : piv_max;
+        L[i][i] = {sqrt(s.re > (T)0 ? s.re : (T)1), (T)0};
+      } else {
+        const T inv = (T)1 / L[j][j].re;
+        L[i][j] = {s.re * inv, s.im * inv};
+      }
+    }
+  }
+  if (!ok || piv_min < (T)1e-6 * piv_max) ok = false;
+  // Li = L^-1 (lower triangular)
+  Cx<T> Li[U][U];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    Li[j][j] = {(T)1 / L[j][j].re, (T)0};
+#pragma unroll
+    for (int i = j + 1; i < U; ++i) {
+      Cx<T> s = {0, 0};
+#pragma unroll
+      for (int k = j; k < i; ++k) {
+        const Cx<T> p = cx_mul(L[i][k], Li[k][j]);
+        s.re += p.re;
+        s.im += p.im;
+      }
+      const T inv = -(T)1 / L[i][i].re;
+      Li[i][j] = {s.re * inv, s.im * inv};
+    }
+  }
+  // Ginv = Li^H Li ; xhat = Ginv rhs ; d_u = Re (Ginv A)_uu
+#pragma unroll
+  for (int a = 0; a < U; ++a) {
+    Cx<T> xs = {0, 0};
+    T dd = 0;
+#pragma unroll
+    for (int b = 0; b < U; ++b) {
+      Cx<T> gi = {0, 0};
+#pragma unroll
+      for (int k = (a > b ? a : b); k < U; ++k) {
+        const Cx<T> p = cx_mulc(Li[k][a], Li[k][b]);
+        gi.re += p.re;
+        gi.im += p.im;
+      }
+      const Cx<T> p = cx_mul(gi, rhs[b]);
+      xs.re += p.re;
+      xs.im += p.im;
+      dd += gi.re * A[b][a].re - gi.im * A[b][a].im;
+      if (b == a) e[a] = n0 * gi.re;
+    }
+    xhat[a] = xs;
+    d[a] = dd;
+  }
+  return ok;
+}
+
+// FP64 redo of one RE (taken when the FP32 Cholesky is ill-conditioned).
+template <int U, int B>
+__device__ __noinline__ void lmmse_solve_f64(const Cx<float> (&H)[U][B], const Cx<float> (&yv)[B], float n0,
+                                             float (&xr)[U], float (&xi)[U], float (&iv)[U]) {
+  Cx<double> Hd[U][B], yd[B], xd[U];
+  double dd[U], ed[U];
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    yd[b] = {(double)yv[b].re, (double)yv[b].im};
+#pragma unroll
+    for (int u = 0; u < U; ++u) Hd[u][b] = {(double)H[u][b].re, (double)H[u][b].im};
+  }
+  lmmse_solve<double, U, B>(Hd, yd, (double)n0, xd, dd, ed);
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    xr[u] = (float)(xd[u].re / dd[u]);
+    xi[u] = (float)(xd[u].im / dd[u]);
+    iv[u] = (float)(dd[u] / ed[u]);
+  }
+}
+
+// Gray PAM level of label l with K bits (bit j of the label = (l >> (K-1-j)) & 1,
+// j = 0 the sign bit): level = (1-2c0) * mag, mag built from the innermost bit out,
+// mag <- 2^(K-j) - (1-2c_j) mag for j = K-1 .. 1, starting from 1.
+template <int K>
+__device__ __forceinline__ float pam_level(int l) {
+  float mag = 1.f;
+#pragma unroll
+  for (int j = K - 1; j >= 1; --j) {
+    const int c = (l >> (K - 1 - j)) & 1;
+    mag = (float)(1 << (K - j)) - (1.f - 2.f * c) * mag;
+  }
+  const int c0 = (l >> (K - 1)) & 1;
+  return (1.f - 2.f * c0) * mag;
+}
+
+// Max-log LLRs of the I component xr and Q component xi for 2K-bit Gray QAM;
+// QAM bit 2j is I-PAM bit j, bit 2j+1 is Q-PAM bit j.  Stores 2K floats.
+template <int K>
+__device__ __forceinline__ void qam_maxlog_store(float xr, float xi, float inv_var, float* __restrict__ dst) {
+  const float scale = rsqrtf(2.f * (float)((1 << (2 * K)) - 1) / 3.f);
+  float o[2 * K];
+#pragma unroll
+  for (int dim = 0; dim < 2; ++dim) {
+    const float x = dim == 0 ? xr : xi;
+    float d0[K], d1[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) d0[j] = d1[j] = 1e30f;
+#pragma unroll
+    for (int l = 0; l < (1 << K); ++l) {
+      const float e = x - pam_level<K>(l) * scale;
+      const float dist = e * e;
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        if ((l >> (K - 1 - j)) & 1)
+          d1[j] = fminf(d1[j], dist);
+        else
+          d0[j] = fminf(d0[j], dist);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) o[2 * j + dim] = (d0[j] - d1[j]) * inv_var;
+  }
+#pragma unroll
+  for (int j = 0; j < 2 * K; ++j) dst[j] = o[j];
+}
+
+template <int TW, int U, int B>
+__global__ void __launch_bounds__(256) k_lmmse(Geometry g, SlotTable tab, const float2* __restrict__ y,
+                                               float* __restrict__ llr) {
+  __shared__ float2 hf[U][2][B][TW];
+  const int tile = blockIdx.x, sl = blockIdx.y;
+  const int S = g.S;
+  const float2* ys = y + (size_t)sl * B * NRX_SYMBOLS * S;
+  for (int i = threadIdx.x; i < U * g.n_dmrs * B * TW; i += blockDim.x) {
+    const int e = i % TW, b = (i / TW) % B, d = (i / (TW * B)) % g.n_dmrs, u = i / (TW * B * g.n_dmrs);
+    const int s = tile * TW + e;
+    float2 v = make_float2(0.f, 0.f);
+    if (s < S) {
+      const int td = d == 0 ? g.td0 : g.td1;
+      v = ls_interp_freq(ys + ((size_t)b * NRX_SYMBOLS + td) * S, tab.dmrs[sl] + (size_t)d * (S / 2), u, U, S, s);
+    }
+    hf[u][d][b][e] = v;
+  }
+  __syncthreads();
+  const float n0 = tab.noise_var[sl];
+  const int n_data_sym = NRX_SYMBOLS - g.n_dmrs;
+  const int dl = g.n_dmrs - 1;
+  for (int i = threadIdx.x; i < n_data_sym * TW; i += blockDim.x) {
+    const int e = i % TW, di = i / TW;
+    const int s = tile * TW + e;
+    if (s >= S) continue;
+    const int t = g.data_t[di];
+    Cx<float> H[U][B], yv[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const float2 v = __ldg(ys + ((size_t)b * NRX_SYMBOLS + t) * S + s);
+      yv[b] = {v.x, v.y};
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float2 hv = interp_time(g, t, hf[u][0][b][e], hf[u][dl][b][e]);
+        H[u][b] = {hv.x, hv.y};
+      }
+    }
+    Cx<float> xh[U];
+    float dd[U], ee[U], xr[U], xi[U], iv[U];
+    if (lmmse_solve<float, U, B>(H, yv, n0, xh, dd, ee)) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float inv_d = 1.f / dd[u];
+        xr[u] = xh[u].re * inv_d;
+        xi[u] = xh[u].im * inv_d;
+        iv[u] = dd[u] / ee[u];  // 1 / var, var = 1/d - 1 = e/d
+      }
+    } else {
+      lmmse_solve_f64<U, B>(H, yv, n0, xr, xi, iv);
+    }
+    const int r = di * S + s;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int m = tab.bits[sl][u];
+      float* dst = llr + tab.llr_off[sl][u] + (size_t)r * m;
+      if (m == 2)
+        qam_maxlog_store<1>(xr[u], xi[u], iv[u], dst);
+      else if (m == 4)
+        qam_maxlog_store<2>(xr[u], xi[u], iv[u], dst);
+      else
+        qam_maxlog_store<3>(xr[u], xi[u], iv[u], dst);
+    }
+  }
+}
+
+template <int U, int B>
+static cudaError_t launch_lmmse_ub(const Geometry& g, const SlotTable& tab, const float2* y, float* llr,
+                                   cudaStream_t st) {
+  constexpr int TW = 32;
+  dim3 grid((g.S + TW - 1) / TW, g.n_slots);
+  k_lmmse<TW, U, B><<<grid, 256, 0, st>>>(g, tab, y, llr);
+  return cudaGetLastError();
+}
+
+template <int B>
+static cudaError_t launch_lmmse_b(const Geometry& g, const SlotTable& tab, const float2* y, float* llr,
+                                  cudaStream_t st) {
+  switch (g.U) {
+    case 1: return launch_lmmse_ub<1, B>(g, tab, y, llr, st);
+    case 2: return launch_lmmse_ub<2, B>(g, tab, y, llr, st);
+    case 3: return launch_lmmse_ub<3, B>(g, tab, y, llr, st);
+    case 4: return launch_lmmse_ub<4, B>(g, tab, y, llr, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_lmmse(const Geometry& g, const SlotTable& tab, const float2* y, float* llr, cudaStream_t st) {
+  switch (g.B) {
+    case 1: return launch_lmmse_b<1>(g, tab, y, llr, st);
+    case 2: return launch_lmmse_b<2>(g, tab, y, llr, st);
+    case 4: return launch_lmmse_b<4>(g, tab, y, llr, st);
+    case 8: return launch_lmmse_b<8>(g, tab, y, llr, st);
+  }
+  return cudaErrorInvalidValue;
+}

@@ -1,0 +1,54 @@
+// Host-side launchers of the NRX / LMMSE kernels (CUDA path only).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+constexpr int kStateInitTile = 16;  // subcarriers per StateInit CTA
+
+template <typename T>
+__device__ __forceinline__ T store_cast(float v);
+template <>
+__device__ __forceinline__ float store_cast<float>(float v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 store_cast<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+
+// Weights of one CGNN iteration on the device (FP32 path: dense layers stored
+// transposed, [in][out]; depthwise taps [C][9]).
+struct IterWeightsF32 {
+  const float* mp1_t;  // [C][C]
+  const float* mp1_b;
+  const float* mp2_t;  // [C][C]
+  const float* mp2_b;
+  const float* in_t;   // [2C+2][C]
+  const float* in_b;
+  const float* dw1[4];
+  const float* pw1_t[4];
+  const float* pw1_b[4];
+  const float* dw2[4];
+  const float* pw2_t[4];
+  const float* pw2_b[4];
+};
+
+size_t state_init_smem_bytes(int C);
+
+template <typename OutT>
+cudaError_t launch_state_init(const Geometry& g, const SlotTable& tab, const float2* y, const float* w_pw,
+                              const float* b_pw, const float* k_dw, OutT* s_out, cudaStream_t st);
+
+cudaError_t launch_lmmse(const Geometry& g, const SlotTable& tab, const float2* y, float* llr, cudaStream_t st);
+
+// FP32 CUDA-core network kernels.
+cudaError_t launch_mp_f32(const Geometry& g, const IterWeightsF32& w, const float* state, float* z,
+                          cudaStream_t st);
+cudaError_t launch_block_f32(const Geometry& g, const IterWeightsF32& w, int r, const float* z_in, float* z_out,
+                             float* state, bool last, cudaStream_t st);
+cudaError_t launch_readout_f32(const Geometry& g, const SlotTable& tab, const float* ro1_t, const float* ro1_b,
+                               const float* ro2, const float* ro2_b, const float* state, float* llr,
+                               cudaStream_t st);

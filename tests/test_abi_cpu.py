@@ -1,0 +1,81 @@
+"""The C-ABI library loads, exports every symbol include/nrx.h declares, and
+its host-side validation works without a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2409_02912_b300 import build as nrx_build
+from paper_2409_02912_b300 import nrx, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    nrx_build.build()
+    return nrx.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "nrx.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?(?:nrx_status|void|size_t|int32_t|char\s*\*|char)\s*\*?\s*(\w+)\s*\(",
+                                 text, flags=re.M)))
+
+
+def test_header_declares_the_binding_exports():
+    assert sorted(nrx.EXPORTED) == declared_functions()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_struct_layout_matches_header():
+    assert ctypes.sizeof(nrx.nrx_slot_cfg) == 40
+    assert nrx.nrx_slot_cfg.dmrs_seq.offset == 32
+
+
+def test_llr_count_and_status_strings(lib):
+    cfg = nrx.make_cfgs(1, 273, 4, (2, 11), [0], [1.0])[0]
+    bits = np.array([2, 4, 6, 6], dtype=np.int32)
+    assert lib.nrx_llr_count(ctypes.byref(cfg), bits.ctypes.data) == 12 * 3276 * 18
+    bad = np.array([2, 3, 6, 6], dtype=np.int32)
+    assert lib.nrx_llr_count(ctypes.byref(cfg), bad.ctypes.data) == 0
+    assert lib.nrx_status_string(nrx.NRX_EINVAL) == b"NRX_EINVAL"
+
+
+def _create(lib, blob, B=2, users=1, prb=4, slots=1, prec=0):
+    ctx = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    st = lib.nrx_create(buf, len(blob), B, users, prb, slots, prec, ctypes.byref(ctx))
+    if st == nrx.NRX_OK:
+        lib.nrx_destroy(ctx)
+    return st
+
+
+def test_create_rejects_bad_blobs(lib):
+    net = synth.WORKLOADS["su_2rx_4prb"].net
+    blob = synth.pack_weights(net, synth.make_weights(net))
+    assert _create(lib, blob[:-4]) == nrx.NRX_EINVAL            # truncated
+    assert _create(lib, b"XXXX" + blob[4:]) == nrx.NRX_EINVAL    # magic
+    assert _create(lib, blob, B=4) == nrx.NRX_EINVAL             # antenna mismatch
+    assert _create(lib, blob, users=5) == nrx.NRX_EINVAL         # limits
+    assert _create(lib, blob, prb=276) == nrx.NRX_EINVAL
+    assert _create(lib, blob, slots=65) == nrx.NRX_EINVAL
+    assert _create(lib, blob, prec=7) == nrx.NRX_EINVAL
+
+
+def test_create_without_gpu_fails_loudly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    net = synth.WORKLOADS["su_2rx_4prb"].net
+    blob = synth.pack_weights(net, synth.make_weights(net))
+    assert _create(lib, blob) == nrx.NRX_ECUDA
+    with pytest.raises(nrx.NrxError):
+        nrx.Receiver(blob, 2, 1, 4)

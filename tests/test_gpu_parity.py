@@ -1,0 +1,138 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerance: per (slot, user) max|llr_gpu - llr_oracle| / max|llr_oracle| <= 1e-4
+for FP32 arithmetic (the FP32 bound of the specification).  The full-size
+273-PRB 4-user batch of 8 slots is checked in the same launch configuration the
+benchmark times."""
+import numpy as np
+import pytest
+
+from oracle import nrx_oracle as O
+from paper_2409_02912_b300 import build as nrx_build
+from paper_2409_02912_b300 import nrx, synth
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+TOL_FP32 = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    nrx_build.build()
+    nrx.load()
+
+
+def _receiver(net, slots, prec="fp32"):
+    c = slots[0].cfg
+    return nrx.Receiver(synth.pack_weights(net, synth.make_weights(net)), net.num_rx_ant, c.num_users,
+                        c.num_prb, len(slots), prec)
+
+
+@pytest.mark.parametrize("workload", ["su_2rx_4prb", "mu2_4rx_24prb", "mu4_4rx_273prb"])
+def test_lmmse_parity(workload):
+    w, slots = H.slots_for(workload)
+    rx = _receiver(w.net, slots)
+    y, dmrs, bits, nv = H.device_inputs(slots)
+    llr = rx.lmmse_detect_batch(y, dmrs, w.dmrs_symbols, bits, nv).cpu().numpy()
+    assert rx.last_launch_count() == 1
+    errs = H.rel_errors(llr, H.oracle_lmmse(slots), slots)
+    assert max(errs) <= TOL_FP32, errs
+
+
+@pytest.mark.parametrize("workload", ["su_2rx_4prb", "mu2_4rx_24prb", "mu4_4rx_273prb"])
+def test_nrx_fp32_parity(workload):
+    w, slots = H.slots_for(workload)
+    rx = _receiver(w.net, slots)
+    y, dmrs, bits, _ = H.device_inputs(slots)
+    llr = rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits).cpu().numpy()
+    assert rx.last_launch_count() == 2 + w.net.iterations * (1 + w.net.res_blocks)
+    errs = H.rel_errors(llr, H.oracle_nrx(slots, H.weights64(w.net), w.net), slots)
+    assert max(errs) <= TOL_FP32, errs
+
+
+EDGE = [
+    # (U, B, num_prb, dmrs, C, R, N_it, bits)
+    (3, 4, 5, (2, 11), 64, 2, 2, (6, 2, 4)),
+    (4, 2, 1, (2,), 32, 1, 3, (2, 4, 6, 2)),
+    (2, 8, 3, (3, 10), 32, 2, 1, (4, 4)),
+    (1, 1, 2, (0, 13), 64, 1, 2, (6,)),
+    (4, 4, 7, (5, 6), 64, 2, 1, (2, 2, 2, 2)),
+]
+
+
+@pytest.mark.parametrize("case", EDGE)
+def test_edge_geometries(case):
+    U, B, prb, dmrs, C, R, N_it, bits = case
+    net = synth.NetConfig(num_rx_ant=B, channels=C, res_blocks=R, iterations=N_it, m_max=6)
+    rng = np.random.Generator(np.random.PCG64(77))
+    slots = []
+    for i in range(2):
+        cfg = synth.SlotConfig(num_prb=prb, num_users=U, num_rx_ant=B, dmrs_symbols=dmrs, bits_per_symbol=bits,
+                               snr_db=float(rng.uniform(0, 15)), num_taps=5, delay_spread_s=150e-9,
+                               doppler_hz=200.0, ula=bool(i))
+        slots.append(synth.make_slot(cfg, rng))
+    rx = _receiver(net, slots)
+    y, d, b, nv = H.device_inputs(slots)
+    llr = rx.nrx_detect_batch(y, d, dmrs, b).cpu().numpy()
+    errs = H.rel_errors(llr, H.oracle_nrx(slots, H.weights64(net), net), slots)
+    assert max(errs) <= TOL_FP32, errs
+    if B in (1, 2, 4, 8):
+        l2 = rx.lmmse_detect_batch(y, d, dmrs, b, nv).cpu().numpy()
+        errs = H.rel_errors(l2, H.oracle_lmmse(slots), slots)
+        assert max(errs) <= TOL_FP32, errs
+
+
+def test_early_exit_and_state_copy():
+    w, slots = H.slots_for("mu2_4rx_24prb", 3)
+    rx = _receiver(w.net, slots)
+    y, dmrs, bits, _ = H.device_inputs(slots)
+    W = H.weights64(w.net)
+    llr = rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits, iterations=1).cpu().numpy()
+    errs = H.rel_errors(llr, H.oracle_nrx(slots, W, w.net, iterations=1), slots)
+    assert max(errs) <= TOL_FP32, errs
+    for i, s in enumerate(slots):
+        st = rx.nrx_copy_state(i, s.cfg.num_users, s.cfg.num_subcarriers).cpu().numpy()
+        ref = O.nrx_states(s.y, s.dmrs, s.cfg.num_users, s.cfg.dmrs_symbols, W, 1, w.net.res_blocks)[1]
+        assert np.max(np.abs(st - ref)) <= TOL_FP32 * np.max(np.abs(ref))
+
+
+def test_host_buffer_entry_point_matches_device_call():
+    import torch
+    w, slots = H.slots_for("mu2_4rx_24prb", 4)
+    rx = _receiver(w.net, slots)
+    y, dmrs, bits, _ = H.device_inputs(slots)
+    dev = rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits).cpu().numpy()
+    y_h = torch.from_numpy(synth.stack_batch(slots)).pin_memory()
+    d_h = torch.from_numpy(np.stack([s.dmrs for s in slots])).pin_memory()
+    out = torch.empty(dev.size, dtype=torch.float32).pin_memory()
+    rx.nrx_detect_batch_host(y_h, d_h, w.dmrs_symbols, bits, out)
+    assert np.array_equal(out.numpy(), dev)
+
+
+def test_invalid_arguments_launch_nothing():
+    w, slots = H.slots_for("mu2_4rx_24prb", 2)
+    rx = _receiver(w.net, slots)
+    y, dmrs, bits, nv = H.device_inputs(slots)
+    with pytest.raises(nrx.NrxError) as e:
+        rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, [[2, 3], [2, 2]])
+    assert e.value.status == nrx.NRX_EINVAL and rx.last_launch_count() == 0
+    with pytest.raises(nrx.NrxError) as e:
+        rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, [[6, 2], [2, 2]])  # 6 > m_max of this net
+    assert e.value.status == nrx.NRX_EINVAL
+    with pytest.raises(nrx.NrxError) as e:
+        rx.lmmse_detect_batch(y, dmrs, w.dmrs_symbols, bits, [0.0, 0.1])
+    assert e.value.status == nrx.NRX_EINVAL
+    with pytest.raises(nrx.NrxError):
+        rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits, iterations=3)
+
+
+def test_results_do_not_depend_on_batch_composition():
+    """A slot's LLRs are the same alone and inside a batch (no cross-slot work)."""
+    w, slots = H.slots_for("mu2_4rx_24prb", 5)
+    rx = _receiver(w.net, slots)
+    y, dmrs, bits, _ = H.device_inputs(slots)
+    batch = rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits).cpu().numpy()
+    per, _ = H.split(batch, slots)
+    y1, d1, b1, _ = H.device_inputs(slots[3:4])
+    alone = rx.nrx_detect_batch(y1, d1, w.dmrs_symbols, b1).cpu().numpy()
+    assert np.array_equal(np.concatenate(per[3]), alone)
