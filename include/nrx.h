@@ -170,6 +170,33 @@ nrx_status nrx_detect_batch_host(nrx_ctx* ctx, int32_t n_slots, const void* y_ho
  */
 nrx_status nrx_copy_state(nrx_ctx* ctx, int32_t slot, float* state_out, void* stream);
 
+/*
+ * NRX forward pass (FP32 arithmetic) over ONE slot that allocates no device
+ * memory and needs no context.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc, such as code running while a
+ * stream is captured into a CUDA graph, real-time pipelines that fix their
+ * device memory at start-up, or plug-ins whose host framework owns every GPU
+ * allocation.
+ *   weights_header  host: the blob's 32-byte header (layout above)
+ *   weights_dev     device float32: the blob's n_floats payload, 16-byte aligned
+ *   y, cfg, bits_per_symbol, llr, stream: as nrx_detect (y device, llr device)
+ * The activation scratch is one static device array of 16 MiB per GPU that
+ * loads the library (held until the process exits); its first MiB holds the
+ * weights in kernel layout, the rest three FP32 activation tensors of
+ * num_users * 14 * 12*num_prb * C floats each.  Larger slots are rejected with
+ * NRX_EINVAL (e.g. C=64: up to 4 users x 27 PRB, 2 users x 55 PRB, 1 user x
+ * 110 PRB).  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array and keeps the last call's contents (each kernel
+ * writes scratch before reading it, so nothing needs clearing); calls whose
+ * executions overlap on the GPU race on it and must be ordered.
+ * Errors: NRX_EINVAL (bad header, slot, sizes beyond the limit, alignment),
+ * NRX_ECUDA.
+ */
+nrx_status nrx_detect_noalloc(const void* weights_header, const float* weights_dev, const void* y,
+                              const nrx_slot_cfg* cfg, const int32_t* bits_per_symbol, float* llr,
+                              void* stream);
+
 /* Network hyper-parameters of the context: B, C, R, N_it, m_max. */
 nrx_status nrx_get_net(const nrx_ctx* ctx, int32_t* num_rx_ant, int32_t* channels,
                        int32_t* res_blocks, int32_t* iterations, int32_t* m_max);

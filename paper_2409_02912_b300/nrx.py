@@ -22,7 +22,7 @@ PRECISIONS = {"fp32": NRX_FP32, "bf16": NRX_BF16}
 EXPORTED = (
     "nrx_create", "nrx_destroy", "nrx_llr_count", "nrx_detect_batch", "nrx_detect", "lmmse_detect_batch",
     "lmmse_detect", "nrx_detect_batch_host", "nrx_copy_state", "nrx_get_net", "nrx_last_launch_count",
-    "nrx_last_error", "nrx_status_string", "nrx_profile", "nrx_profile_read",
+    "nrx_last_error", "nrx_status_string", "nrx_profile", "nrx_profile_read", "nrx_detect_noalloc",
 )
 KERNEL_KINDS = 5
 
@@ -86,6 +86,8 @@ def load() -> ctypes.CDLL:
     lib.nrx_profile_read.argtypes = [P, I32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_int64), I32]
     lib.nrx_profile_read.restype = ctypes.c_int
+    lib.nrx_detect_noalloc.argtypes = [P, P, P, CFG, P, P, P]
+    lib.nrx_detect_noalloc.restype = ctypes.c_int
     lib.nrx_status_string.argtypes = [ctypes.c_int]
     lib.nrx_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -240,3 +242,24 @@ def _host_ptr(a) -> int:
         return a.ctypes.data
     assert not a.is_cuda and a.is_contiguous()
     return a.data_ptr()
+
+
+def nrx_detect_noalloc(weights_blob: bytes, weights_dev, y, dmrs, dmrs_symbols, bits, iterations: int = 0,
+                       out=None, stream=None):
+    """One slot through the allocation-free entry point.  weights_dev: float32
+    cuda tensor holding the blob's payload (bytes 32..); y: complex64 cuda
+    [B, 14, S]; dmrs: complex64 cuda [n_dmrs, S/2]; bits: [U]."""
+    import torch
+    lib = load()
+    hdr = ctypes.create_string_buffer(weights_blob[:32], 32)
+    B, T, S = y.shape
+    b = _bits_array(bits).reshape(-1)
+    cfg = make_cfgs(1, S // 12, b.size, dmrs_symbols, [dmrs.data_ptr()], [1.0], iterations)
+    n = int(lib.nrx_llr_count(cfg, b.ctypes.data))
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=y.device)
+    st = lib.nrx_detect_noalloc(hdr, weights_dev.data_ptr(), y.data_ptr(), cfg, b.ctypes.data, out.data_ptr(),
+                                _stream_ptr(stream))
+    if st != NRX_OK:
+        raise NrxError(st, "nrx_detect_noalloc")
+    return out
