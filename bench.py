@@ -42,8 +42,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["auto", "fp32", "bf16"], default="auto")
+    ap.add_argument("--precision", choices=["auto", "fp32", "bf16", "fp16"], default="auto")
     ap.add_argument("--no-extras", action="store_true", help="skip latency/compare/e2e/cpu legs")
+    ap.add_argument("--batch", type=int, default=0, help="slots per step (0 = the workload's batch of 8)")
     return ap.parse_args()
 
 
@@ -192,7 +193,8 @@ def run_ours(args, rank, world, local):
     w = synth.WORKLOADS[WORKLOAD]
     net = w.net
     blob = synth.pack_weights(net, synth.make_weights(net))
-    slots = synth.workload_slots(w, w.batch, start=rank * w.batch)
+    batch = args.batch or w.batch
+    slots = synth.workload_slots(w, batch, start=rank * batch)
     n = len(slots)
     S = 12 * w.num_prb
     y = torch.from_numpy(synth.stack_batch(slots)).to(dev)
@@ -268,7 +270,7 @@ def run_ours(args, rank, world, local):
         }
         # the other receivers on the same slots
         cmp = {}
-        for other in ("fp32", "bf16"):
+        for other in ("fp32", "bf16", "fp16"):
             if other == precision:
                 continue
             try:

@@ -91,8 +91,15 @@ typedef enum {
 
 typedef enum {
   NRX_FP32 = 0,  /* CUDA-core FP32 arithmetic and FP32 activations */
-  NRX_BF16 = 1   /* BF16 tensor-core GEMMs, FP32 accumulation, BF16 activations */
+  NRX_BF16 = 1,  /* tensor-core GEMMs (tcgen05) on BF16 operands with FP32
+                    accumulation, BF16 activations; each weight matrix is split
+                    into two BF16 parts (hi + lo, two MMA passes) */
+  NRX_FP16 = 2   /* tensor-core GEMMs on FP16 operands with FP32 accumulation,
+                    FP16 activations (the paper's deployment precision, Sec. IV-A) */
 } nrx_precision;
+/* The tensor-core modes need C = 64 (NRX_EUNSUPPORTED otherwise).  In every
+ * mode depthwise taps, biases, ReLU, the cross-user sum, residual adds and
+ * the last read-out layer are FP32 CUDA-core arithmetic. */
 
 /* Per-slot configuration.  A host struct copied at call time. */
 typedef struct {
@@ -196,6 +203,14 @@ nrx_status nrx_copy_state(nrx_ctx* ctx, int32_t slot, float* state_out, void* st
 nrx_status nrx_detect_noalloc(const void* weights_header, const float* weights_dev, const void* y,
                               const nrx_slot_cfg* cfg, const int32_t* bits_per_symbol, float* llr,
                               void* stream);
+
+/*
+ * Synchronise `stream` and report device-side failures of the previous calls:
+ * NRX_ETIMEDOUT if a kernel's bounded wait for its tensor-core work gave up
+ * (the kernel then skipped its remaining tiles; the word is cleared), NRX_ECUDA
+ * on a CUDA error, else NRX_OK.
+ */
+nrx_status nrx_check(nrx_ctx* ctx, void* stream);
 
 /* Network hyper-parameters of the context: B, C, R, N_it, m_max. */
 nrx_status nrx_get_net(const nrx_ctx* ctx, int32_t* num_rx_ant, int32_t* channels,

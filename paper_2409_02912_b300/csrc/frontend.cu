@@ -3,14 +3,32 @@
 // per-RE LMMSE + max-log kernel (the "LS + LMMSE" baseline of Fig. 3).
 #include "common.cuh"
 #include "kernels.h"
+#include "tc.cuh"
 
 // ---------------------------------------------------------------------------
 // StateInit (Sec. II-A): S0 = ReLU(DW(PW(x_u))), x_u = [y, h_u, PE].
 // One CTA per (subcarrier tile of TW, user, slot), all 14 symbols.  The PW
 // output is formed on the tile plus a one-subcarrier halo (zero outside the
 // grid, i.e. the depthwise input's zero padding), then the 3x3 depthwise and
-// ReLU produce the tile.  FP32 CUDA-core arithmetic; output FP32 or BF16.
+// ReLU produce the tile.  FP32 CUDA-core arithmetic (each thread accumulates
+// 4 REs x 4 channels of the input layer; the depthwise slides over the
+// symbols for one channel pair); output FP32, BF16 or FP16.
 // ---------------------------------------------------------------------------
+template <typename OutT>
+__device__ __forceinline__ void store_pair(OutT* p, float a, float b);
+template <>
+__device__ __forceinline__ void store_pair<float>(float* p, float a, float b) {
+  *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+template <>
+__device__ __forceinline__ void store_pair<__nv_bfloat16>(__nv_bfloat16* p, float a, float b) {
+  *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+}
+template <>
+__device__ __forceinline__ void store_pair<__half>(__half* p, float a, float b) {
+  *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+}
+
 template <int C, typename OutT>
 __global__ void __launch_bounds__(256) k_state_init(Geometry g, SlotTable tab, const float2* __restrict__ y,
                                                     const float* __restrict__ w_pw,  // [C][F]
@@ -19,22 +37,28 @@ __global__ void __launch_bounds__(256) k_state_init(Geometry g, SlotTable tab, c
                                                     OutT* __restrict__ s_out) {
   constexpr int TW = kStateInitTile;
   constexpr int EW = TW + 2;
+  constexpr int NRE = NRX_SYMBOLS * EW;  // REs of the extended tile, index t * EW + e
+  constexpr int CQ = C / 4, RG = 256 / CQ;  // PW: channel quads x RE groups
+  constexpr int CP = C / 2, NG = 256 / CP;  // DW: channel pairs x column groups
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* hf = reinterpret_cast<float2*>(smem_raw);          // [2][B][EW]
+  float2* hf = reinterpret_cast<float2*>(smem_raw);                // [2][B][EW]
   float* wt = reinterpret_cast<float*>(hf + 2 * NRX_MAX_RX * EW);  // [F][C]
-  float* feat = wt + (4 * NRX_MAX_RX + 2) * C;              // [14][EW][F]
-  float* h = feat + NRX_SYMBOLS * EW * (4 * NRX_MAX_RX + 2);  // [14][EW][C]
+  float* kd = wt + (4 * NRX_MAX_RX + 2) * C;                       // [C][9]
+  float* feat = kd + 9 * C;                                        // [NRE][F]
+  float* h = feat + NRE * (4 * NRX_MAX_RX + 2);                    // [NRE][C]
 
   const int tile = blockIdx.x, u = blockIdx.y, sl = blockIdx.z;
   const int S = g.S, B = g.B, F = g.F;
   const int s0 = tile * TW - 1;
   const float2* ys = y + (size_t)sl * B * NRX_SYMBOLS * S;
+  const int tid = threadIdx.x;
 
-  for (int i = threadIdx.x; i < F * C; i += blockDim.x) {
+  for (int i = tid; i < F * C; i += 256) {
     const int c = i % C, f = i / C;
     wt[f * C + c] = __ldg(w_pw + c * F + f);
   }
-  for (int i = threadIdx.x; i < g.n_dmrs * B * EW; i += blockDim.x) {
+  for (int i = tid; i < 9 * C; i += 256) kd[i] = __ldg(k_dw + i);
+  for (int i = tid; i < g.n_dmrs * B * EW; i += 256) {
     const int e = i % EW, b = (i / EW) % B, d = i / (EW * B);
     const int s = s0 + e;
     float2 v = make_float2(0.f, 0.f);
@@ -45,7 +69,7 @@ __global__ void __launch_bounds__(256) k_state_init(Geometry g, SlotTable tab, c
     hf[(d * B + b) * EW + e] = v;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < NRX_SYMBOLS * EW; i += blockDim.x) {
+  for (int i = tid; i < NRE; i += 256) {
     const int t = i / EW, e = i % EW, s = s0 + e;
     float* f = feat + i * F;
     if (s < 0 || s >= S) {
@@ -66,39 +90,64 @@ __global__ void __launch_bounds__(256) k_state_init(Geometry g, SlotTable tab, c
     f[4 * B + 1] = pe_freq(u, s);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < NRX_SYMBOLS * EW * C; i += blockDim.x) {
-    const int c = i % C, re = i / C;
-    const int s = s0 + re % EW;
-    float acc = 0.f;
-    if (s >= 0 && s < S) {
-      acc = __ldg(b_pw + c);
-      const float* f = feat + re * F;
-      for (int k = 0; k < F; ++k) acc = fmaf(wt[k * C + c], f[k], acc);
+  // PW (+ bias), zero outside the grid: thread = channel quad cq, REs rg + RG*j.
+  {
+    const int cq = tid % CQ, rg = tid / CQ;
+    const float4 bias = __ldg(reinterpret_cast<const float4*>(b_pw) + cq);
+    for (int r0 = rg; r0 < NRE; r0 += 4 * RG) {
+      float4 acc[4];
+      int rr[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        acc[j] = bias;
+        rr[j] = r0 + j * RG < NRE ? r0 + j * RG : r0;
+      }
+      for (int k = 0; k < F; ++k) {
+        const float4 w = *reinterpret_cast<const float4*>(wt + k * C + 4 * cq);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float x = feat[rr[j] * F + k];
+          acc[j].x = fmaf(w.x, x, acc[j].x);
+          acc[j].y = fmaf(w.y, x, acc[j].y);
+          acc[j].z = fmaf(w.z, x, acc[j].z);
+          acc[j].w = fmaf(w.w, x, acc[j].w);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = r0 + j * RG;
+        if (r >= NRE) continue;
+        const int s = s0 + r % EW;
+        *reinterpret_cast<float4*>(h + r * C + 4 * cq) = (s >= 0 && s < S) ? acc[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
-    h[re * C + c] = acc;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < NRX_SYMBOLS * TW * C; i += blockDim.x) {
-    const int c = i % C, re = i / C;
-    const int t = re / TW, x = re % TW, s = tile * TW + x;
-    if (s >= S) continue;
-    float acc = 0.f;
+  // DW + ReLU: thread = channel pair cp, output columns x = cg, cg + NG, ...
+  {
+    const int cp = tid % CP, cg = tid / CP;
+    float2 kk[9];
 #pragma unroll
-    for (int dt = -1; dt <= 1; ++dt) {
-      const int tt = t + dt;
-      if (tt < 0 || tt >= NRX_SYMBOLS) continue;
-#pragma unroll
-      for (int ds = -1; ds <= 1; ++ds)
-        acc = fmaf(__ldg(k_dw + c * 9 + (dt + 1) * 3 + (ds + 1)), h[(tt * EW + x + 1 + ds) * C + c], acc);
+    for (int i = 0; i < 9; ++i) kk[i] = make_float2(kd[(2 * cp) * 9 + i], kd[(2 * cp + 1) * 9 + i]);
+    OutT* out_base = s_out + (((size_t)sl * g.U + u) * NRX_SYMBOLS) * S * C;
+    for (int x = cg; x < TW; x += NG) {
+      const int s = tile * TW + x;
+      if (s >= S) continue;
+      const float* col = h + x * C + 2 * cp;
+      tc::dw_column(
+          kk, [&](int ti, int k) { return *reinterpret_cast<const float2*>(col + (ti * EW + k) * C); },
+          [&](int t, float2 v) {
+            store_pair<OutT>(out_base + ((size_t)t * S + s) * C + 2 * cp, fmaxf(v.x, 0.f), fmaxf(v.y, 0.f));
+          });
     }
-    s_out[((((size_t)sl * g.U + u) * NRX_SYMBOLS + t) * S + s) * C + c] = store_cast<OutT>(fmaxf(acc, 0.f));
   }
 }
 
 size_t state_init_smem_bytes(int C) {
   constexpr int EW = kStateInitTile + 2;
-  return sizeof(float2) * 2 * NRX_MAX_RX * EW + sizeof(float) * (4 * NRX_MAX_RX + 2) * C +
-         sizeof(float) * NRX_SYMBOLS * EW * (4 * NRX_MAX_RX + 2) + sizeof(float) * NRX_SYMBOLS * EW * C;
+  constexpr int F_MAX = 4 * NRX_MAX_RX + 2;
+  return sizeof(float2) * 2 * NRX_MAX_RX * EW + sizeof(float) * (F_MAX * C + 9 * C) +
+         sizeof(float) * NRX_SYMBOLS * EW * F_MAX + sizeof(float) * NRX_SYMBOLS * EW * C;
 }
 
 template <typename OutT>
@@ -122,6 +171,8 @@ template cudaError_t launch_state_init<float>(const Geometry&, const SlotTable&,
 template cudaError_t launch_state_init<__nv_bfloat16>(const Geometry&, const SlotTable&, const float2*,
                                                       const float*, const float*, const float*, __nv_bfloat16*,
                                                       cudaStream_t);
+template cudaError_t launch_state_init<__half>(const Geometry&, const SlotTable&, const float2*, const float*,
+                                               const float*, const float*, __half*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // LS + LMMSE + max-log.  Per data RE: H = interpolated LS estimates [B x U],

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -17,6 +18,10 @@ __device__ __forceinline__ float store_cast<float>(float v) {
 template <>
 __device__ __forceinline__ __nv_bfloat16 store_cast<__nv_bfloat16>(float v) {
   return __float2bfloat16_rn(v);
+}
+template <>
+__device__ __forceinline__ __half store_cast<__half>(float v) {
+  return __float2half_rn(v);
 }
 
 // Weights of one CGNN iteration on the device (FP32 path: dense layers stored

@@ -1,0 +1,850 @@
+// Tensor-core kernels of the CGNN iterations and the LLR read-out (Sec.
+// II-A).  Every 1x1 / MLP layer is a 128 x 64 x 64 tcgen05 MMA (16-bit
+// operands in shared memory, FP32 accumulators in TMEM); depthwise taps,
+// biases, ReLU, the cross-user aggregation and residual adds run on the CUDA
+// cores in FP32.  Activations are stored in the operand type T (FP16 or BF16)
+// as [slot][user][symbol][subcarrier][64].  With BF16 the weights are split
+// into hi + lo images and each layer is two MMA passes (see net_tc.h).
+//
+// All kernels are persistent (grid = min(tiles, SMs x CTAs/SM)), load their
+// weights into shared memory once, and wait for MMA completion on an mbarrier
+// with a bounded wait: on timeout they set the context's error word, wait once
+// more for their own MMAs, release TMEM and return.
+#include <cstring>
+#include <vector>
+
+#include "net_tc.h"
+#include "tc.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int C64 = 64;
+// Operand traits: MMA input format code, split weights, bf16x2 / f16x2 packing.
+template <typename T>
+struct Op;
+template <>
+struct Op<__nv_bfloat16> {
+  static constexpr uint32_t fmt = 1;
+  static constexpr bool split = true;
+  __device__ static __forceinline__ uint32_t pack(float a, float b) { return tc::pack_bf16x2(a, b); }
+  __device__ static __forceinline__ float2 unpack(uint32_t w) { return tc::unpack_bf16x2(w); }
+};
+template <>
+struct Op<__half> {
+  static constexpr uint32_t fmt = 0;
+  static constexpr bool split = false;
+  __device__ static __forceinline__ uint32_t pack(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  __device__ static __forceinline__ float2 unpack(uint32_t w) {
+    return __half22float2(*reinterpret_cast<__half2*>(&w));
+  }
+};
+template <typename T>
+constexpr uint32_t idesc() {
+  return (1u << 4) | (Op<T>::fmt << 7) | (Op<T>::fmt << 10) | ((uint32_t)(64 >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
+}
+// Bytes of one packed weight matrix in shared memory (hi [+ lo]).
+template <typename T>
+constexpr int wbytes() {
+  return Op<T>::split ? 2 * 8192 : 8192;
+}
+
+// D (+)= A W^T for a 64 x 64 weight matrix at w_saddr (hi, then lo if split).
+template <typename T>
+__device__ __forceinline__ void gemm64(uint32_t d_tmem, uint32_t a_saddr, uint32_t w_saddr, bool accumulate_first) {
+  tc::mma_k64(d_tmem, a_saddr, w_saddr, idesc<T>(), accumulate_first);
+  if (Op<T>::split) tc::mma_k64(d_tmem, a_saddr, w_saddr + 8192, idesc<T>(), true);
+}
+constexpr int kTileBytes = 16384;  // 128 x 64 16-bit operand tile
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+__device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
+  const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023);
+  return reinterpret_cast<unsigned char*>(a);
+}
+
+// Copy a pre-packed weight matrix (wbytes<T>() bytes) into shared memory.
+template <typename T>
+__device__ __forceinline__ void load_wtile(unsigned char* dst, const uint4* __restrict__ src) {
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  for (int i = threadIdx.x; i < wbytes<T>() / 16; i += blockDim.x) d[i] = __ldg(src + i);
+}
+
+template <typename T>
+__device__ __forceinline__ uint4 pack8(const float* v) {
+  return make_uint4(Op<T>::pack(v[0], v[1]), Op<T>::pack(v[2], v[3]), Op<T>::pack(v[4], v[5]),
+                    Op<T>::pack(v[6], v[7]));
+}
+
+// Store 64 FP32 values of one row into a SW128 operand tile.
+template <typename T>
+__device__ __forceinline__ void store_row_sw128(unsigned char* tile, int r, const float (&v)[64]) {
+#pragma unroll
+  for (int ch = 0; ch < 8; ++ch)
+    *reinterpret_cast<uint4*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((ch ^ (r & 7)) << 4)) = pack8<T>(v + ch * 8);
+}
+
+// Store 64 FP32 values as one 128-byte row to global memory.
+template <typename T>
+__device__ __forceinline__ void store_row_global(T* dst, const float (&v)[64]) {
+  uint4* d = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+  for (int ch = 0; ch < 8; ++ch) d[ch] = pack8<T>(v + ch * 8);
+}
+
+// Common prologue / epilogue of the persistent kernels.
+struct TcCta {
+  uint64_t* bar;
+  uint32_t* slot;
+  uint32_t tmem;
+  uint32_t phase;
+};
+
+__device__ __forceinline__ void tc_setup(TcCta& c, uint64_t* bar, uint32_t* slot, uint32_t ncols) {
+  c.bar = bar;
+  c.slot = slot;
+  c.phase = 0;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(bar, 1);
+    tc::fence_mbar_init();
+  }
+  if (threadIdx.x < 32) tc::tmem_alloc(slot, ncols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  c.tmem = *slot;
+}
+
+// Wait for the next MMA commit.  Returns false (for every thread) on timeout,
+// after recording it in *err.
+__device__ __forceinline__ bool tc_wait(TcCta& c, int* err) {
+  // one thread polls; the CTA barrier then orders everyone after the MMAs
+  bool ok = true;
+  if (threadIdx.x == 0) ok = tc::mbar_wait(c.bar, c.phase & 1);
+  c.phase++;
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return false;
+  }
+  tc::tc_fence_after();
+  return true;
+}
+
+__device__ __forceinline__ void tc_teardown(TcCta& c, uint32_t ncols, bool timed_out) {
+  if (timed_out && threadIdx.x == 0) tc::mbar_wait(c.bar, (c.phase - 1) & 1, 100000000ull);  // let in-flight MMAs land
+  tc::tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(c.tmem, ncols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Message passing + CNN-update input layer.  One M tile = 128 rows =
+// `nre` REs x U users (row = u * nre + j).
+//   GEMM1: h = ReLU(S W1^T + b1)            -> TMEM cols [0, 64)
+//   GEMM2: m = h W2^T + b2                  -> TMEM cols [64, 128)
+//   a_u = sum_{v != u} m_v (FP32, through shared memory, two halves of 32 ch)
+//   GEMM3: z = S Win_S^T + a Win_a^T + b + PE Win_pe^T -> TMEM cols [128, 192)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct MpLayout {
+  static constexpr int A_S = 0;
+  static constexpr int A_A = 16384;
+  static constexpr int A_H = 32768;  // also the FP32 exchange buffer (128 x 32 floats)
+  static constexpr int W1 = 49152;
+  static constexpr int W2 = W1 + wbytes<T>();
+  static constexpr int WS = W2 + wbytes<T>();
+  static constexpr int WA = WS + wbytes<T>();
+  static constexpr int VEC = WA + wbytes<T>();  // b1, b2, bin, pe_t, pe_f: 5 x 64 floats
+  static constexpr int BAR = VEC + 5 * 64 * 4;
+  static constexpr int TOTAL = BAR + 16;
+  static constexpr int DYN = TOTAL + 1024;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC w, const T* __restrict__ state,
+                                                       T* __restrict__ z, int nre, int tiles_per_slot) {
+  using MpL = MpLayout<T>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = align1024(smem_raw);
+  float* vec = reinterpret_cast<float*>(sm + MpL::VEC);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  load_wtile<T>(sm + MpL::W1, w.mp1);
+  load_wtile<T>(sm + MpL::W2, w.mp2);
+  load_wtile<T>(sm + MpL::WS, w.in_s);
+  load_wtile<T>(sm + MpL::WA, w.in_a);
+  for (int i = tid; i < 64; i += kThreads) {
+    vec[i] = __ldg(w.mp1_b + i);
+    vec[64 + i] = __ldg(w.mp2_b + i);
+    vec[128 + i] = __ldg(w.in_b + i);
+    vec[192 + i] = __ldg(w.in_pe + i);
+    vec[256 + i] = __ldg(w.in_pe + 64 + i);
+  }
+  TcCta c;
+  tc_setup(c, reinterpret_cast<uint64_t*>(sm + MpL::BAR), reinterpret_cast<uint32_t*>(sm + MpL::BAR + 8),
+           256);
+  const uint32_t sa_s = tc::smem_u32(sm + MpL::A_S), sa_a = tc::smem_u32(sm + MpL::A_A),
+                 sa_h = tc::smem_u32(sm + MpL::A_H);
+  const uint32_t sw1 = tc::smem_u32(sm + MpL::W1), sw2 = tc::smem_u32(sm + MpL::W2),
+                 sws = tc::smem_u32(sm + MpL::WS), swa = tc::smem_u32(sm + MpL::WA);
+  const int U = g.U, S = g.S;
+  const int n_re = NRX_SYMBOLS * S;
+  const int n_tiles = g.n_slots * tiles_per_slot;
+  const int q = warp & 3;  // TMEM lane quarter of this warp
+  const int r = q * 32 + lane;  // the row this thread's epilogue owns (warps 0-3)
+  bool timed_out = false;
+  float* xchg = reinterpret_cast<float*>(sm + MpL::A_H);
+
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int sl = tile / tiles_per_slot;
+    const int re0 = (tile % tiles_per_slot) * nre;
+    // S rows -> A_S (SW128), zero for rows beyond the users / REs.
+    {
+      uint4 v[4];
+#pragma unroll
+      for (int it = 0; it < 4; ++it) {
+        const int i = tid + it * kThreads;
+        const int row = i >> 3, ch = i & 7;
+        const int u = row / nre, j = row % nre, re = re0 + j;
+        v[it] = make_uint4(0, 0, 0, 0);
+        if (u < U && re < n_re)
+          v[it] = __ldg(reinterpret_cast<const uint4*>(state + (((size_t)sl * U + u) * n_re + re) * C64) + ch);
+      }
+#pragma unroll
+      for (int it = 0; it < 4; ++it) {
+        const int i = tid + it * kThreads;
+        const int row = i >> 3, ch = i & 7;
+        *reinterpret_cast<uint4*>(sm + MpL::A_S + (row >> 3) * 1024 + (row & 7) * 128 + ((ch ^ (row & 7)) << 4)) =
+            v[it];
+      }
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::tc_fence_after();
+      gemm64<T>(c.tmem, sa_s, sw1, false);
+      tc::mma_commit(c.bar);
+    }
+    if (!tc_wait(c, w.err)) {
+      timed_out = true;
+      break;
+    }
+    // h = ReLU(acc + b1) -> A_H
+    if (warp < 4) {
+      float v[64];
+      tc::tmem_row64(c.tmem + ((uint32_t)(q * 32) << 16), v);
+#pragma unroll
+      for (int k = 0; k < 64; ++k) v[k] = fmaxf(v[k] + vec[k], 0.f);
+      store_row_sw128<T>(sm + MpL::A_H, r, v);
+    }
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc::tc_fence_after();
+      gemm64<T>(c.tmem + 64, sa_h, sw2, false);
+      tc::mma_commit(c.bar);
+    }
+    if (!tc_wait(c, w.err)) {
+      timed_out = true;
+      break;
+    }
+    // m = acc + b2; a_u = sum_{v != u} m_v, exchanged in two halves of 32 channels.
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      __syncthreads();  // previous readers of the exchange buffer are done
+      // exchange row r: 8 chunks of 4 floats, chunk k stored at position k ^ (r & 7)
+      if (warp < 4) {
+        uint32_t ma[16], mb[16];
+        const uint32_t ta = c.tmem + 64 + half * 32 + ((uint32_t)(q * 32) << 16);
+        tc::tmem_ld16(ta, ma);
+        tc::tmem_ld16(ta + 16, mb);
+        tc::tmem_wait16(ma);
+        tc::tmem_wait16(mb);
+        const float* b2 = vec + 64 + half * 32;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const uint32_t* src = k < 4 ? ma + 4 * k : mb + 4 * (k - 4);
+          *reinterpret_cast<float4*>(xchg + r * 32 + ((k ^ (r & 7)) << 2)) =
+              make_float4(__uint_as_float(src[0]) + b2[4 * k], __uint_as_float(src[1]) + b2[4 * k + 1],
+                          __uint_as_float(src[2]) + b2[4 * k + 2], __uint_as_float(src[3]) + b2[4 * k + 3]);
+        }
+      }
+      __syncthreads();
+      for (int i = tid; i < nre * 16; i += kThreads) {
+        const int j = i >> 4, cp = i & 15;
+        float2 mv[NRX_MAX_USERS];
+#pragma unroll
+        for (int u = 0; u < NRX_MAX_USERS; ++u) {
+          const int rw = u * nre + j;
+          mv[u] = u < U ? *reinterpret_cast<const float2*>(xchg + rw * 32 + (((cp >> 1) ^ (rw & 7)) << 2) + (cp & 1) * 2)
+                        : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < NRX_MAX_USERS; ++u) {
+          if (u >= U) break;
+          float ax = 0.f, ay = 0.f;
+#pragma unroll
+          for (int v = 0; v < NRX_MAX_USERS; ++v)
+            if (v != u && v < U) {
+              ax += mv[v].x;
+              ay += mv[v].y;
+            }
+          const int row = u * nre + j;
+          *reinterpret_cast<uint32_t*>(sm + MpL::A_A + tc::sw128_offset(row, half * 32 + 2 * cp)) =
+              Op<T>::pack(ax, ay);
+        }
+      }
+    }
+    // rows of the A_A tile not covered by (u < U, j < nre) are never read back
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc::tc_fence_after();
+      gemm64<T>(c.tmem + 128, sa_s, sws, false);
+      gemm64<T>(c.tmem + 128, sa_a, swa, true);
+      tc::mma_commit(c.bar);
+    }
+    if (!tc_wait(c, w.err)) {
+      timed_out = true;
+      break;
+    }
+    if (warp < 4) {
+      const int u = r / nre, j = r % nre, re = re0 + j;
+      float v[64];
+      tc::tmem_row64(c.tmem + 128 + ((uint32_t)(q * 32) << 16), v);
+      if (u < U && re < n_re) {
+        const int t = re / S, s = re % S;
+        const float pt = pe_time(g, t), pf = pe_freq(u, s);
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] = v[k] + vec[128 + k] + pt * vec[192 + k] + pf * vec[256 + k];
+        store_row_global<T>(z + (((size_t)sl * U + u) * n_re + re) * C64, v);
+      }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+  }
+  tc_teardown(c, 256, timed_out);
+}
+
+// ---------------------------------------------------------------------------
+// One residual block on a tile of TW = 14 subcarriers x 14 symbols of one
+// (slot, user), input halo 2.  Operand rows are column-major with 16 rows per
+// column, row = column * 16 + t (rows t = 14, 15 are padding, always zero):
+//   DW1 (CUDA cores, packed FP32) on 16 columns -> A (256 rows, 2 M tiles)
+//   PW1 MMA -> TMEM [0,128); epilogue +b1, ReLU, zero outside the grid -> P1
+//   DW2 + ReLU on 14 columns -> A (224 rows)
+//   PW2 MMA -> TMEM [128,256); epilogue +b2 + residual -> z_out, or S += (last)
+// P1 [t][16 columns][64 ch] stores 16-byte chunk k of a row at k ^ (t & 7).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct BlkLayout {
+  static constexpr int TW = 14;
+  static constexpr int IW = TW + 4;  // input columns
+  static constexpr int MW = TW + 2;  // DW1 / PW1 columns
+  static constexpr int A = 0;        // 2 x 16 KB
+  static constexpr int W1 = 32768;
+  static constexpr int W2 = W1 + wbytes<T>();
+  static constexpr int ZB = W2 + wbytes<T>();  // [14][IW][64] input tile; later P1 [14][MW][64]
+  static constexpr int K1 = ZB + NRX_SYMBOLS * IW * 128;
+  static constexpr int K2 = K1 + 64 * 9 * 4;
+  static constexpr int B1 = K2 + 64 * 9 * 4;
+  static constexpr int B2 = B1 + 256;
+  static constexpr int BAR = B2 + 256;
+  static constexpr int TOTAL = BAR + 16;
+  static constexpr int DYN = TOTAL + 1024;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint4* __restrict__ w1p,
+                                                           const uint4* __restrict__ w2p,
+                                                           const float* __restrict__ b1,
+                                                           const float* __restrict__ b2,
+                                                           const float* __restrict__ k1g,
+                                                           const float* __restrict__ k2g,
+                                                           const T* __restrict__ z_in, T* __restrict__ z_out,
+                                                           T* __restrict__ state, int last, int* err) {
+  using L = BlkLayout<T>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = align1024(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  load_wtile<T>(sm + L::W1, w1p);
+  load_wtile<T>(sm + L::W2, w2p);
+  float* sk1 = reinterpret_cast<float*>(sm + L::K1);
+  float* sk2 = reinterpret_cast<float*>(sm + L::K2);
+  float* sb1 = reinterpret_cast<float*>(sm + L::B1);
+  float* sb2 = reinterpret_cast<float*>(sm + L::B2);
+  for (int i = tid; i < 64 * 9; i += kThreads) {
+    sk1[i] = __ldg(k1g + i);
+    sk2[i] = __ldg(k2g + i);
+  }
+  for (int i = tid; i < 64; i += kThreads) {
+    sb1[i] = __ldg(b1 + i);
+    sb2[i] = __ldg(b2 + i);
+  }
+  // zero the A tiles once: padding rows (t = 14, 15) are never written
+  for (int i = tid; i < 2 * kTileBytes / 16; i += kThreads) reinterpret_cast<uint4*>(sm + L::A)[i] = make_uint4(0, 0, 0, 0);
+  TcCta c;
+  tc_setup(c, reinterpret_cast<uint64_t*>(sm + L::BAR), reinterpret_cast<uint32_t*>(sm + L::BAR + 8), 256);
+  // this thread's channel pair (2 cp, 2 cp + 1) for the depthwise phases; its taps
+  // are read from shared memory at the start of each phase (short live range)
+  const int cp = lane, cg = warp;
+  const uint32_t sa = tc::smem_u32(sm + L::A), sw1 = tc::smem_u32(sm + L::W1), sw2 = tc::smem_u32(sm + L::W2);
+  const int U = g.U, S = g.S;
+  const int tps = (S + L::TW - 1) / L::TW;
+  const int n_tiles = g.n_slots * U * tps;
+  const int q = warp & 3, mt = warp >> 2;
+  const int row = mt * 128 + q * 32 + lane;  // epilogue row of this thread: column row>>4, symbol row&15
+  const int rcol = row >> 4, rt = row & 15;
+  const uint32_t* zw = reinterpret_cast<const uint32_t*>(sm + L::ZB);
+  unsigned char* const a_tile = sm + L::A;
+  const int cpc = cp >> 2, cpl = cp & 3;  // 16-byte chunk and word within it of this channel pair
+  bool timed_out = false;
+
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int su = tile / tps;  // slot * U + user
+    const int s0 = (tile % tps) * L::TW;
+    const size_t base = (size_t)su * NRX_SYMBOLS * S;
+    // input tile with a two-subcarrier halo, zero outside the grid (all loads
+    // of a thread issued before its stores)
+    {
+      constexpr int kN = NRX_SYMBOLS * L::IW * 8;
+      constexpr int kIt = (kN + kThreads - 1) / kThreads;
+      uint4 v[kIt];
+#pragma unroll
+      for (int it = 0; it < kIt; ++it) {
+        const int i = tid + it * kThreads;
+        const int ch = i & 7, re = i >> 3;
+        const int t = re / L::IW, e = re % L::IW, s = s0 - 2 + e;
+        v[it] = make_uint4(0, 0, 0, 0);
+        if (i < kN && s >= 0 && s < S)
+          v[it] = __ldg(reinterpret_cast<const uint4*>(z_in + (base + (size_t)t * S + s) * C64) + ch);
+      }
+#pragma unroll
+      for (int it = 0; it < kIt; ++it) {
+        const int i = tid + it * kThreads;
+        if (i < kN) reinterpret_cast<uint4*>(sm + L::ZB)[i] = v[it];
+      }
+    }
+    __syncthreads();
+    // DW1: output column e (s = s0-1+e) reads input columns e, e+1, e+2.
+    float2 k1[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) k1[i] = make_float2(sk1[(2 * cp) * 9 + i], sk1[(2 * cp + 1) * 9 + i]);
+    for (int e = cg; e < L::MW; e += 8) {
+      const uint32_t* col = zw + e * 32 + cp;
+      unsigned char* dst = a_tile + e * 2048;
+      tc::dw_column(
+          k1, [&](int ti, int k) { return Op<T>::unpack(col[(ti * L::IW + k) * 32]); },
+          [&](int t, float2 v) {
+            *reinterpret_cast<uint32_t*>(dst + (t >> 3) * 1024 + (t & 7) * 128 + ((cpc ^ (t & 7)) << 4) + cpl * 4) =
+                Op<T>::pack(v.x, v.y);
+          });
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::tc_fence_after();
+      gemm64<T>(c.tmem, sa, sw1, false);
+      gemm64<T>(c.tmem + 64, sa + kTileBytes, sw1, false);
+      tc::mma_commit(c.bar);
+    }
+    if (!tc_wait(c, err)) {
+      timed_out = true;
+      break;
+    }
+    // PW1 epilogue -> P1 (over the input tile, which DW1 no longer needs)
+    {
+      float v[64];
+      tc::tmem_row64(c.tmem + mt * 64 + ((uint32_t)(q * 32) << 16), v);
+      const int s = s0 - 1 + rcol;
+      const bool inside = s >= 0 && s < S;
+      if (rt < NRX_SYMBOLS) {
+        uint4* dst = reinterpret_cast<uint4*>(sm + L::ZB + (rt * L::MW + rcol) * 128);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          float f[8];
+#pragma unroll
+          for (int z8 = 0; z8 < 8; ++z8) f[z8] = inside ? fmaxf(v[k * 8 + z8] + sb1[k * 8 + z8], 0.f) : 0.f;
+          dst[k ^ (rt & 7)] = pack8<T>(f);
+        }
+      }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    // DW2 + ReLU: output column x (s = s0+x) reads P1 columns x, x+1, x+2.
+    float2 k2[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) k2[i] = make_float2(sk2[(2 * cp) * 9 + i], sk2[(2 * cp + 1) * 9 + i]);
+    for (int x = cg; x < L::TW; x += 8) {
+      const uint32_t* col = zw + x * 32 + cpl;
+      unsigned char* dst = a_tile + x * 2048;
+      tc::dw_column(
+          k2, [&](int ti, int k) { return Op<T>::unpack(col[(ti * L::MW + k) * 32 + ((cpc ^ (ti & 7)) << 2)]); },
+          [&](int t, float2 v) {
+            *reinterpret_cast<uint32_t*>(dst + (t >> 3) * 1024 + (t & 7) * 128 + ((cpc ^ (t & 7)) << 4) + cpl * 4) =
+                Op<T>::pack(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f));
+          });
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::tc_fence_after();
+      gemm64<T>(c.tmem + 128, sa, sw2, false);
+      gemm64<T>(c.tmem + 192, sa + kTileBytes, sw2, false);
+      tc::mma_commit(c.bar);
+    }
+    if (!tc_wait(c, err)) {
+      timed_out = true;
+      break;
+    }
+    {
+      float v[64];
+      tc::tmem_row64(c.tmem + 128 + mt * 64 + ((uint32_t)(q * 32) << 16), v);
+      const int s = s0 + rcol;
+      if (rt < NRX_SYMBOLS && rcol < L::TW && s < S) {
+        const size_t off = (base + (size_t)rt * S + s) * C64;
+        const uint4* res = reinterpret_cast<const uint4*>(z_in + off);
+        uint4* dst = reinterpret_cast<uint4*>((last ? state : z_out) + off);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // two halves of 4 chunks: loads batched, registers bounded
+        uint4 rq[4], sq[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) rq[j] = __ldg(res + 4 * h + j);
+        if (last) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) sq[j] = dst[4 * h + j];  // plain load: this kernel writes the state
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int ch = 4 * h + j;
+          float o[8];
+          const uint32_t rw[4] = {rq[j].x, rq[j].y, rq[j].z, rq[j].w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float2 f = Op<T>::unpack(rw[k]);
+            o[2 * k] = v[ch * 8 + 2 * k] + sb2[ch * 8 + 2 * k] + f.x;
+            o[2 * k + 1] = v[ch * 8 + 2 * k + 1] + sb2[ch * 8 + 2 * k + 1] + f.y;
+          }
+          if (last) {
+            const uint32_t sw[4] = {sq[j].x, sq[j].y, sq[j].z, sq[j].w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float2 f = Op<T>::unpack(sw[k]);
+              o[2 * k] += f.x;
+              o[2 * k + 1] += f.y;
+            }
+          }
+          dst[ch] = pack8<T>(o);
+        }
+        }
+      }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+  }
+  tc_teardown(c, 256, timed_out);
+}
+
+// ---------------------------------------------------------------------------
+// ReadoutLLRs + masking: 128 data REs of one (slot, user) per tile;
+// h = ReLU(S W_o1^T + b) by MMA, then the m_u outputs on the CUDA cores.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct RoLayout {
+  static constexpr int A = 0;
+  static constexpr int W1 = kTileBytes;
+  static constexpr int W2F = W1 + wbytes<T>();  // [8][64] FP32
+  static constexpr int B1 = W2F + 8 * 64 * 4;
+  static constexpr int B2 = B1 + 256;
+  static constexpr int BAR = B2 + 64;
+  static constexpr int TOTAL = BAR + 16;
+  static constexpr int DYN = TOTAL + 1024;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, ReadoutWeightsTC w,
+                                                    const T* __restrict__ state, float* __restrict__ llr,
+                                                    int tiles_per_su) {
+  using L = RoLayout<T>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = align1024(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  load_wtile<T>(sm + L::W1, w.ro1);
+  float* w2 = reinterpret_cast<float*>(sm + L::W2F);
+  float* sb1 = reinterpret_cast<float*>(sm + L::B1);
+  float* sb2 = reinterpret_cast<float*>(sm + L::B2);
+  for (int i = tid; i < g.m_max * 64; i += blockDim.x) w2[i] = __ldg(w.ro2 + i);
+  for (int i = tid; i < 64; i += blockDim.x) sb1[i] = __ldg(w.ro1_b + i);
+  for (int i = tid; i < g.m_max; i += blockDim.x) sb2[i] = __ldg(w.ro2_b + i);
+  TcCta c;
+  tc_setup(c, reinterpret_cast<uint64_t*>(sm + L::BAR), reinterpret_cast<uint32_t*>(sm + L::BAR + 8), 64);
+  const uint32_t sa = tc::smem_u32(sm + L::A), sw1 = tc::smem_u32(sm + L::W1);
+  const int U = g.U, S = g.S;
+  const int n_tiles = g.n_slots * U * tiles_per_su;
+  const int row = warp * 32 + lane;
+  bool timed_out = false;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int su = tile / tiles_per_su, sl = su / U, u = su % U;
+    const int r0 = (tile % tiles_per_su) * 128;
+    const size_t base = (size_t)su * NRX_SYMBOLS * S;
+    {
+      uint4 v[8];
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int i = tid + it * 128;
+        const int rw = i >> 3, ch = i & 7, rd = r0 + rw;
+        v[it] = make_uint4(0, 0, 0, 0);
+        if (rd < g.n_data) {
+          const int t = g.data_t[rd / S], s = rd % S;
+          v[it] = __ldg(reinterpret_cast<const uint4*>(state + (base + (size_t)t * S + s) * C64) + ch);
+        }
+      }
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int i = tid + it * 128;
+        const int rw = i >> 3, ch = i & 7;
+        *reinterpret_cast<uint4*>(sm + L::A + (rw >> 3) * 1024 + (rw & 7) * 128 + ((ch ^ (rw & 7)) << 4)) = v[it];
+      }
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::tc_fence_after();
+      gemm64<T>(c.tmem, sa, sw1, false);
+      tc::mma_commit(c.bar);
+    }
+    if (!tc_wait(c, w.err)) {
+      timed_out = true;
+      break;
+    }
+    float h[64];
+    tc::tmem_row64(c.tmem + ((uint32_t)(warp * 32) << 16), h);
+    const int rd = r0 + row;
+    if (rd < g.n_data) {
+#pragma unroll
+      for (int k = 0; k < 64; ++k) h[k] = fmaxf(h[k] + sb1[k], 0.f);
+      const int m = tab.bits[sl][u];
+      float* dst = llr + tab.llr_off[sl][u] + (size_t)rd * m;
+      for (int o = 0; o < m; ++o) {
+        float a = sb2[o];
+#pragma unroll
+        for (int k = 0; k < 64; ++k) a = fmaf(w2[o * 64 + k], h[k], a);
+        dst[o] = a;
+      }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+  }
+  tc_teardown(c, 64, timed_out);
+}
+
+template <typename T>
+__global__ void k_to_f32(const T* __restrict__ in, float* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+template <typename K>
+void set_smem(K kernel, int bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+uint16_t f32_to_bf16_rn(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+float bf16_to_f32(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+
+// Pack M[n][k] (64 x 64 FP32, row-major) into the SW128 K-major image.
+void pack_sw128(const float* M, unsigned char* dst, bool bf16) {
+  for (int n = 0; n < 64; ++n)
+    for (int k = 0; k < 64; ++k) {
+      const float v = M[n * 64 + k];
+      uint16_t b;
+      if (bf16) {
+        b = f32_to_bf16_rn(v);
+      } else {
+        __half h = __float2half_rn(v);
+        memcpy(&b, &h, 2);
+      }
+      const size_t off = (size_t)(n >> 3) * 1024 + (n & 7) * 128 + (((k >> 3) ^ (n & 7)) << 4) + ((k & 7) << 1);
+      memcpy(dst + off, &b, 2);
+    }
+}
+
+// One weight matrix W[n][col0 .. col0+63] (row stride ld) -> packed image(s):
+// FP16: one image; BF16: hi image then lo = bf16(W - hi) image.
+void pack_weight(const float* W, int ld, int col0, unsigned char* dst, bool bf16) {
+  float m[64 * 64];
+  for (int n = 0; n < 64; ++n)
+    for (int k = 0; k < 64; ++k) m[n * 64 + k] = W[(size_t)n * ld + col0 + k];
+  pack_sw128(m, dst, bf16);
+  if (bf16) {
+    float lo[64 * 64];
+    for (int i = 0; i < 64 * 64; ++i) lo[i] = m[i] - bf16_to_f32(f32_to_bf16_rn(m[i]));
+    pack_sw128(lo, dst + 8192, true);
+  }
+}
+
+// Persistent grid: CTAs per SM from shared memory (228 KB per SM, 1 KB reserved
+// per CTA), capped by `max_per_sm` (registers / TMEM columns).
+int grid_for(int smem, int max_per_sm, int tiles) {
+  int occ = (228 * 1024) / (smem + 1024);
+  if (occ > max_per_sm) occ = max_per_sm;
+  if (occ < 1) occ = 1;
+  const int g = occ * num_sms();
+  return tiles < g ? tiles : g;
+}
+
+}  // namespace
+
+nrx_status upload_tc_weights(bool bf16, int C, int R, int N_it, const std::vector<const float*>& blob_it,
+                             const float* ro1w, const std::vector<IterWeightsF32>& it32, const float* ro1_b_dev,
+                             const float* ro2_dev, const float* ro2_b_dev, std::vector<IterWeightsTC>* out,
+                             void** dev_alloc, ReadoutWeightsTC* ro, int** err_word) {
+  if (C != 64) return NRX_EUNSUPPORTED;
+  const size_t wb = bf16 ? 2 * 8192 : 8192;
+  const int per_it = 4 + 2 * R;
+  const size_t n_mats = (size_t)N_it * per_it + 1;
+  std::vector<unsigned char> host(n_mats * wb + 256, 0);
+  size_t t = 0;
+  const size_t per_blob = 6 + 6 * R;
+  for (int k = 0; k < N_it; ++k) {
+    const float* const* b = blob_it.data() + k * per_blob;
+    pack_weight(b[0], C, 0, host.data() + (t++) * wb, bf16);           // mp1
+    pack_weight(b[2], C, 0, host.data() + (t++) * wb, bf16);           // mp2
+    pack_weight(b[4], 2 * C + 2, 0, host.data() + (t++) * wb, bf16);  // in, S columns
+    pack_weight(b[4], 2 * C + 2, C, host.data() + (t++) * wb, bf16);  // in, aggregate columns
+    for (int r = 0; r < R; ++r) {
+      const float* const* blk = b + 6 + 6 * r;
+      pack_weight(blk[1], C, 0, host.data() + (t++) * wb, bf16);  // pw1
+      pack_weight(blk[4], C, 0, host.data() + (t++) * wb, bf16);  // pw2
+    }
+  }
+  pack_weight(ro1w, C, 0, host.data() + (t++) * wb, bf16);
+  void* d = nullptr;
+  if (cudaMalloc(&d, host.size()) != cudaSuccess) {
+    cudaGetLastError();
+    return NRX_ENOMEM;
+  }
+  if (cudaMemcpy(d, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return NRX_ECUDA;
+  }
+  *dev_alloc = d;
+  unsigned char* base = static_cast<unsigned char*>(d);
+  int* err = reinterpret_cast<int*>(base + n_mats * wb);
+  *err_word = err;
+  auto mat = [&](size_t i) { return reinterpret_cast<const uint4*>(base + i * wb); };
+  out->resize(N_it);
+  t = 0;
+  for (int k = 0; k < N_it; ++k) {
+    IterWeightsTC& w = (*out)[k];
+    memset(&w, 0, sizeof(w));
+    const IterWeightsF32& f = it32[k];
+    w.mp1 = mat(t++);
+    w.mp2 = mat(t++);
+    w.in_s = mat(t++);
+    w.in_a = mat(t++);
+    w.mp1_b = f.mp1_b;
+    w.mp2_b = f.mp2_b;
+    w.in_b = f.in_b;
+    w.in_pe = f.in_t + (size_t)2 * C * C;
+    for (int r = 0; r < R; ++r) {
+      w.pw1[r] = mat(t++);
+      w.pw2[r] = mat(t++);
+      w.pw1_b[r] = f.pw1_b[r];
+      w.pw2_b[r] = f.pw2_b[r];
+      w.dw1[r] = f.dw1[r];
+      w.dw2[r] = f.dw2[r];
+    }
+    w.err = err;
+  }
+  ro->ro1 = mat(t++);
+  ro->ro1_b = ro1_b_dev;
+  ro->ro2 = ro2_dev;
+  ro->ro2_b = ro2_b_dev;
+  ro->err = err;
+  return NRX_OK;
+}
+
+template <typename T>
+cudaError_t launch_mp_tc(const Geometry& g, const IterWeightsTC& w, const T* state, T* z, cudaStream_t st) {
+  if (g.C != 64) return cudaErrorInvalidValue;
+  const int nre = g.U == 4 ? 32 : g.U == 3 ? 40 : g.U == 2 ? 64 : 128;
+  const int tps = (NRX_SYMBOLS * g.S + nre - 1) / nre;
+  const int tiles = g.n_slots * tps;
+  const int smem = MpLayout<T>::DYN;
+  set_smem(k_mp_tc<T>, smem);
+  const int grid = grid_for(smem, 2, tiles);
+  k_mp_tc<T><<<grid, kThreads, smem, st>>>(g, w, state, z, nre, tps);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_block_tc(const Geometry& g, const IterWeightsTC& w, int r, const T* z_in, T* z_out, T* state,
+                            bool last, cudaStream_t st) {
+  if (g.C != 64) return cudaErrorInvalidValue;
+  const int tps = (g.S + BlkLayout<T>::TW - 1) / BlkLayout<T>::TW;
+  const int tiles = g.n_slots * g.U * tps;
+  const int smem = BlkLayout<T>::DYN;
+  set_smem(k_block_tc<T>, smem);
+  const int grid = grid_for(smem, 2, tiles);
+  k_block_tc<T><<<grid, kThreads, smem, st>>>(g, w.pw1[r], w.pw2[r], w.pw1_b[r], w.pw2_b[r], w.dw1[r], w.dw2[r],
+                                               z_in, z_out, state, last ? 1 : 0, w.err);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_readout_tc(const Geometry& g, const SlotTable& tab, const ReadoutWeightsTC& w, const T* state,
+                              float* llr, cudaStream_t st) {
+  if (g.C != 64) return cudaErrorInvalidValue;
+  const int tpsu = (g.n_data + 127) / 128;
+  const int tiles = g.n_slots * g.U * tpsu;
+  const int smem = RoLayout<T>::DYN;
+  set_smem(k_readout_tc<T>, smem);
+  const int grid = grid_for(smem, 4, tiles);
+  k_readout_tc<T><<<grid, 128, smem, st>>>(g, tab, w, state, llr, tpsu);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_to_f32(const T* in, float* out, size_t n, cudaStream_t st) {
+  k_to_f32<T><<<256, 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+#define NRX_INSTANTIATE(T)                                                                                     \
+  template cudaError_t launch_mp_tc<T>(const Geometry&, const IterWeightsTC&, const T*, T*, cudaStream_t);     \
+  template cudaError_t launch_block_tc<T>(const Geometry&, const IterWeightsTC&, int, const T*, T*, T*, bool,  \
+                                          cudaStream_t);                                                       \
+  template cudaError_t launch_readout_tc<T>(const Geometry&, const SlotTable&, const ReadoutWeightsTC&,        \
+                                            const T*, float*, cudaStream_t);                                   \
+  template cudaError_t launch_to_f32<T>(const T*, float*, size_t, cudaStream_t);
+NRX_INSTANTIATE(__nv_bfloat16)
+NRX_INSTANTIATE(__half)

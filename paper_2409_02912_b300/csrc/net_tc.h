@@ -1,0 +1,67 @@
+// Tensor-core (tcgen05) network kernels, FP16 or BF16 operands: weights and launchers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/nrx.h"
+#include "common.cuh"
+#include "kernels.h"
+
+// Weights of one CGNN iteration for the tensor-core path.  Dense 64x64
+// matrices are pre-packed on the host into the 8 KB K-major 128-byte-swizzle
+// shared-memory image the MMA reads ([out][in] = N x K).  With BF16 operands
+// each matrix is stored as two such images, W_hi = bf16(W) followed by
+// W_lo = bf16(W - W_hi), and multiplied as A W_hi^T + A W_lo^T (the weight
+// rounding error drops to that of a 16-bit mantissa).  Biases, depthwise taps
+// and the PE columns of the input layer stay FP32.
+struct IterWeightsTC {
+  const uint4* mp1;
+  const uint4* mp2;
+  const uint4* in_s;   // input layer, columns acting on S
+  const uint4* in_a;   // input layer, columns acting on the aggregate
+  const float* mp1_b;
+  const float* mp2_b;
+  const float* in_b;
+  const float* in_pe;  // [2][C]: columns acting on (dt, df)
+  const uint4* pw1[4];
+  const uint4* pw2[4];
+  const float* pw1_b[4];
+  const float* pw2_b[4];
+  const float* dw1[4];
+  const float* dw2[4];
+  int* err;            // device word set when a bounded wait gives up
+};
+
+struct ReadoutWeightsTC {
+  const uint4* ro1;
+  const float* ro1_b;
+  const float* ro2;    // [m_max][C] FP32
+  const float* ro2_b;
+  int* err;
+};
+
+// blob_it: per iteration {mp1w, mp1b, mp2w, mp2b, inw, inb} then per block
+// {dw1, pw1w, pw1b, dw2, pw2w, pw2b} (host pointers into the blob).  FP32
+// device tensors (biases, taps, PE columns, readout head) are taken from the
+// FP32 upload.  Only C = 64 is supported.  bf16 selects the operand type
+// (BF16 with split weights, else FP16).
+nrx_status upload_tc_weights(bool bf16, int C, int R, int N_it, const std::vector<const float*>& blob_it,
+                             const float* ro1w, const std::vector<IterWeightsF32>& it32, const float* ro1_b_dev,
+                             const float* ro2_dev, const float* ro2_b_dev, std::vector<IterWeightsTC>* out,
+                             void** dev_alloc, ReadoutWeightsTC* ro, int** err_word);
+
+// T = __nv_bfloat16 or __half (operand and activation storage type).
+template <typename T>
+cudaError_t launch_mp_tc(const Geometry& g, const IterWeightsTC& w, const T* state, T* z, cudaStream_t st);
+template <typename T>
+cudaError_t launch_block_tc(const Geometry& g, const IterWeightsTC& w, int r, const T* z_in, T* z_out, T* state,
+                            bool last, cudaStream_t st);
+template <typename T>
+cudaError_t launch_readout_tc(const Geometry& g, const SlotTable& tab, const ReadoutWeightsTC& w, const T* state,
+                              float* llr, cudaStream_t st);
+template <typename T>
+cudaError_t launch_to_f32(const T* in, float* out, size_t n, cudaStream_t st);

@@ -11,7 +11,7 @@
 #include "../../include/nrx.h"
 #include "common.cuh"
 #include "kernels.h"
-#include "net_bf16.h"
+#include "net_tc.h"
 
 namespace {
 
@@ -27,17 +27,18 @@ struct nrx_ctx {
   int device = 0;
   // device weights (one allocation per precision)
   float* w_f32 = nullptr;
-  void* w_bf16 = nullptr;
+  void* w_tc = nullptr;
   const float* init_pw_w = nullptr;
   const float* init_pw_b = nullptr;
   const float* init_dw = nullptr;
   std::vector<IterWeightsF32> it32;
-  std::vector<IterWeightsBF16> it16;
+  std::vector<IterWeightsTC> it16;
   const float* ro1_t = nullptr;
   const float* ro1_b = nullptr;
   const float* ro2 = nullptr;
   const float* ro2_b = nullptr;
-  ReadoutWeightsBF16 ro_bf16{};
+  ReadoutWeightsTC ro_tc{};
+  int* d_err = nullptr;  // device word set by a bounded wait that gave up (tensor-core path)
   // workspaces [max_slots][max_users][14][S_max][C]
   void* state = nullptr;
   void* z_a = nullptr;
@@ -186,6 +187,51 @@ nrx_status prepare(nrx_ctx* ctx, int32_t n_slots, const nrx_slot_cfg* cfgs, cons
   return NRX_OK;
 }
 
+template <typename T>
+nrx_status run_tc(nrx_ctx* ctx, const Geometry& g, const SlotTable& tab, int its, const float2* y, float* llr,
+                  cudaStream_t st, int* launches) {
+  cudaError_t e;
+  T* S = static_cast<T*>(ctx->state);
+  T* za = static_cast<T*>(ctx->z_a);
+  T* zb = static_cast<T*>(ctx->z_b);
+  {
+    KernelTimer kt(ctx, K_INIT, st);
+    e = launch_state_init<T>(g, tab, y, ctx->init_pw_w, ctx->init_pw_b, ctx->init_dw, S, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "state_init");
+  ++*launches;
+  for (int k = 0; k < its; ++k) {
+    const IterWeightsTC& w = ctx->it16[k];
+    {
+      KernelTimer kt(ctx, K_MP, st);
+      e = launch_mp_tc<T>(g, w, S, za, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "message_passing");
+    ++*launches;
+    T* zin = za;
+    T* zout = zb;
+    for (int r = 0; r < ctx->R; ++r) {
+      const bool last = r == ctx->R - 1;
+      {
+        KernelTimer kt(ctx, K_BLOCK, st);
+        e = launch_block_tc<T>(g, w, r, zin, zout, S, last, st);
+      }
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "residual_block");
+      ++*launches;
+      T* tmp = zin;
+      zin = zout;
+      zout = tmp;
+    }
+  }
+  {
+    KernelTimer kt(ctx, K_READOUT, st);
+    e = launch_readout_tc<T>(g, tab, ctx->ro_tc, S, llr, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "readout");
+  ++*launches;
+  return NRX_OK;
+}
+
 nrx_status run_nrx(nrx_ctx* ctx, const Geometry& g, const SlotTable& tab, int its, const float2* y, float* llr,
                    cudaStream_t st) {
   cudaError_t e;
@@ -229,46 +275,10 @@ nrx_status run_nrx(nrx_ctx* ctx, const Geometry& g, const SlotTable& tab, int it
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "readout_f32");
     ++launches;
+  } else if (ctx->prec == NRX_BF16) {
+    if (run_tc<__nv_bfloat16>(ctx, g, tab, its, y, llr, st, &launches) != NRX_OK) return NRX_ECUDA;
   } else {
-    using bf = __nv_bfloat16;
-    bf* S = static_cast<bf*>(ctx->state);
-    bf* za = static_cast<bf*>(ctx->z_a);
-    bf* zb = static_cast<bf*>(ctx->z_b);
-    {
-      KernelTimer kt(ctx, K_INIT, st);
-      e = launch_state_init<bf>(g, tab, y, ctx->init_pw_w, ctx->init_pw_b, ctx->init_dw, S, st);
-    }
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "state_init");
-    ++launches;
-    for (int k = 0; k < its; ++k) {
-      const IterWeightsBF16& w = ctx->it16[k];
-      {
-        KernelTimer kt(ctx, K_MP, st);
-        e = launch_mp_bf16(g, w, S, za, st);
-      }
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "mp_bf16");
-      ++launches;
-      bf* zin = za;
-      bf* zout = zb;
-      for (int r = 0; r < ctx->R; ++r) {
-        const bool last = r == ctx->R - 1;
-        {
-          KernelTimer kt(ctx, K_BLOCK, st);
-          e = launch_block_bf16(g, w, r, zin, zout, S, last, st);
-        }
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "block_bf16");
-        ++launches;
-        bf* tmp = zin;
-        zin = zout;
-        zout = tmp;
-      }
-    }
-    {
-      KernelTimer kt(ctx, K_READOUT, st);
-      e = launch_readout_bf16(g, tab, ctx->ro_bf16, S, llr, st);
-    }
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "readout_bf16");
-    ++launches;
+    if (run_tc<__half>(ctx, g, tab, its, y, llr, st, &launches) != NRX_OK) return NRX_ECUDA;
   }
   ctx->last_geo = g;
   ctx->have_state = true;
@@ -297,6 +307,23 @@ const char* nrx_status_string(nrx_status s) {
 const char* nrx_last_error(const nrx_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int32_t nrx_last_launch_count(const nrx_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+nrx_status nrx_check(nrx_ctx* ctx, void* stream) {
+  if (!ctx) return NRX_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stream");
+  if (ctx->d_err) {
+    int v = 0;
+    e = cudaMemcpy(&v, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "read device status");
+    if (v) {
+      cudaMemset(ctx->d_err, 0, sizeof(int));
+      return fail(ctx, NRX_ETIMEDOUT, "a kernel's bounded wait for its tensor-core work gave up");
+    }
+  }
+  return NRX_OK;
+}
 
 nrx_status nrx_profile(nrx_ctx* ctx, int32_t enable) {
   if (!ctx) return NRX_EINVAL;
@@ -357,7 +384,7 @@ void nrx_destroy(nrx_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   cudaFree(ctx->w_f32);
-  cudaFree(ctx->w_bf16);
+  cudaFree(ctx->w_tc);
   cudaFree(ctx->state);
   cudaFree(ctx->z_a);
   cudaFree(ctx->z_b);
@@ -380,7 +407,7 @@ nrx_status nrx_create(const void* weights, size_t weights_bytes, int32_t num_rx_
   if ((num_rx_ant != 1 && num_rx_ant != 2 && num_rx_ant != 4 && num_rx_ant != 8) || max_users < 1 || max_users > NRX_MAX_USERS || max_prb < 1 ||
       max_prb > 275 || max_slots < 1 || max_slots > NRX_MAX_LAUNCH_SLOTS)
     return NRX_EINVAL;
-  if (precision != NRX_FP32 && precision != NRX_BF16) return NRX_EINVAL;
+  if (precision != NRX_FP32 && precision != NRX_BF16 && precision != NRX_FP16) return NRX_EINVAL;
   int32_t hdr[8];
   memcpy(hdr, weights, sizeof(hdr));
   const int B = hdr[2], C = hdr[3], R = hdr[4], N_it = hdr[5], m_max = hdr[6];
@@ -515,9 +542,9 @@ nrx_status nrx_create(const void* weights, size_t weights_bytes, int32_t num_rx_
       w.pw2_b[r] = W + o.f[fi++];
     }
   }
-  if (precision == NRX_BF16) {
-    nrx_status st = upload_bf16_weights(C, R, N_it, m_max, blob_it, ro1w, ro1b, ro2w, ro2b, ctx->it32,
-                                        &ctx->it16, &ctx->w_bf16, &ctx->ro_bf16);
+  if (precision != NRX_FP32) {
+    nrx_status st = upload_tc_weights(precision == NRX_BF16, C, R, N_it, blob_it, ro1w, ctx->it32, ctx->ro1_b,
+                                      ctx->ro2, ctx->ro2_b, &ctx->it16, &ctx->w_tc, &ctx->ro_tc, &ctx->d_err);
     if (st != NRX_OK) {
       nrx_destroy(ctx);
       return st;
@@ -632,7 +659,10 @@ nrx_status nrx_copy_state(nrx_ctx* ctx, int32_t slot, float* out, void* stream) 
     e = cudaMemcpyAsync(out, static_cast<float*>(ctx->state) + slot * n, n * sizeof(float), cudaMemcpyDeviceToDevice,
                         s);
   } else {
-    e = launch_bf16_to_f32(static_cast<const __nv_bfloat16*>(ctx->state) + slot * n, out, n, s);
+    if (ctx->prec == NRX_BF16)
+      e = launch_to_f32<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(ctx->state) + slot * n, out, n, s);
+    else
+      e = launch_to_f32<__half>(static_cast<const __half*>(ctx->state) + slot * n, out, n, s);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "copy state");
   return NRX_OK;

@@ -16,13 +16,14 @@ import numpy as np
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libnrx.so")
 
 NRX_OK, NRX_EINVAL, NRX_ENOMEM, NRX_ECUDA, NRX_ETIMEDOUT, NRX_EUNSUPPORTED = range(6)
-NRX_FP32, NRX_BF16 = 0, 1
-PRECISIONS = {"fp32": NRX_FP32, "bf16": NRX_BF16}
+NRX_FP32, NRX_BF16, NRX_FP16 = 0, 1, 2
+PRECISIONS = {"fp32": NRX_FP32, "bf16": NRX_BF16, "fp16": NRX_FP16}
 
 EXPORTED = (
     "nrx_create", "nrx_destroy", "nrx_llr_count", "nrx_detect_batch", "nrx_detect", "lmmse_detect_batch",
     "lmmse_detect", "nrx_detect_batch_host", "nrx_copy_state", "nrx_get_net", "nrx_last_launch_count",
     "nrx_last_error", "nrx_status_string", "nrx_profile", "nrx_profile_read", "nrx_detect_noalloc",
+    "nrx_check",
 )
 KERNEL_KINDS = 5
 
@@ -86,6 +87,8 @@ def load() -> ctypes.CDLL:
     lib.nrx_profile_read.argtypes = [P, I32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_int64), I32]
     lib.nrx_profile_read.restype = ctypes.c_int
+    lib.nrx_check.argtypes = [P, P]
+    lib.nrx_check.restype = ctypes.c_int
     lib.nrx_detect_noalloc.argtypes = [P, P, P, CFG, P, P, P]
     lib.nrx_detect_noalloc.restype = ctypes.c_int
     lib.nrx_status_string.argtypes = [ctypes.c_int]
@@ -164,6 +167,10 @@ class Receiver:
 
     def last_launch_count(self) -> int:
         return int(self._lib.nrx_last_launch_count(self.ctx))
+
+    def nrx_check(self, stream=None):
+        """Synchronise and raise on a device-side failure (e.g. NRX_ETIMEDOUT)."""
+        self._check(self._lib.nrx_check(self.ctx, _stream_ptr(stream)), "nrx_check")
 
     def nrx_profile(self, enable: bool):
         self._check(self._lib.nrx_profile(self.ctx, int(bool(enable))), "nrx_profile")

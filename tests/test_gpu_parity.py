@@ -136,3 +136,73 @@ def test_results_do_not_depend_on_batch_composition():
     y1, d1, b1, _ = H.device_inputs(slots[3:4])
     alone = rx.nrx_detect_batch(y1, d1, w.dmrs_symbols, b1).cpu().numpy()
     assert np.array_equal(np.concatenate(per[3]), alone)
+
+
+TOL_TC = 2e-2  # the BF16 bound of the specification, applied to both 16-bit modes
+TC_MODES = ["bf16", "fp16"]
+
+
+@pytest.mark.parametrize("prec", TC_MODES)
+@pytest.mark.parametrize("workload", ["mu2_4rx_24prb", "mu4_4rx_273prb"])
+def test_nrx_tc_parity(workload, prec):
+    """Tensor-core path (tcgen05 GEMMs on 16-bit operands, 16-bit activations)
+    vs the FP64 oracle."""
+    w, slots = H.slots_for(workload)
+    rx = _receiver(w.net, slots, prec)
+    y, dmrs, bits, _ = H.device_inputs(slots)
+    llr = rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits).cpu().numpy()
+    rx.nrx_check()
+    assert rx.last_launch_count() == 2 + w.net.iterations * (1 + w.net.res_blocks)
+    errs = H.rel_errors(llr, H.oracle_nrx(slots, H.weights64(w.net), w.net), slots)
+    assert max(errs) <= TOL_TC, errs
+
+
+TC_EDGE = [
+    # (U, B, num_prb, dmrs, R, N_it, bits): ragged tiles, 1..4 users, 1 DMRS symbol
+    (1, 4, 1, (2,), 1, 1, (6,)),
+    (3, 2, 5, (2, 11), 2, 2, (6, 2, 4)),
+    (2, 8, 3, (3, 10), 2, 1, (4, 4)),
+    (4, 4, 7, (5, 6), 1, 3, (2, 4, 6, 2)),
+]
+
+
+@pytest.mark.parametrize("prec", TC_MODES)
+@pytest.mark.parametrize("case", TC_EDGE)
+def test_tc_edge_geometries(case, prec):
+    U, B, prb, dmrs, R, N_it, bits = case
+    net = synth.NetConfig(num_rx_ant=B, channels=64, res_blocks=R, iterations=N_it, m_max=6)
+    rng = np.random.Generator(np.random.PCG64(91))
+    slots = []
+    for i in range(3):
+        cfg = synth.SlotConfig(num_prb=prb, num_users=U, num_rx_ant=B, dmrs_symbols=dmrs, bits_per_symbol=bits,
+                               snr_db=float(rng.uniform(0, 15)), num_taps=5, delay_spread_s=150e-9,
+                               doppler_hz=200.0, ula=bool(i % 2))
+        slots.append(synth.make_slot(cfg, rng))
+    rx = _receiver(net, slots, prec)
+    y, d, b, _ = H.device_inputs(slots)
+    llr = rx.nrx_detect_batch(y, d, dmrs, b).cpu().numpy()
+    rx.nrx_check()
+    errs = H.rel_errors(llr, H.oracle_nrx(slots, H.weights64(net), net), slots)
+    assert max(errs) <= TOL_TC, errs
+
+
+@pytest.mark.parametrize("prec", TC_MODES)
+def test_tc_state_after_one_iteration(prec):
+    w, slots = H.slots_for("mu2_4rx_24prb", 2)
+    rx = _receiver(w.net, slots, prec)
+    y, dmrs, bits, _ = H.device_inputs(slots)
+    rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits, iterations=1)
+    rx.nrx_check()
+    W = H.weights64(w.net)
+    for i, s in enumerate(slots):
+        st = rx.nrx_copy_state(i, s.cfg.num_users, s.cfg.num_subcarriers).cpu().numpy()
+        ref = O.nrx_states(s.y, s.dmrs, s.cfg.num_users, s.cfg.dmrs_symbols, W, 1, w.net.res_blocks)[1]
+        assert np.max(np.abs(st - ref)) <= TOL_TC * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec", TC_MODES)
+def test_tc_context_rejects_c32(prec):
+    w = synth.WORKLOADS["su_2rx_4prb"]
+    with pytest.raises(nrx.NrxError) as e:
+        _receiver(w.net, synth.workload_slots(w, 1), prec)
+    assert e.value.status == nrx.NRX_EUNSUPPORTED
