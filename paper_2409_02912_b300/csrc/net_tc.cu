@@ -515,46 +515,65 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
       timed_out = true;
       break;
     }
+    // PW2 epilogue, step 1: accumulator rows (+ b2) -> FP32 staging in shared
+    // memory (the A tiles and P1 are free now).  Staging row sr = x * 14 + t;
+    // 16-byte chunk k of a row is stored at k ^ (sr & 7).
     {
       float v[64];
       tc::tmem_row64(c.tmem + 128 + mt * 64 + ((uint32_t)(q * 32) << 16), v);
-      const int s = s0 + rcol;
-      if (rt < NRX_SYMBOLS && rcol < L::TW && s < S) {
-        const size_t off = (base + (size_t)rt * S + s) * C64;
-        const uint4* res = reinterpret_cast<const uint4*>(z_in + off);
-        uint4* dst = reinterpret_cast<uint4*>((last ? state : z_out) + off);
+      if (rt < NRX_SYMBOLS && rcol < L::TW) {
+        const int sr = rcol * NRX_SYMBOLS + rt;
+        float4* dst = reinterpret_cast<float4*>(sr < 128 ? sm + L::A + sr * 256 : sm + L::ZB + (sr - 128) * 256);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {  // two halves of 4 chunks: loads batched, registers bounded
-        uint4 rq[4], sq[4];
+        for (int k = 0; k < 16; ++k)
+          dst[k ^ (sr & 7)] = make_float4(v[4 * k] + sb2[4 * k], v[4 * k + 1] + sb2[4 * k + 1],
+                                          v[4 * k + 2] + sb2[4 * k + 2], v[4 * k + 3] + sb2[4 * k + 3]);
+      }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    // Step 2: + residual (+ state), coalesced: 8 threads per row, rows ordered
+    // symbol-major then subcarrier (each warp moves 4 consecutive 128-byte rows).
+    {
+      constexpr int kItems = NRX_SYMBOLS * L::TW * 8;
+      constexpr int kIt = (kItems + kThreads - 1) / kThreads;
+      T* out = last ? state : z_out;
+      uint4 rq[kIt], sq[kIt];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) rq[j] = __ldg(res + 4 * h + j);
-        if (last) {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) sq[j] = dst[4 * h + j];  // plain load: this kernel writes the state
+      for (int it = 0; it < kIt; ++it) {
+        const int i = tid + it * kThreads;
+        const int c8 = i & 7, x = (i >> 3) % L::TW, t = (i >> 3) / L::TW, s = s0 + x;
+        rq[it] = make_uint4(0, 0, 0, 0);
+        sq[it] = make_uint4(0, 0, 0, 0);
+        if (i < kItems && s < S) {
+          const size_t off = (base + (size_t)t * S + s) * C64 + c8 * 8;
+          rq[it] = __ldg(reinterpret_cast<const uint4*>(z_in + off));
+          if (last) sq[it] = *reinterpret_cast<const uint4*>(state + off);  // plain load: written here
         }
+      }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int ch = 4 * h + j;
-          float o[8];
-          const uint32_t rw[4] = {rq[j].x, rq[j].y, rq[j].z, rq[j].w};
+      for (int it = 0; it < kIt; ++it) {
+        const int i = tid + it * kThreads;
+        const int c8 = i & 7, x = (i >> 3) % L::TW, t = (i >> 3) / L::TW, s = s0 + x;
+        if (i >= kItems || s >= S) continue;
+        const int sr = x * NRX_SYMBOLS + t;
+        const float4* src = reinterpret_cast<const float4*>(sr < 128 ? sm + L::A + sr * 256 : sm + L::ZB + (sr - 128) * 256);
+        const float4 a = src[(2 * c8) ^ (sr & 7)], b = src[(2 * c8 + 1) ^ (sr & 7)];
+        float o[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        const uint32_t rw[4] = {rq[it].x, rq[it].y, rq[it].z, rq[it].w};
+        const uint32_t sw[4] = {sq[it].x, sq[it].y, sq[it].z, sq[it].w};
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float2 f = Op<T>::unpack(rw[k]);
-            o[2 * k] = v[ch * 8 + 2 * k] + sb2[ch * 8 + 2 * k] + f.x;
-            o[2 * k + 1] = v[ch * 8 + 2 * k + 1] + sb2[ch * 8 + 2 * k + 1] + f.y;
-          }
+        for (int k = 0; k < 4; ++k) {
+          const float2 f = Op<T>::unpack(rw[k]);
+          o[2 * k] += f.x;
+          o[2 * k + 1] += f.y;
           if (last) {
-            const uint32_t sw[4] = {sq[j].x, sq[j].y, sq[j].z, sq[j].w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const float2 f = Op<T>::unpack(sw[k]);
-              o[2 * k] += f.x;
-              o[2 * k + 1] += f.y;
-            }
+            const float2 g2 = Op<T>::unpack(sw[k]);
+            o[2 * k] += g2.x;
+            o[2 * k + 1] += g2.y;
           }
-          dst[ch] = pack8<T>(o);
         }
-        }
+        *reinterpret_cast<uint4*>(out + (base + (size_t)t * S + s) * C64 + c8 * 8) = pack8<T>(o);
       }
     }
     tc::tc_fence_before();
