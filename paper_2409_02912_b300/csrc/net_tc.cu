@@ -157,21 +157,23 @@ __device__ __forceinline__ void tc_teardown(TcCta& c, uint32_t ncols, bool timed
 // ---------------------------------------------------------------------------
 // Message passing + CNN-update input layer.  One M tile = 128 rows =
 // `nre` REs x U users (row = u * nre + j).
-//   GEMM1: h = ReLU(S W1^T + b1)            -> TMEM cols [0, 64)
-//   GEMM2: m = h W2^T + b2                  -> TMEM cols [64, 128)
-//   a_u = sum_{v != u} m_v (FP32, through shared memory, two halves of 32 ch)
-//   GEMM3: z = S Win_S^T + a Win_a^T + b + PE Win_pe^T -> TMEM cols [128, 192)
+//   GEMM1: h = ReLU(S W1^T + b1)                          -> TMEM cols [0, 64)
+//   g_u = sum_{v != u} h_v  (FP32, through shared memory)
+//   GEMM2: z = S Win_S^T + g (Win_a W2)^T + b + (U-1) Win_a b2 + PE Win_pe^T
+//                                                          -> TMEM cols [64, 128)
+// (the message output layer W2 folded into the input layer, see net_tc.h).
+// Epilogues use all 8 warps (warp w: TMEM lanes 32 (w & 3), column half w >> 2);
+// z rows are staged in shared memory and stored 8 threads per row.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct MpLayout {
   static constexpr int A_S = 0;
-  static constexpr int A_A = 16384;
-  static constexpr int A_H = 32768;  // also the FP32 exchange buffer (128 x 32 floats)
-  static constexpr int W1 = 49152;
-  static constexpr int W2 = W1 + wbytes<T>();
-  static constexpr int WS = W2 + wbytes<T>();
-  static constexpr int WA = WS + wbytes<T>();
-  static constexpr int VEC = WA + wbytes<T>();  // b1, b2, bin, pe_t, pe_f: 5 x 64 floats
+  static constexpr int A_G = 16384;
+  static constexpr int XCH = 32768;  // FP32 [128][64] exchange of h; later 16-bit z staging
+  static constexpr int W1 = 65536;
+  static constexpr int WS = W1 + wbytes<T>();
+  static constexpr int WC = WS + wbytes<T>();
+  static constexpr int VEC = WC + wbytes<T>();  // b1, bin, cb2, pe_t, pe_f: 5 x 64 floats
   static constexpr int BAR = VEC + 5 * 64 * 4;
   static constexpr int TOTAL = BAR + 16;
   static constexpr int DYN = TOTAL + 1024;
@@ -186,30 +188,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
   float* vec = reinterpret_cast<float*>(sm + MpL::VEC);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   load_wtile<T>(sm + MpL::W1, w.mp1);
-  load_wtile<T>(sm + MpL::W2, w.mp2);
   load_wtile<T>(sm + MpL::WS, w.in_s);
-  load_wtile<T>(sm + MpL::WA, w.in_a);
+  load_wtile<T>(sm + MpL::WC, w.in_c);
+  const int U = g.U, S = g.S;
   for (int i = tid; i < 64; i += kThreads) {
     vec[i] = __ldg(w.mp1_b + i);
-    vec[64 + i] = __ldg(w.mp2_b + i);
-    vec[128 + i] = __ldg(w.in_b + i);
+    vec[64 + i] = __ldg(w.in_b + i) + (float)(U - 1) * __ldg(w.cb2 + i);
     vec[192 + i] = __ldg(w.in_pe + i);
     vec[256 + i] = __ldg(w.in_pe + 64 + i);
   }
   TcCta c;
-  tc_setup(c, reinterpret_cast<uint64_t*>(sm + MpL::BAR), reinterpret_cast<uint32_t*>(sm + MpL::BAR + 8),
-           256);
-  const uint32_t sa_s = tc::smem_u32(sm + MpL::A_S), sa_a = tc::smem_u32(sm + MpL::A_A),
-                 sa_h = tc::smem_u32(sm + MpL::A_H);
-  const uint32_t sw1 = tc::smem_u32(sm + MpL::W1), sw2 = tc::smem_u32(sm + MpL::W2),
-                 sws = tc::smem_u32(sm + MpL::WS), swa = tc::smem_u32(sm + MpL::WA);
-  const int U = g.U, S = g.S;
+  tc_setup(c, reinterpret_cast<uint64_t*>(sm + MpL::BAR), reinterpret_cast<uint32_t*>(sm + MpL::BAR + 8), 128);
+  const uint32_t sa_s = tc::smem_u32(sm + MpL::A_S), sa_g = tc::smem_u32(sm + MpL::A_G);
+  const uint32_t sw1 = tc::smem_u32(sm + MpL::W1), sws = tc::smem_u32(sm + MpL::WS),
+                 swc = tc::smem_u32(sm + MpL::WC);
   const int n_re = NRX_SYMBOLS * S;
   const int n_tiles = g.n_slots * tiles_per_slot;
-  const int q = warp & 3;  // TMEM lane quarter of this warp
-  const int r = q * 32 + lane;  // the row this thread's epilogue owns (warps 0-3)
+  const int q = warp & 3, hc = warp >> 2;  // TMEM lane quarter, column half
+  const int r = q * 32 + lane;             // epilogue row of this thread
+  const uint32_t tlane = (uint32_t)(q * 32) << 16;
   bool timed_out = false;
-  float* xchg = reinterpret_cast<float*>(sm + MpL::A_H);
+  float* xch = reinterpret_cast<float*>(sm + MpL::XCH);
 
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int sl = tile / tiles_per_slot;
@@ -245,103 +244,114 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
       timed_out = true;
       break;
     }
-    // h = ReLU(acc + b1) -> A_H
-    if (warp < 4) {
-      float v[64];
-      tc::tmem_row64(c.tmem + ((uint32_t)(q * 32) << 16), v);
+    // h = ReLU(acc + b1) -> FP32 exchange, row r, columns [32 hc, 32 hc + 32);
+    // float4 chunk k of a row is stored at k ^ (r & 7)
+    {
+      uint32_t a[16], b[16];
+      tc::tmem_ld16(c.tmem + tlane + 32 * hc, a);
+      tc::tmem_ld16(c.tmem + tlane + 32 * hc + 16, b);
+      tc::tmem_wait16(a);
+      tc::tmem_wait16(b);
+      const float* b1 = vec + 32 * hc;
 #pragma unroll
-      for (int k = 0; k < 64; ++k) v[k] = fmaxf(v[k] + vec[k], 0.f);
-      store_row_sw128<T>(sm + MpL::A_H, r, v);
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t* src = k < 4 ? a + 4 * k : b + 4 * (k - 4);
+        const int kk = 8 * hc + k;
+        *reinterpret_cast<float4*>(xch + r * 64 + ((kk ^ (r & 7)) << 2)) =
+            make_float4(fmaxf(__uint_as_float(src[0]) + b1[4 * k], 0.f),
+                        fmaxf(__uint_as_float(src[1]) + b1[4 * k + 1], 0.f),
+                        fmaxf(__uint_as_float(src[2]) + b1[4 * k + 2], 0.f),
+                        fmaxf(__uint_as_float(src[3]) + b1[4 * k + 3], 0.f));
+      }
     }
-    tc::fence_async_smem();
     tc::tc_fence_before();
+    __syncthreads();
+    // g_u = sum over the other active users -> A_G (16-bit, SW128)
+    for (int i = tid; i < nre * 16; i += kThreads) {
+      const int j = i >> 4, cq = i & 15;
+      float4 hv[NRX_MAX_USERS];
+#pragma unroll
+      for (int u = 0; u < NRX_MAX_USERS; ++u) {
+        const int rw = u * nre + j;
+        hv[u] = u < U ? *reinterpret_cast<const float4*>(xch + rw * 64 + ((cq ^ (rw & 7)) << 2))
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < NRX_MAX_USERS; ++u) {
+        if (u >= U) break;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int v = 0; v < NRX_MAX_USERS; ++v)
+          if (v != u && v < U) {
+            a.x += hv[v].x;
+            a.y += hv[v].y;
+            a.z += hv[v].z;
+            a.w += hv[v].w;
+          }
+        const int row = u * nre + j;
+        *reinterpret_cast<uint2*>(sm + MpL::A_G + tc::sw128_offset(row, 4 * cq)) =
+            make_uint2(Op<T>::pack(a.x, a.y), Op<T>::pack(a.z, a.w));
+      }
+    }
+    // rows of A_G not covered by (u < U, j < nre) only feed rows that are never stored
+    tc::fence_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc::tc_fence_after();
-      gemm64<T>(c.tmem + 64, sa_h, sw2, false);
+      gemm64<T>(c.tmem + 64, sa_s, sws, false);
+      gemm64<T>(c.tmem + 64, sa_g, swc, true);
       tc::mma_commit(c.bar);
     }
     if (!tc_wait(c, w.err)) {
       timed_out = true;
       break;
     }
-    // m = acc + b2; a_u = sum_{v != u} m_v, exchanged in two halves of 32 channels.
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      __syncthreads();  // previous readers of the exchange buffer are done
-      // exchange row r: 8 chunks of 4 floats, chunk k stored at position k ^ (r & 7)
-      if (warp < 4) {
-        uint32_t ma[16], mb[16];
-        const uint32_t ta = c.tmem + 64 + half * 32 + ((uint32_t)(q * 32) << 16);
-        tc::tmem_ld16(ta, ma);
-        tc::tmem_ld16(ta + 16, mb);
-        tc::tmem_wait16(ma);
-        tc::tmem_wait16(mb);
-        const float* b2 = vec + 64 + half * 32;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const uint32_t* src = k < 4 ? ma + 4 * k : mb + 4 * (k - 4);
-          *reinterpret_cast<float4*>(xchg + r * 32 + ((k ^ (r & 7)) << 2)) =
-              make_float4(__uint_as_float(src[0]) + b2[4 * k], __uint_as_float(src[1]) + b2[4 * k + 1],
-                          __uint_as_float(src[2]) + b2[4 * k + 2], __uint_as_float(src[3]) + b2[4 * k + 3]);
-        }
-      }
-      __syncthreads();
-      for (int i = tid; i < nre * 16; i += kThreads) {
-        const int j = i >> 4, cp = i & 15;
-        float2 mv[NRX_MAX_USERS];
-#pragma unroll
-        for (int u = 0; u < NRX_MAX_USERS; ++u) {
-          const int rw = u * nre + j;
-          mv[u] = u < U ? *reinterpret_cast<const float2*>(xchg + rw * 32 + (((cp >> 1) ^ (rw & 7)) << 2) + (cp & 1) * 2)
-                        : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < NRX_MAX_USERS; ++u) {
-          if (u >= U) break;
-          float ax = 0.f, ay = 0.f;
-#pragma unroll
-          for (int v = 0; v < NRX_MAX_USERS; ++v)
-            if (v != u && v < U) {
-              ax += mv[v].x;
-              ay += mv[v].y;
-            }
-          const int row = u * nre + j;
-          *reinterpret_cast<uint32_t*>(sm + MpL::A_A + tc::sw128_offset(row, half * 32 + 2 * cp)) =
-              Op<T>::pack(ax, ay);
-        }
-      }
-    }
-    // rows of the A_A tile not covered by (u < U, j < nre) are never read back
-    tc::fence_async_smem();
-    tc::tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc::tc_fence_after();
-      gemm64<T>(c.tmem + 128, sa_s, sws, false);
-      gemm64<T>(c.tmem + 128, sa_a, swa, true);
-      tc::mma_commit(c.bar);
-    }
-    if (!tc_wait(c, w.err)) {
-      timed_out = true;
-      break;
-    }
-    if (warp < 4) {
+    // z = acc + b + (U-1) Win_a b2 + PE terms -> 16-bit staging [128][128 B] in
+    // the exchange region; 16-byte chunk k of a row stored at k ^ (r & 7)
+    {
+      uint32_t a[16], b[16];
+      tc::tmem_ld16(c.tmem + 64 + tlane + 32 * hc, a);
+      tc::tmem_ld16(c.tmem + 64 + tlane + 32 * hc + 16, b);
+      tc::tmem_wait16(a);
+      tc::tmem_wait16(b);
       const int u = r / nre, j = r % nre, re = re0 + j;
-      float v[64];
-      tc::tmem_row64(c.tmem + 128 + ((uint32_t)(q * 32) << 16), v);
+      float pt = 0.f, pf = 0.f;
       if (u < U && re < n_re) {
-        const int t = re / S, s = re % S;
-        const float pt = pe_time(g, t), pf = pe_freq(u, s);
+        pt = pe_time(g, re / S);
+        pf = pe_freq(u, re % S);
+      }
+      const float* bb = vec + 64 + 32 * hc;
+      const float* wt = vec + 192 + 32 * hc;
+      const float* wf = vec + 256 + 32 * hc;
+      unsigned char* rowp = sm + MpL::XCH + r * 128;
 #pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = v[k] + vec[128 + k] + pt * vec[192 + k] + pf * vec[256 + k];
-        store_row_global<T>(z + (((size_t)sl * U + u) * n_re + re) * C64, v);
+      for (int k = 0; k < 4; ++k) {
+        float o[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int cc = 8 * k + e;
+          const uint32_t raw = cc < 16 ? a[cc] : b[cc - 16];
+          o[e] = __uint_as_float(raw) + bb[cc] + pt * wt[cc] + pf * wf[cc];
+        }
+        const int kk = 4 * hc + k;
+        *reinterpret_cast<uint4*>(rowp + ((kk ^ (r & 7)) << 4)) = pack8<T>(o);
       }
     }
     tc::tc_fence_before();
+    __syncthreads();
+    // coalesced store: 8 threads per 128-byte row
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int i = tid + it * kThreads;
+      const int row = i >> 3, ch = i & 7;
+      const int u = row / nre, j = row % nre, re = re0 + j;
+      if (u < U && re < n_re)
+        reinterpret_cast<uint4*>(z + (((size_t)sl * U + u) * n_re + re) * C64)[ch] =
+            *reinterpret_cast<const uint4*>(sm + MpL::XCH + row * 128 + ((ch ^ (row & 7)) << 4));
+    }
     __syncthreads();
   }
-  tc_teardown(c, 256, timed_out);
+  tc_teardown(c, 128, timed_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -748,17 +758,32 @@ nrx_status upload_tc_weights(bool bf16, int C, int R, int N_it, const std::vecto
                              void** dev_alloc, ReadoutWeightsTC* ro, int** err_word) {
   if (C != 64) return NRX_EUNSUPPORTED;
   const size_t wb = bf16 ? 2 * 8192 : 8192;
-  const int per_it = 4 + 2 * R;
+  const int per_it = 3 + 2 * R;  // mp1, in_s, in_c, then pw1/pw2 per block
   const size_t n_mats = (size_t)N_it * per_it + 1;
-  std::vector<unsigned char> host(n_mats * wb + 256, 0);
+  const size_t cb2_off = n_mats * wb;                    // N_it x C floats
+  const size_t err_off = cb2_off + (size_t)N_it * C * 4;  // one int
+  std::vector<unsigned char> host(err_off + 256, 0);
+  float* cb2_host = reinterpret_cast<float*>(host.data() + cb2_off);
   size_t t = 0;
   const size_t per_blob = 6 + 6 * R;
   for (int k = 0; k < N_it; ++k) {
-    const float* const* b = blob_it.data() + k * per_blob;
-    pack_weight(b[0], C, 0, host.data() + (t++) * wb, bf16);           // mp1
-    pack_weight(b[2], C, 0, host.data() + (t++) * wb, bf16);           // mp2
-    pack_weight(b[4], 2 * C + 2, 0, host.data() + (t++) * wb, bf16);  // in, S columns
-    pack_weight(b[4], 2 * C + 2, C, host.data() + (t++) * wb, bf16);  // in, aggregate columns
+    const float* const* b = blob_it.data() + k * per_blob;  // mp1w, mp1b, mp2w, mp2b, inw, inb, blocks
+    const int ld = 2 * C + 2;
+    pack_weight(b[0], C, 0, host.data() + (t++) * wb, bf16);   // mp1
+    pack_weight(b[4], ld, 0, host.data() + (t++) * wb, bf16);  // in, S columns
+    // Win_a W2 and Win_a b2 in FP64 (the message output layer folded in)
+    std::vector<float> wc((size_t)C * C);
+    for (int n = 0; n < C; ++n) {
+      double cb = 0.0;
+      for (int kk = 0; kk < C; ++kk) {
+        double acc = 0.0;
+        for (int m = 0; m < C; ++m) acc += (double)b[4][(size_t)n * ld + C + m] * (double)b[2][(size_t)m * C + kk];
+        wc[(size_t)n * C + kk] = (float)acc;
+        cb += (double)b[4][(size_t)n * ld + C + kk] * (double)b[3][kk];
+      }
+      cb2_host[(size_t)k * C + n] = (float)cb;
+    }
+    pack_weight(wc.data(), C, 0, host.data() + (t++) * wb, bf16);  // in_c
     for (int r = 0; r < R; ++r) {
       const float* const* blk = b + 6 + 6 * r;
       pack_weight(blk[1], C, 0, host.data() + (t++) * wb, bf16);  // pw1
@@ -777,7 +802,7 @@ nrx_status upload_tc_weights(bool bf16, int C, int R, int N_it, const std::vecto
   }
   *dev_alloc = d;
   unsigned char* base = static_cast<unsigned char*>(d);
-  int* err = reinterpret_cast<int*>(base + n_mats * wb);
+  int* err = reinterpret_cast<int*>(base + err_off);
   *err_word = err;
   auto mat = [&](size_t i) { return reinterpret_cast<const uint4*>(base + i * wb); };
   out->resize(N_it);
@@ -787,12 +812,11 @@ nrx_status upload_tc_weights(bool bf16, int C, int R, int N_it, const std::vecto
     memset(&w, 0, sizeof(w));
     const IterWeightsF32& f = it32[k];
     w.mp1 = mat(t++);
-    w.mp2 = mat(t++);
     w.in_s = mat(t++);
-    w.in_a = mat(t++);
+    w.in_c = mat(t++);
     w.mp1_b = f.mp1_b;
-    w.mp2_b = f.mp2_b;
     w.in_b = f.in_b;
+    w.cb2 = reinterpret_cast<const float*>(base + cb2_off) + (size_t)k * C;
     w.in_pe = f.in_t + (size_t)2 * C * C;
     for (int r = 0; r < R; ++r) {
       w.pw1[r] = mat(t++);

@@ -18,14 +18,18 @@
 // W_lo = bf16(W - W_hi), and multiplied as A W_hi^T + A W_lo^T (the weight
 // rounding error drops to that of a 16-bit mantissa).  Biases, depthwise taps
 // and the PE columns of the input layer stay FP32.
+//
+// The message MLP's output layer is folded into the CNN-update input layer:
+// with h_v = ReLU(W1 S_v + b1) and g_u = sum_{v != u} h_v, the aggregate is
+// a_u = W2 g_u + (U-1) b2, so Win_a a_u = (Win_a W2) g_u + (U-1) Win_a b2.
+// in_c holds Win_a W2 (formed in FP64 on the host) and cb2 = Win_a b2.
 struct IterWeightsTC {
   const uint4* mp1;
-  const uint4* mp2;
   const uint4* in_s;   // input layer, columns acting on S
-  const uint4* in_a;   // input layer, columns acting on the aggregate
+  const uint4* in_c;   // Win_a W2, acting on g
   const float* mp1_b;
-  const float* mp2_b;
   const float* in_b;
+  const float* cb2;    // [C] Win_a b2
   const float* in_pe;  // [2][C]: columns acting on (dt, df)
   const uint4* pw1[4];
   const uint4* pw2[4];
