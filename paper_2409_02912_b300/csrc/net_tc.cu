@@ -382,6 +382,44 @@ struct BlkLayout {
   static constexpr int DYN = TOTAL + 1024;
 };
 
+// Sliding 3x3 depthwise for two adjacent output columns (o = 0, 1) of one
+// channel pair: in(ti, k) gives input column k in [0, 4) of symbol ti;
+// out(t, o, v) receives output column o of symbol t.  Acc is float2 (packed
+// FP32 FMAs) or __half2 (packed FP16 FMAs); zero padding in time.
+template <typename Acc, typename In, typename Fma, typename Out>
+__device__ __forceinline__ void dw_2col(const Acc (&kk)[9], Acc zero, In in, Fma fma, Out out) {
+  Acc am[2] = {zero, zero}, a0[2] = {zero, zero}, ap[2] = {zero, zero};
+#pragma unroll
+  for (int ti = 0; ti < NRX_SYMBOLS; ++ti) {
+    Acc x[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = in(ti, k);
+#pragma unroll
+    for (int o = 0; o < 2; ++o)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        am[o] = fma(kk[6 + k], x[o + k], am[o]);  // output ti-1 (tap row +1)
+        a0[o] = fma(kk[3 + k], x[o + k], a0[o]);  // output ti (tap row 0)
+        ap[o] = fma(kk[k], x[o + k], ap[o]);      // output ti+1 (tap row -1)
+      }
+    if (ti >= 1) {
+      out(ti - 1, 0, am[0]);
+      out(ti - 1, 1, am[1]);
+    }
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      am[o] = a0[o];
+      a0[o] = ap[o];
+      ap[o] = zero;
+    }
+  }
+  out(NRX_SYMBOLS - 1, 0, am[0]);
+  out(NRX_SYMBOLS - 1, 1, am[1]);
+}
+
+__device__ __forceinline__ __half2 h2_from_u32(uint32_t w) { return *reinterpret_cast<__half2*>(&w); }
+__device__ __forceinline__ uint32_t u32_from_h2(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint4* __restrict__ w1p,
                                                            const uint4* __restrict__ w2p,
@@ -454,19 +492,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
       }
     }
     __syncthreads();
-    // DW1: output column e (s = s0-1+e) reads input columns e, e+1, e+2.
-    float2 k1[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) k1[i] = make_float2(sk1[(2 * cp) * 9 + i], sk1[(2 * cp + 1) * 9 + i]);
-    for (int e = cg; e < L::MW; e += 8) {
+    // DW1: output column e (s = s0-1+e) reads input columns e, e+1, e+2; warp
+    // cg computes output columns 2 cg and 2 cg + 1.
+    {
+      const int e = 2 * cg;
       const uint32_t* col = zw + e * 32 + cp;
       unsigned char* dst = a_tile + e * 2048;
-      tc::dw_column(
-          k1, [&](int ti, int k) { return Op<T>::unpack(col[(ti * L::IW + k) * 32]); },
-          [&](int t, float2 v) {
-            *reinterpret_cast<uint32_t*>(dst + (t >> 3) * 1024 + (t & 7) * 128 + ((cpc ^ (t & 7)) << 4) + cpl * 4) =
-                Op<T>::pack(v.x, v.y);
-          });
+      auto store = [&](int t, int o, uint32_t word) {
+        *reinterpret_cast<uint32_t*>(dst + o * 2048 + (t >> 3) * 1024 + (t & 7) * 128 + ((cpc ^ (t & 7)) << 4) +
+                                     cpl * 4) = word;
+      };
+      if constexpr (Op<T>::split) {  // BF16 operands: FP32 packed FMAs
+        float2 k1[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) k1[i] = make_float2(sk1[(2 * cp) * 9 + i], sk1[(2 * cp + 1) * 9 + i]);
+        dw_2col(
+            k1, make_float2(0.f, 0.f), [&](int ti, int k) { return Op<T>::unpack(col[(ti * L::IW + k) * 32]); },
+            [](float2 a, float2 b, float2 c2) { return tc::ffma2(a, b, c2); },
+            [&](int t, int o, float2 v) { store(t, o, Op<T>::pack(v.x, v.y)); });
+      } else {  // FP16 operands: packed FP16 FMAs
+        __half2 k1[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) k1[i] = __floats2half2_rn(sk1[(2 * cp) * 9 + i], sk1[(2 * cp + 1) * 9 + i]);
+        dw_2col(
+            k1, __float2half2_rn(0.f), [&](int ti, int k) { return h2_from_u32(col[(ti * L::IW + k) * 32]); },
+            [](__half2 a, __half2 b, __half2 c2) { return __hfma2(a, b, c2); },
+            [&](int t, int o, __half2 v) { store(t, o, u32_from_h2(v)); });
+      }
     }
     tc::fence_async_smem();
     __syncthreads();
@@ -499,19 +551,35 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
     }
     tc::tc_fence_before();
     __syncthreads();
-    // DW2 + ReLU: output column x (s = s0+x) reads P1 columns x, x+1, x+2.
-    float2 k2[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) k2[i] = make_float2(sk2[(2 * cp) * 9 + i], sk2[(2 * cp + 1) * 9 + i]);
-    for (int x = cg; x < L::TW; x += 8) {
+    // DW2 + ReLU: output column x (s = s0+x) reads P1 columns x, x+1, x+2;
+    // warps 0..6 compute output columns 2 cg and 2 cg + 1.
+    if (cg < L::TW / 2) {
+      const int x = 2 * cg;
       const uint32_t* col = zw + x * 32 + cpl;
       unsigned char* dst = a_tile + x * 2048;
-      tc::dw_column(
-          k2, [&](int ti, int k) { return Op<T>::unpack(col[(ti * L::MW + k) * 32 + ((cpc ^ (ti & 7)) << 2)]); },
-          [&](int t, float2 v) {
-            *reinterpret_cast<uint32_t*>(dst + (t >> 3) * 1024 + (t & 7) * 128 + ((cpc ^ (t & 7)) << 4) + cpl * 4) =
-                Op<T>::pack(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f));
-          });
+      auto store = [&](int t, int o, uint32_t word) {
+        *reinterpret_cast<uint32_t*>(dst + o * 2048 + (t >> 3) * 1024 + (t & 7) * 128 + ((cpc ^ (t & 7)) << 4) +
+                                     cpl * 4) = word;
+      };
+      auto load = [&](int ti, int k) { return col[(ti * L::MW + k) * 32 + ((cpc ^ (ti & 7)) << 2)]; };
+      if constexpr (Op<T>::split) {
+        float2 k2[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) k2[i] = make_float2(sk2[(2 * cp) * 9 + i], sk2[(2 * cp + 1) * 9 + i]);
+        dw_2col(
+            k2, make_float2(0.f, 0.f), [&](int ti, int k) { return Op<T>::unpack(load(ti, k)); },
+            [](float2 a, float2 b, float2 c2) { return tc::ffma2(a, b, c2); },
+            [&](int t, int o, float2 v) { store(t, o, Op<T>::pack(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f))); });
+      } else {
+        __half2 k2[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) k2[i] = __floats2half2_rn(sk2[(2 * cp) * 9 + i], sk2[(2 * cp + 1) * 9 + i]);
+        const __half2 hz = __float2half2_rn(0.f);
+        dw_2col(
+            k2, hz, [&](int ti, int k) { return h2_from_u32(load(ti, k)); },
+            [](__half2 a, __half2 b, __half2 c2) { return __hfma2(a, b, c2); },
+            [&](int t, int o, __half2 v) { store(t, o, u32_from_h2(__hmax2(v, hz))); });
+      }
     }
     tc::fence_async_smem();
     __syncthreads();
