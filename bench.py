@@ -72,6 +72,27 @@ def nrx_flops_per_re_ue(net: synth.NetConfig) -> dict:
     }
 
 
+def kernel_bytes_per_launch(w: synth.Workload, n_slots: int, bits, act_bytes: int) -> dict:
+    """Algorithmic DRAM bytes per launch of each kernel kind: every tensor it
+    must read or write once (activations of act_bytes per element), halo
+    re-reads and other redundancy excluded.  The residual block is averaged
+    over the R launches of an iteration (R-1 read z and write z; the last
+    reads z and the state and writes the state)."""
+    net = w.net
+    S = 12 * w.num_prb
+    n_dmrs = len(w.dmrs_symbols)
+    act = n_slots * w.num_users * synth.NUM_SYMBOLS * S * net.channels * act_bytes
+    y = n_slots * net.num_rx_ant * synth.NUM_SYMBOLS * S * 8
+    llr = sum((synth.NUM_SYMBOLS - n_dmrs) * S * sum(b) * 4 for b in bits)
+    R = net.res_blocks
+    return {
+        "state_init": y + act,
+        "message_passing": 2 * act,
+        "residual_block": (2 * (R - 1) + 3) * act / R,
+        "readout": act * (synth.NUM_SYMBOLS - n_dmrs) / synth.NUM_SYMBOLS + llr,
+    }
+
+
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -137,6 +158,29 @@ def res_per_slot(w: synth.Workload) -> int:
     return synth.NUM_SYMBOLS * 12 * w.num_prb
 
 
+# ---- multi-rank bookkeeping (one independent replica per GPU, no data-path collective)
+
+def rank_slot_start(rank: int, batch: int) -> int:
+    """First slot index of this rank's batch: ranks draw disjoint seeded slots."""
+    return rank * batch
+
+
+def reduce_max_ms(total_ms: float, world: int, device=None) -> float:
+    """Max over ranks of the timed region (the job is as slow as its slowest rank)."""
+    if world == 1:
+        return total_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(world: int, steps: int, res_per_step: int, max_total_ms: float) -> float:
+    """Whole-job REs/s: REs all ranks processed / the slowest rank's time."""
+    return world * steps * res_per_step / (max_total_ms * 1e-3)
+
+
 def run_reference(args, rank, world):
     """FP64 CPU oracle on the host cores, one slot of the workload per step."""
     if rank != 0:
@@ -194,7 +238,7 @@ def run_ours(args, rank, world, local):
     net = w.net
     blob = synth.pack_weights(net, synth.make_weights(net))
     batch = args.batch or w.batch
-    slots = synth.workload_slots(w, batch, start=rank * batch)
+    slots = synth.workload_slots(w, batch, start=rank_slot_start(rank, batch))
     n = len(slots)
     S = 12 * w.num_prb
     y = torch.from_numpy(synth.stack_batch(slots)).to(dev)
@@ -249,13 +293,9 @@ def run_ours(args, rank, world, local):
         dist.barrier()
     clk = clocks.stop()
     prof = rx.nrx_profile_read(reset=True)
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max_ms(sum(times), world, dev)
     res_step = n * res_per_slot(w)
-    value = world * args.steps * res_step / (total_ms * 1e-3)
+    value = aggregate_value(world, args.steps, res_step, total_ms)
 
     extras = {}
     if not args.no_extras and rank == 0:
@@ -310,22 +350,32 @@ def run_ours(args, rank, world, local):
         extras["cpu_baseline"] = {"value": res_per_slot(w) / secs, "unit": UNIT, "cores": blas_threads(),
                                   "kind": "oracle", "sample": f"1 slot of {WORKLOAD} (45864 REs), FP64 numpy oracle"}
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel: bound by its arithmetic intensity
     pk, src = peaks()
     kern = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     k_ms, k_n = prof[kern]
     per_launch_ms = k_ms / max(k_n, 1)
     flops = nrx_flops_per_re_ue(net)[kern] * n * w.num_users * res_per_slot(w)
+    nbytes = kernel_bytes_per_launch(w, n, bits, 4 if precision == "fp32" else 2)[kern]
     if precision == "fp32":
         peak = pk["sm_max_mhz"] * 1e6 * 148 * FP32_CORE_FLOP_PER_CLK_PER_SM / 1e12
-        bound, unit = "alu", "TFLOP/s"
+        bound, unit, achieved = "alu", "TFLOP/s", flops / (per_launch_ms * 1e-3) / 1e12
+        peak_desc = "FP32 CUDA-core FMA rate at the measured max SM clock"
     else:
-        peak = pk["bf16_tflops_sustained"]
-        bound, unit = "tensor", "TFLOP/s"
-    achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        ridge = pk["bf16_tflops_sustained"] * 1e12 / (pk["hbm_gbs"] * 1e9)
+        if flops / nbytes < ridge:
+            bound, unit, peak = "hbm", "GB/s", pk["hbm_gbs"]
+            achieved = nbytes / (per_launch_ms * 1e-3) / 1e9
+            peak_desc = "measured HBM copy bandwidth"
+        else:
+            bound, unit, peak = "tensor", "TFLOP/s", pk["bf16_tflops_sustained"]
+            achieved = flops / (per_launch_ms * 1e-3) / 1e12
+            peak_desc = "measured sustained dense BF16 tensor rate (FP16 has the same rate)"
     roofline = {"bound": bound, "kernel": kern, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "peak_source": src, "traffic": traffic_for(kern, precision),
-                "flop_per_launch": flops, "launch_ms": per_launch_ms,
+                "frac": achieved / peak, "peak_source": f"{src}: {peak_desc}",
+                "traffic": traffic_for(kern, precision),
+                "flop_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+                "intensity_flop_per_byte": flops / nbytes, "launch_ms": per_launch_ms,
                 "kernel_share": {k: prof[k][0] / max(sum(v[0] for v in prof.values()), 1e-12) for k in prof
                                  if prof[k][1] > 0}}
 

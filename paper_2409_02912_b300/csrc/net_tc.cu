@@ -233,6 +233,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
             v[it];
       }
     }
+    {  // L2 prefetch of the next tile's rows
+      const int nt = tile + gridDim.x;
+      if (nt < n_tiles && tid < 128) {
+        const int nsl = nt / tiles_per_slot, nre0 = (nt % tiles_per_slot) * nre;
+        const int u = tid / nre, j = tid % nre, re = nre0 + j;
+        if (u < U && re < n_re) tc::prefetch_l2(state + (((size_t)nsl * U + u) * n_re + re) * C64);
+      }
+    }
     tc::fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -489,6 +497,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
       for (int it = 0; it < kIt; ++it) {
         const int i = tid + it * kThreads;
         if (i < kN) reinterpret_cast<uint4*>(sm + L::ZB)[i] = v[it];
+      }
+    }
+    // L2 prefetch: the next tile's input rows, and this tile's state rows (last block)
+    {
+      const int nt = tile + gridDim.x;
+      if (nt < n_tiles && tid < NRX_SYMBOLS * L::IW) {
+        const int t = tid / L::IW, e = tid % L::IW;
+        const int ns0 = (nt % tps) * L::TW, s = ns0 - 2 + e;
+        if (s >= 0 && s < S) tc::prefetch_l2(z_in + ((size_t)(nt / tps) * NRX_SYMBOLS * S + (size_t)t * S + s) * C64);
+      }
+      if (last && tid >= 256 - NRX_SYMBOLS * L::TW) {
+        const int k = tid - (256 - NRX_SYMBOLS * L::TW);
+        const int t = k / L::TW, x = k % L::TW, s = s0 + x;
+        if (s < S) tc::prefetch_l2(state + (base + (size_t)t * S + s) * C64);
       }
     }
     __syncthreads();

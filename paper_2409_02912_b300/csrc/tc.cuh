@@ -188,6 +188,11 @@ __device__ __forceinline__ void tmem_row64(uint32_t taddr, float (&v)[64]) {
   }
 }
 
+// Bring the line holding p into L2 (no register result, no ordering).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // d = a * b + c on both FP32 lanes (one packed instruction).
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
   unsigned long long d;
