@@ -29,142 +29,168 @@ __device__ __forceinline__ void store_pair<__half>(__half* p, float a, float b) 
   *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
 }
 
-template <int C, typename OutT>
+template <int C, int B, typename OutT>
 __global__ void __launch_bounds__(256) k_state_init(Geometry g, SlotTable tab, const float2* __restrict__ y,
                                                     const float* __restrict__ w_pw,  // [C][F]
                                                     const float* __restrict__ b_pw,  // [C]
                                                     const float* __restrict__ k_dw,  // [C][9]
                                                     OutT* __restrict__ s_out) {
+  constexpr int F = 4 * B + 2;
   constexpr int TW = kStateInitTile;
   constexpr int EW = TW + 2;
-  constexpr int NRE = NRX_SYMBOLS * EW;  // REs of the extended tile, index t * EW + e
-  constexpr int CQ = C / 4, RG = 256 / CQ;  // PW: channel quads x RE groups
+  constexpr int NRE = NRX_SYMBOLS * EW;  // REs of the extended tile, index t * EW + e (<= 256)
+  constexpr int NQ = C / 4;               // channel quads
   constexpr int CP = C / 2, NG = 256 / CP;  // DW: channel pairs x column groups
+  static_assert(NRE <= 256, "one RE per thread");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* hf = reinterpret_cast<float2*>(smem_raw);                // [2][B][EW]
-  float* wt = reinterpret_cast<float*>(hf + 2 * NRX_MAX_RX * EW);  // [F][C]
-  float* kd = wt + (4 * NRX_MAX_RX + 2) * C;                       // [C][9]
-  float* feat = kd + 9 * C;                                        // [NRE][F]
-  float* h = feat + NRE * (4 * NRX_MAX_RX + 2);                    // [NRE][C]
+  float2* hf = reinterpret_cast<float2*>(smem_raw);  // [2][B][EW]
+  float* wt = reinterpret_cast<float*>(hf + 2 * B * EW);  // [F][C]
+  float* kd = wt + F * C;                                // [C][9]
+  float* bias = kd + 9 * C;                              // [C]
+  float* h = bias + C;  // [NRE][C], float4 chunk q of row r stored at q ^ (r & (NQ - 1))
 
-  const int tile = blockIdx.x, u = blockIdx.y, sl = blockIdx.z;
-  const int S = g.S, B = g.B, F = g.F;
-  const int s0 = tile * TW - 1;
-  const float2* ys = y + (size_t)sl * B * NRX_SYMBOLS * S;
   const int tid = threadIdx.x;
-
   for (int i = tid; i < F * C; i += 256) {
     const int c = i % C, f = i / C;
     wt[f * C + c] = __ldg(w_pw + c * F + f);
   }
   for (int i = tid; i < 9 * C; i += 256) kd[i] = __ldg(k_dw + i);
-  for (int i = tid; i < g.n_dmrs * B * EW; i += 256) {
-    const int e = i % EW, b = (i / EW) % B, d = i / (EW * B);
-    const int s = s0 + e;
-    float2 v = make_float2(0.f, 0.f);
-    if (s >= 0 && s < S) {
-      const int td = d == 0 ? g.td0 : g.td1;
-      v = ls_interp_freq(ys + ((size_t)b * NRX_SYMBOLS + td) * S, tab.dmrs[sl] + (size_t)d * (S / 2), u, g.U, S, s);
-    }
-    hf[(d * B + b) * EW + e] = v;
-  }
-  __syncthreads();
-  for (int i = tid; i < NRE; i += 256) {
-    const int t = i / EW, e = i % EW, s = s0 + e;
-    float* f = feat + i * F;
-    if (s < 0 || s >= S) {
-      for (int k = 0; k < F; ++k) f[k] = 0.f;
-      continue;
-    }
-    for (int b = 0; b < B; ++b) {
-      const float2 v = __ldg(ys + ((size_t)b * NRX_SYMBOLS + t) * S + s);
-      f[2 * b] = v.x;
-      f[2 * b + 1] = v.y;
-    }
-    for (int b = 0; b < B; ++b) {
-      const float2 hv = interp_time(g, t, hf[b * EW + e], hf[((g.n_dmrs - 1) * B + b) * EW + e]);
-      f[2 * B + 2 * b] = hv.x;
-      f[2 * B + 2 * b + 1] = hv.y;
-    }
-    f[4 * B] = pe_time(g, t);
-    f[4 * B + 1] = pe_freq(u, s);
-  }
-  __syncthreads();
-  // PW (+ bias), zero outside the grid: thread = channel quad cq, REs rg + RG*j.
-  {
-    const int cq = tid % CQ, rg = tid / CQ;
-    const float4 bias = __ldg(reinterpret_cast<const float4*>(b_pw) + cq);
-    for (int r0 = rg; r0 < NRE; r0 += 4 * RG) {
-      float4 acc[4];
-      int rr[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        acc[j] = bias;
-        rr[j] = r0 + j * RG < NRE ? r0 + j * RG : r0;
+  for (int i = tid; i < C; i += 256) bias[i] = __ldg(b_pw + i);
+  const int S = g.S;
+  const int tps = (S + TW - 1) / TW;
+  const int n_tiles = g.n_slots * g.U * tps;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int su = tile / tps, u = su % g.U, sl = su / g.U;
+    const int s0 = (tile % tps) * TW - 1;
+    const float2* ys = y + (size_t)sl * B * NRX_SYMBOLS * S;
+    __syncthreads();  // previous tile's readers of hf and h are done
+    for (int i = tid; i < g.n_dmrs * B * EW; i += 256) {
+      const int e = i % EW, b = (i / EW) % B, d = i / (EW * B);
+      const int s = s0 + e;
+      float2 v = make_float2(0.f, 0.f);
+      if (s >= 0 && s < S) {
+        const int td = d == 0 ? g.td0 : g.td1;
+        v = ls_interp_freq(ys + ((size_t)b * NRX_SYMBOLS + td) * S, tab.dmrs[sl] + (size_t)d * (S / 2), u, g.U, S, s);
       }
-      for (int k = 0; k < F; ++k) {
-        const float4 w = *reinterpret_cast<const float4*>(wt + k * C + 4 * cq);
+      hf[(d * B + b) * EW + e] = v;
+    }
+    __syncthreads();
+    // features of RE tid (registers) and the input layer, channel quad by quad
+    if (tid < NRE) {
+      const int t = tid / EW, e = tid % EW, s = s0 + e;
+      float4* hrow = reinterpret_cast<float4*>(h + tid * C);
+      if (s < 0 || s >= S) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float x = feat[rr[j] * F + k];
-          acc[j].x = fmaf(w.x, x, acc[j].x);
-          acc[j].y = fmaf(w.y, x, acc[j].y);
-          acc[j].z = fmaf(w.z, x, acc[j].z);
-          acc[j].w = fmaf(w.w, x, acc[j].w);
+        for (int q = 0; q < NQ; ++q) hrow[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        float x[F];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          const float2 v = __ldg(ys + ((size_t)b * NRX_SYMBOLS + t) * S + s);
+          x[2 * b] = v.x;
+          x[2 * b + 1] = v.y;
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          const float2 hv = interp_time(g, t, hf[b * EW + e], hf[((g.n_dmrs - 1) * B + b) * EW + e]);
+          x[2 * B + 2 * b] = hv.x;
+          x[2 * B + 2 * b + 1] = hv.y;
+        }
+        x[4 * B] = pe_time(g, t);
+        x[4 * B + 1] = pe_freq(u, s);
+#pragma unroll 4
+        for (int q = 0; q < NQ; ++q) {
+          float4 acc = *reinterpret_cast<const float4*>(bias + 4 * q);
+#pragma unroll
+          for (int k = 0; k < F; ++k) {
+            const float4 w = *reinterpret_cast<const float4*>(wt + k * C + 4 * q);  // same for all lanes
+            acc.x = fmaf(w.x, x[k], acc.x);
+            acc.y = fmaf(w.y, x[k], acc.y);
+            acc.z = fmaf(w.z, x[k], acc.z);
+            acc.w = fmaf(w.w, x[k], acc.w);
+          }
+          hrow[q ^ (tid & (NQ - 1))] = acc;
         }
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int r = r0 + j * RG;
-        if (r >= NRE) continue;
-        const int s = s0 + r % EW;
-        *reinterpret_cast<float4*>(h + r * C + 4 * cq) = (s >= 0 && s < S) ? acc[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
     }
-  }
-  __syncthreads();
-  // DW + ReLU: thread = channel pair cp, output columns x = cg, cg + NG, ...
-  {
-    const int cp = tid % CP, cg = tid / CP;
-    float2 kk[9];
+    __syncthreads();
+    // DW + ReLU: thread = channel pair cp, output columns x = cg, cg + NG, ...
+    {
+      const int cp = tid % CP, cg = tid / CP;
+      float2 kk[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) kk[i] = make_float2(kd[(2 * cp) * 9 + i], kd[(2 * cp + 1) * 9 + i]);
-    OutT* out_base = s_out + (((size_t)sl * g.U + u) * NRX_SYMBOLS) * S * C;
-    for (int x = cg; x < TW; x += NG) {
-      const int s = tile * TW + x;
-      if (s >= S) continue;
-      const float* col = h + x * C + 2 * cp;
-      tc::dw_column(
-          kk, [&](int ti, int k) { return *reinterpret_cast<const float2*>(col + (ti * EW + k) * C); },
-          [&](int t, float2 v) {
-            store_pair<OutT>(out_base + ((size_t)t * S + s) * C + 2 * cp, fmaxf(v.x, 0.f), fmaxf(v.y, 0.f));
-          });
+      for (int i = 0; i < 9; ++i) kk[i] = make_float2(kd[(2 * cp) * 9 + i], kd[(2 * cp + 1) * 9 + i]);
+      OutT* out_base = s_out + (size_t)su * NRX_SYMBOLS * S * C;
+      const int sx0 = (tile % tps) * TW;
+      for (int xc = cg; xc < TW; xc += NG) {
+        const int s = sx0 + xc;
+        if (s >= S) continue;
+        tc::dw_column(
+            kk,
+            [&](int ti, int k) {
+              const int r = ti * EW + xc + k;
+              return *reinterpret_cast<const float2*>(h + r * C + (((cp >> 1) ^ (r & (NQ - 1))) << 2) + (cp & 1) * 2);
+            },
+            [&](int t, float2 v) {
+              store_pair<OutT>(out_base + ((size_t)t * S + s) * C + 2 * cp, fmaxf(v.x, 0.f), fmaxf(v.y, 0.f));
+            });
+      }
     }
   }
 }
 
-size_t state_init_smem_bytes(int C) {
+size_t state_init_smem_bytes(int C, int B) {
   constexpr int EW = kStateInitTile + 2;
-  constexpr int F_MAX = 4 * NRX_MAX_RX + 2;
-  return sizeof(float2) * 2 * NRX_MAX_RX * EW + sizeof(float) * (F_MAX * C + 9 * C) +
-         sizeof(float) * NRX_SYMBOLS * EW * F_MAX + sizeof(float) * NRX_SYMBOLS * EW * C;
+  const int F = 4 * B + 2;
+  return sizeof(float2) * 2 * B * EW + sizeof(float) * ((size_t)F * C + 9 * C + C) +
+         sizeof(float) * NRX_SYMBOLS * EW * C;
 }
+
+namespace {
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+template <int C, int B, typename OutT>
+cudaError_t launch_si(const Geometry& g, const SlotTable& tab, const float2* y, const float* w_pw, const float* b_pw,
+                      const float* k_dw, OutT* s_out, cudaStream_t st) {
+  const size_t smem = state_init_smem_bytes(C, B);
+  cudaFuncSetAttribute(k_state_init<C, B, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = (int)((228 * 1024) / (smem + 1024));
+  if (per_sm > 4) per_sm = 4;
+  if (per_sm < 1) per_sm = 1;
+  const int tiles = g.n_slots * g.U * ((g.S + kStateInitTile - 1) / kStateInitTile);
+  const int grid = tiles < per_sm * sm_count() ? tiles : per_sm * sm_count();
+  k_state_init<C, B, OutT><<<grid, 256, smem, st>>>(g, tab, y, w_pw, b_pw, k_dw, s_out);
+  return cudaGetLastError();
+}
+
+template <int C, typename OutT>
+cudaError_t launch_si_b(const Geometry& g, const SlotTable& tab, const float2* y, const float* w_pw,
+                        const float* b_pw, const float* k_dw, OutT* s_out, cudaStream_t st) {
+  switch (g.B) {
+    case 1: return launch_si<C, 1, OutT>(g, tab, y, w_pw, b_pw, k_dw, s_out, st);
+    case 2: return launch_si<C, 2, OutT>(g, tab, y, w_pw, b_pw, k_dw, s_out, st);
+    case 4: return launch_si<C, 4, OutT>(g, tab, y, w_pw, b_pw, k_dw, s_out, st);
+    case 8: return launch_si<C, 8, OutT>(g, tab, y, w_pw, b_pw, k_dw, s_out, st);
+  }
+  return cudaErrorInvalidValue;
+}
+}  // namespace
 
 template <typename OutT>
 cudaError_t launch_state_init(const Geometry& g, const SlotTable& tab, const float2* y, const float* w_pw,
                               const float* b_pw, const float* k_dw, OutT* s_out, cudaStream_t st) {
-  dim3 grid((g.S + kStateInitTile - 1) / kStateInitTile, g.U, g.n_slots);
-  const size_t smem = state_init_smem_bytes(g.C);
-  if (g.C == 64) {
-    cudaFuncSetAttribute(k_state_init<64, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_state_init<64, OutT><<<grid, 256, smem, st>>>(g, tab, y, w_pw, b_pw, k_dw, s_out);
-  } else if (g.C == 32) {
-    cudaFuncSetAttribute(k_state_init<32, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_state_init<32, OutT><<<grid, 256, smem, st>>>(g, tab, y, w_pw, b_pw, k_dw, s_out);
-  } else {
-    return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  if (g.C == 64) return launch_si_b<64, OutT>(g, tab, y, w_pw, b_pw, k_dw, s_out, st);
+  if (g.C == 32) return launch_si_b<32, OutT>(g, tab, y, w_pw, b_pw, k_dw, s_out, st);
+  return cudaErrorInvalidValue;
 }
 template cudaError_t launch_state_init<float>(const Geometry&, const SlotTable&, const float2*, const float*,
                                               const float*, const float*, float*, cudaStream_t);

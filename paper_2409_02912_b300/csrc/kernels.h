@@ -41,7 +41,7 @@ struct IterWeightsF32 {
   const float* pw2_b[4];
 };
 
-size_t state_init_smem_bytes(int C);
+size_t state_init_smem_bytes(int C, int B);
 
 template <typename OutT>
 cudaError_t launch_state_init(const Geometry& g, const SlotTable& tab, const float2* y, const float* w_pw,
