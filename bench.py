@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["auto", "fp32", "bf16", "fp16"], default="auto")
+    ap.add_argument("--precision", choices=["auto", "fp32", "bf16", "fp16", "fp8"], default="auto")
     ap.add_argument("--no-extras", action="store_true", help="skip latency/compare/e2e/cpu legs")
     ap.add_argument("--batch", type=int, default=0, help="slots per step (0 = the workload's batch of 8)")
     return ap.parse_args()
@@ -310,7 +310,7 @@ def run_ours(args, rank, world, local):
         }
         # the other receivers on the same slots
         cmp = {}
-        for other in ("fp32", "bf16", "fp16"):
+        for other in ("fp32", "bf16", "fp16", "fp8"):
             if other == precision:
                 continue
             try:

@@ -94,8 +94,11 @@ typedef enum {
   NRX_BF16 = 1,  /* tensor-core GEMMs (tcgen05) on BF16 operands with FP32
                     accumulation, BF16 activations; each weight matrix is split
                     into two BF16 parts (hi + lo, two MMA passes) */
-  NRX_FP16 = 2   /* tensor-core GEMMs on FP16 operands with FP32 accumulation,
+  NRX_FP16 = 2,  /* tensor-core GEMMs on FP16 operands with FP32 accumulation,
                     FP16 activations (the paper's deployment precision, Sec. IV-A) */
+  NRX_FP8 = 3    /* tensor-core GEMMs on E4M3 operands (per-row activation scales,
+                    per-output-channel weight scales), FP32 accumulation, FP16
+                    activations and depthwise; error reported, not bounded */
 } nrx_precision;
 /* The tensor-core modes need C = 64 (NRX_EUNSUPPORTED otherwise).  In every
  * mode depthwise taps, biases, ReLU, the cross-user sum, residual adds and

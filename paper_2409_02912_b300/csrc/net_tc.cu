@@ -10,11 +10,14 @@
 // weights into shared memory once, and wait for MMA completion on an mbarrier
 // with a bounded wait: on timeout they set the context's error word, wait once
 // more for their own MMAs, release TMEM and return.
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
 #include "net_tc.h"
 #include "tc.cuh"
+#include <cuda_fp8.h>
 
 namespace {
 
@@ -48,17 +51,30 @@ constexpr uint32_t idesc() {
          ((uint32_t)(128 >> 4) << 24);
 }
 // Bytes of one packed weight matrix in shared memory (hi [+ lo]).
-template <typename T>
+template <typename P>
 constexpr int wbytes() {
-  return Op<T>::split ? 2 * 8192 : 8192;
+  return P::split ? 2 * 8192 : 8192;
 }
 
-// D (+)= A W^T for a 64 x 64 weight matrix at w_saddr (hi, then lo if split).
-template <typename T>
+// D (+)= A W^T for a 64 x 64 weight matrix at w_saddr: 16-bit operands (hi,
+// then lo if split), or E4M3 operands in the first 64 bytes of each row.
+template <typename P>
 __device__ __forceinline__ void gemm64(uint32_t d_tmem, uint32_t a_saddr, uint32_t w_saddr, bool accumulate_first) {
-  tc::mma_k64(d_tmem, a_saddr, w_saddr, idesc<T>(), accumulate_first);
-  if (Op<T>::split) tc::mma_k64(d_tmem, a_saddr, w_saddr + 8192, idesc<T>(), true);
+  if constexpr (P::fp8) {
+    tc::mma_k64_f8(d_tmem, a_saddr, w_saddr, accumulate_first);
+  } else {
+    using T = typename P::T;
+    tc::mma_k64(d_tmem, a_saddr, w_saddr, idesc<T>(), accumulate_first);
+    if constexpr (P::split) tc::mma_k64(d_tmem, a_saddr, w_saddr + 8192, idesc<T>(), true);
+  }
 }
+
+// E4M3 pair (lo = a, hi = b) of two FP32 values.
+__device__ __forceinline__ uint32_t e4m3x2(float a, float b) {
+  return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+}
+// Per-row E4M3 scale from the row's absolute maximum: values / s fit 448.
+__device__ __forceinline__ float e4m3_scale(float amax) { return amax > 0.f ? amax * (1.f / 448.f) : 1.f; }
 constexpr int kTileBytes = 16384;  // 128 x 64 16-bit operand tile
 
 int num_sms() {
@@ -77,11 +93,11 @@ __device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
   return reinterpret_cast<unsigned char*>(a);
 }
 
-// Copy a pre-packed weight matrix (wbytes<T>() bytes) into shared memory.
-template <typename T>
+// Copy a pre-packed weight matrix (wbytes<P>() bytes) into shared memory.
+template <typename P>
 __device__ __forceinline__ void load_wtile(unsigned char* dst, const uint4* __restrict__ src) {
   uint4* d = reinterpret_cast<uint4*>(dst);
-  for (int i = threadIdx.x; i < wbytes<T>() / 16; i += blockDim.x) d[i] = __ldg(src + i);
+  for (int i = threadIdx.x; i < wbytes<P>() / 16; i += blockDim.x) d[i] = __ldg(src + i);
 }
 
 template <typename T>
@@ -165,40 +181,51 @@ __device__ __forceinline__ void tc_teardown(TcCta& c, uint32_t ncols, bool timed
 // Epilogues use all 8 warps (warp w: TMEM lanes 32 (w & 3), column half w >> 2);
 // z rows are staged in shared memory and stored 8 threads per row.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename P>
 struct MpLayout {
   static constexpr int A_S = 0;
   static constexpr int A_G = 16384;
   static constexpr int XCH = 32768;  // FP32 [128][64] exchange of h; later 16-bit z staging
   static constexpr int W1 = 65536;
-  static constexpr int WS = W1 + wbytes<T>();
-  static constexpr int WC = WS + wbytes<T>();
-  static constexpr int VEC = WC + wbytes<T>();  // b1, bin, cb2, pe_t, pe_f: 5 x 64 floats
-  static constexpr int BAR = VEC + 5 * 64 * 4;
+  static constexpr int WS = W1 + wbytes<P>();
+  static constexpr int WC = WS + wbytes<P>();
+  static constexpr int VEC = WC + wbytes<P>();  // b1, bin, -, pe_t, pe_f, sW1, sWS, sWC: 8 x 64 floats
+  static constexpr int RSC = VEC + 8 * 64 * 4;   // E4M3 row scales of A_S and A_G: 2 x 128 floats
+  static constexpr int BAR = RSC + 256 * 4;
   static constexpr int TOTAL = BAR + 16;
   static constexpr int DYN = TOTAL + 1024;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC w, const T* __restrict__ state,
-                                                       T* __restrict__ z, int nre, int tiles_per_slot) {
-  using MpL = MpLayout<T>;
+template <typename P>
+__global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC w,
+                                                       const typename P::T* __restrict__ state,
+                                                       typename P::T* __restrict__ z, int nre, int tiles_per_slot) {
+  using T = typename P::T;
+  using MpL = MpLayout<P>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = align1024(smem_raw);
   float* vec = reinterpret_cast<float*>(sm + MpL::VEC);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  load_wtile<T>(sm + MpL::W1, w.mp1);
-  load_wtile<T>(sm + MpL::WS, w.in_s);
-  load_wtile<T>(sm + MpL::WC, w.in_c);
+  load_wtile<P>(sm + MpL::W1, w.mp1);
+  load_wtile<P>(sm + MpL::WS, w.in_s);
+  load_wtile<P>(sm + MpL::WC, w.in_c);
   const int U = g.U, S = g.S;
   for (int i = tid; i < 64; i += kThreads) {
     vec[i] = __ldg(w.mp1_b + i);
     vec[64 + i] = __ldg(w.in_b + i) + (float)(U - 1) * __ldg(w.cb2 + i);
     vec[192 + i] = __ldg(w.in_pe + i);
     vec[256 + i] = __ldg(w.in_pe + 64 + i);
+    if constexpr (P::fp8) {
+      vec[320 + i] = __ldg(w.mp1_sc + i);
+      vec[384 + i] = __ldg(w.in_s_sc + i);
+      vec[448 + i] = __ldg(w.in_c_sc + i);
+    }
   }
+  float* rsc_s = reinterpret_cast<float*>(sm + MpL::RSC);  // row scales of A_S (FP8)
+  float* rsc_g = rsc_s + 128;                               // row scales of A_G (FP8)
   TcCta c;
-  tc_setup(c, reinterpret_cast<uint64_t*>(sm + MpL::BAR), reinterpret_cast<uint32_t*>(sm + MpL::BAR + 8), 128);
+  tc_setup(c, reinterpret_cast<uint64_t*>(sm + MpL::BAR), reinterpret_cast<uint32_t*>(sm + MpL::BAR + 8),
+           P::fp8 ? 256 : 128);
   const uint32_t sa_s = tc::smem_u32(sm + MpL::A_S), sa_g = tc::smem_u32(sm + MpL::A_G);
   const uint32_t sw1 = tc::smem_u32(sm + MpL::W1), sws = tc::smem_u32(sm + MpL::WS),
                  swc = tc::smem_u32(sm + MpL::WC);
@@ -229,8 +256,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
       for (int it = 0; it < 4; ++it) {
         const int i = tid + it * kThreads;
         const int row = i >> 3, ch = i & 7;
-        *reinterpret_cast<uint4*>(sm + MpL::A_S + (row >> 3) * 1024 + (row & 7) * 128 + ((ch ^ (row & 7)) << 4)) =
-            v[it];
+        if constexpr (P::fp8) {
+          // E4M3 with a per-row scale: the row's 8 chunks sit in 8 consecutive lanes
+          float f[8];
+          const uint32_t wv[4] = {v[it].x, v[it].y, v[it].z, v[it].w};
+          float am = 0.f;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float2 x = Op<T>::unpack(wv[k]);
+            f[2 * k] = x.x;
+            f[2 * k + 1] = x.y;
+            am = fmaxf(am, fmaxf(fabsf(x.x), fabsf(x.y)));
+          }
+          am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 1));
+          am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 2));
+          am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 4));
+          const float sc = e4m3_scale(am), inv = 1.f / sc;
+          const uint2 q = make_uint2(e4m3x2(f[0] * inv, f[1] * inv) | (e4m3x2(f[2] * inv, f[3] * inv) << 16),
+                                     e4m3x2(f[4] * inv, f[5] * inv) | (e4m3x2(f[6] * inv, f[7] * inv) << 16));
+          *reinterpret_cast<uint2*>(sm + MpL::A_S + (row >> 3) * 1024 + (row & 7) * 128 +
+                                    (((ch >> 1) ^ (row & 7)) << 4) + (ch & 1) * 8) = q;
+          if (ch == 0) rsc_s[row] = sc;
+        } else {
+          *reinterpret_cast<uint4*>(sm + MpL::A_S + (row >> 3) * 1024 + (row & 7) * 128 + ((ch ^ (row & 7)) << 4)) =
+              v[it];
+        }
       }
     }
     {  // L2 prefetch of the next tile's rows
@@ -245,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
     __syncthreads();
     if (tid == 0) {
       tc::tc_fence_after();
-      gemm64<T>(c.tmem, sa_s, sw1, false);
+      gemm64<P>(c.tmem, sa_s, sw1, false);
       tc::mma_commit(c.bar);
     }
     if (!tc_wait(c, w.err)) {
@@ -261,22 +311,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
       tc::tmem_wait16(a);
       tc::tmem_wait16(b);
       const float* b1 = vec + 32 * hc;
+      float sc[32];  // dequantisation factor per column (1 unless FP8)
+#pragma unroll
+      for (int e = 0; e < 32; ++e) sc[e] = 1.f;
+      if constexpr (P::fp8) {
+        const float rs = rsc_s[r];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) sc[e] = rs * vec[320 + 32 * hc + e];
+      }
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const uint32_t* src = k < 4 ? a + 4 * k : b + 4 * (k - 4);
         const int kk = 8 * hc + k;
         *reinterpret_cast<float4*>(xch + r * 64 + ((kk ^ (r & 7)) << 2)) =
-            make_float4(fmaxf(__uint_as_float(src[0]) + b1[4 * k], 0.f),
-                        fmaxf(__uint_as_float(src[1]) + b1[4 * k + 1], 0.f),
-                        fmaxf(__uint_as_float(src[2]) + b1[4 * k + 2], 0.f),
-                        fmaxf(__uint_as_float(src[3]) + b1[4 * k + 3], 0.f));
+            make_float4(fmaxf(fmaf(__uint_as_float(src[0]), sc[4 * k], b1[4 * k]), 0.f),
+                        fmaxf(fmaf(__uint_as_float(src[1]), sc[4 * k + 1], b1[4 * k + 1]), 0.f),
+                        fmaxf(fmaf(__uint_as_float(src[2]), sc[4 * k + 2], b1[4 * k + 2]), 0.f),
+                        fmaxf(fmaf(__uint_as_float(src[3]), sc[4 * k + 3], b1[4 * k + 3]), 0.f));
       }
     }
     tc::tc_fence_before();
     __syncthreads();
-    // g_u = sum over the other active users -> A_G (16-bit, SW128)
-    for (int i = tid; i < nre * 16; i += kThreads) {
-      const int j = i >> 4, cq = i & 15;
+    // g_u = sum over the other active users -> A_G (SW128).  Items (j, channel
+    // quad cq); the loop is warp-uniform so FP8 can reduce a row over 16 lanes.
+    for (int i0 = 0; i0 < nre * 16; i0 += kThreads) {
+      const int i = i0 + tid;
+      const bool valid = i < nre * 16;
+      const int j = valid ? i >> 4 : 0, cq = i & 15;
       float4 hv[NRX_MAX_USERS];
 #pragma unroll
       for (int u = 0; u < NRX_MAX_USERS; ++u) {
@@ -297,8 +358,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
             a.w += hv[v].w;
           }
         const int row = u * nre + j;
-        *reinterpret_cast<uint2*>(sm + MpL::A_G + tc::sw128_offset(row, 4 * cq)) =
-            make_uint2(Op<T>::pack(a.x, a.y), Op<T>::pack(a.z, a.w));
+        if constexpr (P::fp8) {
+          float am = fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w)));
+#pragma unroll
+          for (int o = 1; o < 16; o <<= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+          const float sc = e4m3_scale(am), inv = 1.f / sc;
+          if (valid) {
+            *reinterpret_cast<uint32_t*>(sm + MpL::A_G + (row >> 3) * 1024 + (row & 7) * 128 +
+                                         (((cq >> 2) ^ (row & 7)) << 4) + (cq & 3) * 4) =
+                e4m3x2(a.x * inv, a.y * inv) | (e4m3x2(a.z * inv, a.w * inv) << 16);
+            if (cq == 0) rsc_g[row] = sc;
+          }
+        } else if (valid) {
+          *reinterpret_cast<uint2*>(sm + MpL::A_G + tc::sw128_offset(row, 4 * cq)) =
+              make_uint2(Op<T>::pack(a.x, a.y), Op<T>::pack(a.z, a.w));
+        }
       }
     }
     // rows of A_G not covered by (u < U, j < nre) only feed rows that are never stored
@@ -306,8 +380,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
     __syncthreads();
     if (tid == 0) {
       tc::tc_fence_after();
-      gemm64<T>(c.tmem + 64, sa_s, sws, false);
-      gemm64<T>(c.tmem + 64, sa_g, swc, true);
+      gemm64<P>(c.tmem + 64, sa_s, sws, false);
+      // FP8: the two products carry different scales -> separate accumulators
+      gemm64<P>(c.tmem + (P::fp8 ? 128 : 64), sa_g, swc, !P::fp8);
       tc::mma_commit(c.bar);
     }
     if (!tc_wait(c, w.err)) {
@@ -322,6 +397,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
       tc::tmem_ld16(c.tmem + 64 + tlane + 32 * hc + 16, b);
       tc::tmem_wait16(a);
       tc::tmem_wait16(b);
+      float acc[32];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        acc[e] = __uint_as_float(a[e]);
+        acc[16 + e] = __uint_as_float(b[e]);
+      }
+      if constexpr (P::fp8) {  // z = accS sS[r] sWS + accG sG[r] sWC
+        uint32_t ga[16], gb[16];
+        tc::tmem_ld16(c.tmem + 128 + tlane + 32 * hc, ga);
+        tc::tmem_ld16(c.tmem + 128 + tlane + 32 * hc + 16, gb);
+        tc::tmem_wait16(ga);
+        tc::tmem_wait16(gb);
+        const float rs = rsc_s[r], rg = rsc_g[r];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          const float gv = __uint_as_float(e < 16 ? ga[e] : gb[e - 16]);
+          acc[e] = acc[e] * (rs * vec[384 + 32 * hc + e]) + gv * (rg * vec[448 + 32 * hc + e]);
+        }
+      }
       const int u = r / nre, j = r % nre, re = re0 + j;
       float pt = 0.f, pf = 0.f;
       if (u < U && re < n_re) {
@@ -338,8 +432,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const int cc = 8 * k + e;
-          const uint32_t raw = cc < 16 ? a[cc] : b[cc - 16];
-          o[e] = __uint_as_float(raw) + bb[cc] + pt * wt[cc] + pf * wf[cc];
+          o[e] = acc[cc] + bb[cc] + pt * wt[cc] + pf * wf[cc];
         }
         const int kk = 4 * hc + k;
         *reinterpret_cast<uint4*>(rowp + ((kk ^ (r & 7)) << 4)) = pack8<T>(o);
@@ -359,7 +452,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
     }
     __syncthreads();
   }
-  tc_teardown(c, 128, timed_out);
+  tc_teardown(c, P::fp8 ? 256 : 128, timed_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -372,20 +465,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
 //   PW2 MMA -> TMEM [128,256); epilogue +b2 + residual -> z_out, or S += (last)
 // P1 [t][16 columns][64 ch] stores 16-byte chunk k of a row at k ^ (t & 7).
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename P>
 struct BlkLayout {
   static constexpr int TW = 14;
   static constexpr int IW = TW + 4;  // input columns
   static constexpr int MW = TW + 2;  // DW1 / PW1 columns
   static constexpr int A = 0;        // 2 x 16 KB
   static constexpr int W1 = 32768;
-  static constexpr int W2 = W1 + wbytes<T>();
-  static constexpr int ZB = W2 + wbytes<T>();  // [14][IW][64] input tile; later P1 [14][MW][64]
+  static constexpr int W2 = W1 + wbytes<P>();
+  static constexpr int ZB = W2 + wbytes<P>();  // [14][IW][64] input tile; later P1 [14][MW][64]
   static constexpr int K1 = ZB + NRX_SYMBOLS * IW * 128;
   static constexpr int K2 = K1 + 64 * 9 * 4;
   static constexpr int B1 = K2 + 64 * 9 * 4;
   static constexpr int B2 = B1 + 256;
-  static constexpr int BAR = B2 + 256;
+  static constexpr int SW = B2 + 256;       // E4M3 weight scales: W1, W2 (2 x 64 floats)
+  static constexpr int RS = SW + 512;       // E4M3 row scales of the A tiles (256 floats)
+  static constexpr int BAR = RS + 1024;
   static constexpr int TOTAL = BAR + 16;
   static constexpr int DYN = TOTAL + 1024;
 };
@@ -428,21 +523,39 @@ __device__ __forceinline__ void dw_2col(const Acc (&kk)[9], Acc zero, In in, Fma
 __device__ __forceinline__ __half2 h2_from_u32(uint32_t w) { return *reinterpret_cast<__half2*>(&w); }
 __device__ __forceinline__ uint32_t u32_from_h2(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
 
-template <typename T>
+// FP8 operand write of one A-tile row whose 64 channels are spread over a
+// warp (lane cp holds channels 2 cp, 2 cp + 1): row scale from the warp-wide
+// absolute maximum, E4M3 pair stored at logical byte 2 cp of the row (rows
+// t of a 16-row column block at col_base), lane 0 records the scale.
+__device__ __forceinline__ void store_e4m3_row_pair(unsigned char* col_base, int t, int cp, float2 v, float* scale) {
+  float am = fmaxf(fabsf(v.x), fabsf(v.y));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+  const float sc = e4m3_scale(am), inv = 1.f / sc;
+  *reinterpret_cast<uint16_t*>(col_base + (t >> 3) * 1024 + (t & 7) * 128 + (((cp >> 3) ^ (t & 7)) << 4) +
+                               ((2 * cp) & 15)) = (uint16_t)e4m3x2(v.x * inv, v.y * inv);
+  if (cp == 0) *scale = sc;
+}
+
+template <typename P>
 __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint4* __restrict__ w1p,
                                                            const uint4* __restrict__ w2p,
                                                            const float* __restrict__ b1,
                                                            const float* __restrict__ b2,
                                                            const float* __restrict__ k1g,
                                                            const float* __restrict__ k2g,
-                                                           const T* __restrict__ z_in, T* __restrict__ z_out,
-                                                           T* __restrict__ state, int last, int* err) {
-  using L = BlkLayout<T>;
+                                                           const float* __restrict__ w1s,
+                                                           const float* __restrict__ w2s,
+                                                           const typename P::T* __restrict__ z_in,
+                                                           typename P::T* __restrict__ z_out,
+                                                           typename P::T* __restrict__ state, int last, int* err) {
+  using T = typename P::T;
+  using L = BlkLayout<P>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = align1024(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  load_wtile<T>(sm + L::W1, w1p);
-  load_wtile<T>(sm + L::W2, w2p);
+  load_wtile<P>(sm + L::W1, w1p);
+  load_wtile<P>(sm + L::W2, w2p);
   float* sk1 = reinterpret_cast<float*>(sm + L::K1);
   float* sk2 = reinterpret_cast<float*>(sm + L::K2);
   float* sb1 = reinterpret_cast<float*>(sm + L::B1);
@@ -451,10 +564,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
     sk1[i] = __ldg(k1g + i);
     sk2[i] = __ldg(k2g + i);
   }
+  float* ssw = reinterpret_cast<float*>(sm + L::SW);  // [2][64] weight scales (FP8)
+  float* srs = reinterpret_cast<float*>(sm + L::RS);  // [256] A-tile row scales (FP8)
   for (int i = tid; i < 64; i += kThreads) {
     sb1[i] = __ldg(b1 + i);
     sb2[i] = __ldg(b2 + i);
+    if constexpr (P::fp8) {
+      ssw[i] = __ldg(w1s + i);
+      ssw[64 + i] = __ldg(w2s + i);
+    }
   }
+  if constexpr (P::fp8)
+    for (int i = tid; i < 256; i += kThreads) srs[i] = 1.f;
   // zero the A tiles once: padding rows (t = 14, 15) are never written
   for (int i = tid; i < 2 * kTileBytes / 16; i += kThreads) reinterpret_cast<uint4*>(sm + L::A)[i] = make_uint4(0, 0, 0, 0);
   TcCta c;
@@ -524,7 +645,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
         *reinterpret_cast<uint32_t*>(dst + o * 2048 + (t >> 3) * 1024 + (t & 7) * 128 + ((cpc ^ (t & 7)) << 4) +
                                      cpl * 4) = word;
       };
-      if constexpr (Op<T>::split) {  // BF16 operands: FP32 packed FMAs
+      if constexpr (P::split) {  // BF16 operands: FP32 packed FMAs
         float2 k1[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) k1[i] = make_float2(sk1[(2 * cp) * 9 + i], sk1[(2 * cp + 1) * 9 + i]);
@@ -532,22 +653,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
             k1, make_float2(0.f, 0.f), [&](int ti, int k) { return Op<T>::unpack(col[(ti * L::IW + k) * 32]); },
             [](float2 a, float2 b, float2 c2) { return tc::ffma2(a, b, c2); },
             [&](int t, int o, float2 v) { store(t, o, Op<T>::pack(v.x, v.y)); });
-      } else {  // FP16 operands: packed FP16 FMAs
+      } else {  // FP16 storage: packed FP16 FMAs
         __half2 k1[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) k1[i] = __floats2half2_rn(sk1[(2 * cp) * 9 + i], sk1[(2 * cp + 1) * 9 + i]);
         dw_2col(
             k1, __float2half2_rn(0.f), [&](int ti, int k) { return h2_from_u32(col[(ti * L::IW + k) * 32]); },
             [](__half2 a, __half2 b, __half2 c2) { return __hfma2(a, b, c2); },
-            [&](int t, int o, __half2 v) { store(t, o, u32_from_h2(v)); });
+            [&](int t, int o, __half2 v) {
+              if constexpr (P::fp8) {
+                store_e4m3_row_pair(dst + o * 2048, t, cp, __half22float2(v), srs + (e + o) * 16 + t);
+              } else {
+                store(t, o, u32_from_h2(v));
+              }
+            });
       }
     }
     tc::fence_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc::tc_fence_after();
-      gemm64<T>(c.tmem, sa, sw1, false);
-      gemm64<T>(c.tmem + 64, sa + kTileBytes, sw1, false);
+      gemm64<P>(c.tmem, sa, sw1, false);
+      gemm64<P>(c.tmem + 64, sa + kTileBytes, sw1, false);
       tc::mma_commit(c.bar);
     }
     if (!tc_wait(c, err)) {
@@ -560,6 +687,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
       tc::tmem_row64(c.tmem + mt * 64 + ((uint32_t)(q * 32) << 16), v);
       const int s = s0 - 1 + rcol;
       const bool inside = s >= 0 && s < S;
+      if constexpr (P::fp8) {
+        const float rs = srs[row];
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] *= rs * ssw[k];
+      }
       if (rt < NRX_SYMBOLS) {
         uint4* dst = reinterpret_cast<uint4*>(sm + L::ZB + (rt * L::MW + rcol) * 128);
 #pragma unroll
@@ -584,7 +716,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
                                      cpl * 4) = word;
       };
       auto load = [&](int ti, int k) { return col[(ti * L::MW + k) * 32 + ((cpc ^ (ti & 7)) << 2)]; };
-      if constexpr (Op<T>::split) {
+      if constexpr (P::split) {
         float2 k2[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) k2[i] = make_float2(sk2[(2 * cp) * 9 + i], sk2[(2 * cp + 1) * 9 + i]);
@@ -600,15 +732,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
         dw_2col(
             k2, hz, [&](int ti, int k) { return h2_from_u32(load(ti, k)); },
             [](__half2 a, __half2 b, __half2 c2) { return __hfma2(a, b, c2); },
-            [&](int t, int o, __half2 v) { store(t, o, u32_from_h2(__hmax2(v, hz))); });
+            [&](int t, int o, __half2 v) {
+              if constexpr (P::fp8) {
+                store_e4m3_row_pair(dst + o * 2048, t, cp, __half22float2(__hmax2(v, hz)), srs + (x + o) * 16 + t);
+              } else {
+                store(t, o, u32_from_h2(__hmax2(v, hz)));
+              }
+            });
       }
     }
     tc::fence_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc::tc_fence_after();
-      gemm64<T>(c.tmem + 128, sa, sw2, false);
-      gemm64<T>(c.tmem + 192, sa + kTileBytes, sw2, false);
+      gemm64<P>(c.tmem + 128, sa, sw2, false);
+      gemm64<P>(c.tmem + 192, sa + kTileBytes, sw2, false);
       tc::mma_commit(c.bar);
     }
     if (!tc_wait(c, err)) {
@@ -621,6 +759,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
     {
       float v[64];
       tc::tmem_row64(c.tmem + 128 + mt * 64 + ((uint32_t)(q * 32) << 16), v);
+      if constexpr (P::fp8) {
+        const float rs = srs[row];
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] *= rs * ssw[64 + k];
+      }
       if (rt < NRX_SYMBOLS && rcol < L::TW) {
         const int sr = rcol * NRX_SYMBOLS + rt;
         float4* dst = reinterpret_cast<float4*>(sr < 128 ? sm + L::A + sr * 256 : sm + L::ZB + (sr - 128) * 256);
@@ -686,33 +829,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
 // ReadoutLLRs + masking: 128 data REs of one (slot, user) per tile;
 // h = ReLU(S W_o1^T + b) by MMA, then the m_u outputs on the CUDA cores.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename P>
 struct RoLayout {
   static constexpr int A = 0;
   static constexpr int W1 = kTileBytes;
-  static constexpr int W2F = W1 + wbytes<T>();  // [8][64] FP32
+  static constexpr int W2F = W1 + wbytes<P>();  // [8][64] FP32
   static constexpr int B1 = W2F + 8 * 64 * 4;
   static constexpr int B2 = B1 + 256;
-  static constexpr int BAR = B2 + 64;
+  static constexpr int SC = B2 + 64;   // E4M3: weight scales [64], row scales [128]
+  static constexpr int BAR = SC + 192 * 4;
   static constexpr int TOTAL = BAR + 16;
   static constexpr int DYN = TOTAL + 1024;
 };
 
-template <typename T>
+template <typename P>
 __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, ReadoutWeightsTC w,
-                                                    const T* __restrict__ state, float* __restrict__ llr,
+                                                    const typename P::T* __restrict__ state, float* __restrict__ llr,
                                                     int tiles_per_su) {
-  using L = RoLayout<T>;
+  using T = typename P::T;
+  using L = RoLayout<P>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = align1024(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  load_wtile<T>(sm + L::W1, w.ro1);
+  load_wtile<P>(sm + L::W1, w.ro1);
   float* w2 = reinterpret_cast<float*>(sm + L::W2F);
   float* sb1 = reinterpret_cast<float*>(sm + L::B1);
   float* sb2 = reinterpret_cast<float*>(sm + L::B2);
   for (int i = tid; i < g.m_max * 64; i += blockDim.x) w2[i] = __ldg(w.ro2 + i);
   for (int i = tid; i < 64; i += blockDim.x) sb1[i] = __ldg(w.ro1_b + i);
   for (int i = tid; i < g.m_max; i += blockDim.x) sb2[i] = __ldg(w.ro2_b + i);
+  float* ssc = reinterpret_cast<float*>(sm + L::SC);  // [64] weight scales, then [128] row scales
+  if constexpr (P::fp8)
+    for (int i = tid; i < 64; i += blockDim.x) ssc[i] = __ldg(w.ro1_sc + i);
   TcCta c;
   tc_setup(c, reinterpret_cast<uint64_t*>(sm + L::BAR), reinterpret_cast<uint32_t*>(sm + L::BAR + 8), 64);
   const uint32_t sa = tc::smem_u32(sm + L::A), sw1 = tc::smem_u32(sm + L::W1);
@@ -740,14 +888,36 @@ __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, R
       for (int it = 0; it < 8; ++it) {
         const int i = tid + it * 128;
         const int rw = i >> 3, ch = i & 7;
-        *reinterpret_cast<uint4*>(sm + L::A + (rw >> 3) * 1024 + (rw & 7) * 128 + ((ch ^ (rw & 7)) << 4)) = v[it];
+        if constexpr (P::fp8) {
+          float f[8];
+          const uint32_t wv[4] = {v[it].x, v[it].y, v[it].z, v[it].w};
+          float am = 0.f;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float2 x = Op<T>::unpack(wv[k]);
+            f[2 * k] = x.x;
+            f[2 * k + 1] = x.y;
+            am = fmaxf(am, fmaxf(fabsf(x.x), fabsf(x.y)));
+          }
+          am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 1));
+          am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 2));
+          am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 4));
+          const float sc = e4m3_scale(am), inv = 1.f / sc;
+          *reinterpret_cast<uint2*>(sm + L::A + (rw >> 3) * 1024 + (rw & 7) * 128 + (((ch >> 1) ^ (rw & 7)) << 4) +
+                                    (ch & 1) * 8) =
+              make_uint2(e4m3x2(f[0] * inv, f[1] * inv) | (e4m3x2(f[2] * inv, f[3] * inv) << 16),
+                         e4m3x2(f[4] * inv, f[5] * inv) | (e4m3x2(f[6] * inv, f[7] * inv) << 16));
+          if (ch == 0) ssc[64 + rw] = sc;
+        } else {
+          *reinterpret_cast<uint4*>(sm + L::A + (rw >> 3) * 1024 + (rw & 7) * 128 + ((ch ^ (rw & 7)) << 4)) = v[it];
+        }
       }
     }
     tc::fence_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc::tc_fence_after();
-      gemm64<T>(c.tmem, sa, sw1, false);
+      gemm64<P>(c.tmem, sa, sw1, false);
       tc::mma_commit(c.bar);
     }
     if (!tc_wait(c, w.err)) {
@@ -758,6 +928,11 @@ __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, R
     tc::tmem_row64(c.tmem + ((uint32_t)(warp * 32) << 16), h);
     const int rd = r0 + row;
     if (rd < g.n_data) {
+      if constexpr (P::fp8) {
+        const float rs = ssc[64 + row];
+#pragma unroll
+        for (int k = 0; k < 64; ++k) h[k] *= rs * ssc[k];
+      }
 #pragma unroll
       for (int k = 0; k < 64; ++k) h[k] = fmaxf(h[k] + sb1[k], 0.f);
       const int m = tab.bits[sl][u];
@@ -816,12 +991,33 @@ void pack_sw128(const float* M, unsigned char* dst, bool bf16) {
     }
 }
 
+// E4M3 image: row n holds W[n][k] / s_n in its first 64 (logical) bytes, s_n =
+// max_k |W[n][k]| / 448 stored in scale[n]; the other 64 bytes stay zero.
+void pack_sw128_e4m3(const float* M, unsigned char* dst, float* scale) {
+  for (int n = 0; n < 64; ++n) {
+    float am = 0.f;
+    for (int k = 0; k < 64; ++k) am = std::max(am, std::fabs(M[n * 64 + k]));
+    const float s = am > 0.f ? am / 448.f : 1.f;
+    scale[n] = s;
+    for (int k = 0; k < 64; ++k) {
+      const unsigned char q = (unsigned char)__nv_cvt_float_to_fp8(M[n * 64 + k] / s, __NV_SATFINITE, __NV_E4M3);
+      dst[(size_t)(n >> 3) * 1024 + (n & 7) * 128 + (((k >> 4) ^ (n & 7)) << 4) + (k & 15)] = q;
+    }
+  }
+}
+
 // One weight matrix W[n][col0 .. col0+63] (row stride ld) -> packed image(s):
-// FP16: one image; BF16: hi image then lo = bf16(W - hi) image.
-void pack_weight(const float* W, int ld, int col0, unsigned char* dst, bool bf16) {
+// FP16: one image; BF16: hi image then lo = bf16(W - hi) image; FP8: one E4M3
+// image plus 64 per-row scales.
+void pack_weight(const float* W, int ld, int col0, unsigned char* dst, int mode, float* scale) {
   float m[64 * 64];
   for (int n = 0; n < 64; ++n)
     for (int k = 0; k < 64; ++k) m[n * 64 + k] = W[(size_t)n * ld + col0 + k];
+  if (mode == 2) {
+    pack_sw128_e4m3(m, dst, scale);
+    return;
+  }
+  const bool bf16 = mode == 1;
   pack_sw128(m, dst, bf16);
   if (bf16) {
     float lo[64 * 64];
@@ -842,25 +1038,31 @@ int grid_for(int smem, int max_per_sm, int tiles) {
 
 }  // namespace
 
-nrx_status upload_tc_weights(bool bf16, int C, int R, int N_it, const std::vector<const float*>& blob_it,
+nrx_status upload_tc_weights(int mode, int C, int R, int N_it, const std::vector<const float*>& blob_it,
                              const float* ro1w, const std::vector<IterWeightsF32>& it32, const float* ro1_b_dev,
                              const float* ro2_dev, const float* ro2_b_dev, std::vector<IterWeightsTC>* out,
                              void** dev_alloc, ReadoutWeightsTC* ro, int** err_word) {
   if (C != 64) return NRX_EUNSUPPORTED;
-  const size_t wb = bf16 ? 2 * 8192 : 8192;
+  const size_t wb = mode == 1 ? 2 * 8192 : 8192;
   const int per_it = 3 + 2 * R;  // mp1, in_s, in_c, then pw1/pw2 per block
   const size_t n_mats = (size_t)N_it * per_it + 1;
-  const size_t cb2_off = n_mats * wb;                    // N_it x C floats
-  const size_t err_off = cb2_off + (size_t)N_it * C * 4;  // one int
+  const size_t cb2_off = n_mats * wb;                         // N_it x C floats
+  const size_t sc_off = cb2_off + (size_t)N_it * C * 4;        // n_mats x 64 E4M3 scales
+  const size_t err_off = sc_off + n_mats * 64 * 4;             // one int
   std::vector<unsigned char> host(err_off + 256, 0);
   float* cb2_host = reinterpret_cast<float*>(host.data() + cb2_off);
+  float* sc_host = reinterpret_cast<float*>(host.data() + sc_off);
   size_t t = 0;
+  auto put = [&](const float* W, int ld, int col0) {
+    pack_weight(W, ld, col0, host.data() + t * wb, mode, sc_host + t * 64);
+    ++t;
+  };
   const size_t per_blob = 6 + 6 * R;
   for (int k = 0; k < N_it; ++k) {
     const float* const* b = blob_it.data() + k * per_blob;  // mp1w, mp1b, mp2w, mp2b, inw, inb, blocks
     const int ld = 2 * C + 2;
-    pack_weight(b[0], C, 0, host.data() + (t++) * wb, bf16);   // mp1
-    pack_weight(b[4], ld, 0, host.data() + (t++) * wb, bf16);  // in, S columns
+    put(b[0], C, 0);   // mp1
+    put(b[4], ld, 0);  // in, S columns
     // Win_a W2 and Win_a b2 in FP64 (the message output layer folded in)
     std::vector<float> wc((size_t)C * C);
     for (int n = 0; n < C; ++n) {
@@ -873,14 +1075,14 @@ nrx_status upload_tc_weights(bool bf16, int C, int R, int N_it, const std::vecto
       }
       cb2_host[(size_t)k * C + n] = (float)cb;
     }
-    pack_weight(wc.data(), C, 0, host.data() + (t++) * wb, bf16);  // in_c
+    put(wc.data(), C, 0);  // in_c
     for (int r = 0; r < R; ++r) {
       const float* const* blk = b + 6 + 6 * r;
-      pack_weight(blk[1], C, 0, host.data() + (t++) * wb, bf16);  // pw1
-      pack_weight(blk[4], C, 0, host.data() + (t++) * wb, bf16);  // pw2
+      put(blk[1], C, 0);  // pw1
+      put(blk[4], C, 0);  // pw2
     }
   }
-  pack_weight(ro1w, C, 0, host.data() + (t++) * wb, bf16);
+  put(ro1w, C, 0);
   void* d = nullptr;
   if (cudaMalloc(&d, host.size()) != cudaSuccess) {
     cudaGetLastError();
@@ -894,22 +1096,29 @@ nrx_status upload_tc_weights(bool bf16, int C, int R, int N_it, const std::vecto
   unsigned char* base = static_cast<unsigned char*>(d);
   int* err = reinterpret_cast<int*>(base + err_off);
   *err_word = err;
+  const float* scd = reinterpret_cast<const float*>(base + sc_off);
   auto mat = [&](size_t i) { return reinterpret_cast<const uint4*>(base + i * wb); };
+  auto scl = [&](size_t i) { return mode == 2 ? scd + i * 64 : nullptr; };
   out->resize(N_it);
   t = 0;
   for (int k = 0; k < N_it; ++k) {
     IterWeightsTC& w = (*out)[k];
     memset(&w, 0, sizeof(w));
     const IterWeightsF32& f = it32[k];
+    w.mp1_sc = scl(t);
     w.mp1 = mat(t++);
+    w.in_s_sc = scl(t);
     w.in_s = mat(t++);
+    w.in_c_sc = scl(t);
     w.in_c = mat(t++);
     w.mp1_b = f.mp1_b;
     w.in_b = f.in_b;
     w.cb2 = reinterpret_cast<const float*>(base + cb2_off) + (size_t)k * C;
     w.in_pe = f.in_t + (size_t)2 * C * C;
     for (int r = 0; r < R; ++r) {
+      w.pw1_sc[r] = scl(t);
       w.pw1[r] = mat(t++);
+      w.pw2_sc[r] = scl(t);
       w.pw2[r] = mat(t++);
       w.pw1_b[r] = f.pw1_b[r];
       w.pw2_b[r] = f.pw2_b[r];
@@ -918,6 +1127,7 @@ nrx_status upload_tc_weights(bool bf16, int C, int R, int N_it, const std::vecto
     }
     w.err = err;
   }
+  ro->ro1_sc = scl(t);
   ro->ro1 = mat(t++);
   ro->ro1_b = ro1_b_dev;
   ro->ro2 = ro2_dev;
@@ -926,43 +1136,44 @@ nrx_status upload_tc_weights(bool bf16, int C, int R, int N_it, const std::vecto
   return NRX_OK;
 }
 
-template <typename T>
-cudaError_t launch_mp_tc(const Geometry& g, const IterWeightsTC& w, const T* state, T* z, cudaStream_t st) {
+template <typename P>
+cudaError_t launch_mp_tc(const Geometry& g, const IterWeightsTC& w, const typename P::T* state, typename P::T* z,
+                         cudaStream_t st) {
   if (g.C != 64) return cudaErrorInvalidValue;
   const int nre = g.U == 4 ? 32 : g.U == 3 ? 40 : g.U == 2 ? 64 : 128;
   const int tps = (NRX_SYMBOLS * g.S + nre - 1) / nre;
   const int tiles = g.n_slots * tps;
-  const int smem = MpLayout<T>::DYN;
-  set_smem(k_mp_tc<T>, smem);
+  const int smem = MpLayout<P>::DYN;
+  set_smem(k_mp_tc<P>, smem);
   const int grid = grid_for(smem, 2, tiles);
-  k_mp_tc<T><<<grid, kThreads, smem, st>>>(g, w, state, z, nre, tps);
+  k_mp_tc<P><<<grid, kThreads, smem, st>>>(g, w, state, z, nre, tps);
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_block_tc(const Geometry& g, const IterWeightsTC& w, int r, const T* z_in, T* z_out, T* state,
-                            bool last, cudaStream_t st) {
+template <typename P>
+cudaError_t launch_block_tc(const Geometry& g, const IterWeightsTC& w, int r, const typename P::T* z_in,
+                            typename P::T* z_out, typename P::T* state, bool last, cudaStream_t st) {
   if (g.C != 64) return cudaErrorInvalidValue;
-  const int tps = (g.S + BlkLayout<T>::TW - 1) / BlkLayout<T>::TW;
+  const int tps = (g.S + BlkLayout<P>::TW - 1) / BlkLayout<P>::TW;
   const int tiles = g.n_slots * g.U * tps;
-  const int smem = BlkLayout<T>::DYN;
-  set_smem(k_block_tc<T>, smem);
+  const int smem = BlkLayout<P>::DYN;
+  set_smem(k_block_tc<P>, smem);
   const int grid = grid_for(smem, 2, tiles);
-  k_block_tc<T><<<grid, kThreads, smem, st>>>(g, w.pw1[r], w.pw2[r], w.pw1_b[r], w.pw2_b[r], w.dw1[r], w.dw2[r],
-                                               z_in, z_out, state, last ? 1 : 0, w.err);
+  k_block_tc<P><<<grid, kThreads, smem, st>>>(g, w.pw1[r], w.pw2[r], w.pw1_b[r], w.pw2_b[r], w.dw1[r], w.dw2[r],
+                                               w.pw1_sc[r], w.pw2_sc[r], z_in, z_out, state, last ? 1 : 0, w.err);
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_readout_tc(const Geometry& g, const SlotTable& tab, const ReadoutWeightsTC& w, const T* state,
-                              float* llr, cudaStream_t st) {
+template <typename P>
+cudaError_t launch_readout_tc(const Geometry& g, const SlotTable& tab, const ReadoutWeightsTC& w,
+                              const typename P::T* state, float* llr, cudaStream_t st) {
   if (g.C != 64) return cudaErrorInvalidValue;
   const int tpsu = (g.n_data + 127) / 128;
   const int tiles = g.n_slots * g.U * tpsu;
-  const int smem = RoLayout<T>::DYN;
-  set_smem(k_readout_tc<T>, smem);
+  const int smem = RoLayout<P>::DYN;
+  set_smem(k_readout_tc<P>, smem);
   const int grid = grid_for(smem, 4, tiles);
-  k_readout_tc<T><<<grid, 128, smem, st>>>(g, tab, w, state, llr, tpsu);
+  k_readout_tc<P><<<grid, 128, smem, st>>>(g, tab, w, state, llr, tpsu);
   return cudaGetLastError();
 }
 
@@ -972,12 +1183,14 @@ cudaError_t launch_to_f32(const T* in, float* out, size_t n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-#define NRX_INSTANTIATE(T)                                                                                     \
-  template cudaError_t launch_mp_tc<T>(const Geometry&, const IterWeightsTC&, const T*, T*, cudaStream_t);     \
-  template cudaError_t launch_block_tc<T>(const Geometry&, const IterWeightsTC&, int, const T*, T*, T*, bool,  \
-                                          cudaStream_t);                                                       \
-  template cudaError_t launch_readout_tc<T>(const Geometry&, const SlotTable&, const ReadoutWeightsTC&,        \
-                                            const T*, float*, cudaStream_t);                                   \
-  template cudaError_t launch_to_f32<T>(const T*, float*, size_t, cudaStream_t);
-NRX_INSTANTIATE(__nv_bfloat16)
-NRX_INSTANTIATE(__half)
+#define NRX_INSTANTIATE(P)                                                                                         \
+  template cudaError_t launch_mp_tc<P>(const Geometry&, const IterWeightsTC&, const P::T*, P::T*, cudaStream_t);   \
+  template cudaError_t launch_block_tc<P>(const Geometry&, const IterWeightsTC&, int, const P::T*, P::T*, P::T*,   \
+                                          bool, cudaStream_t);                                                     \
+  template cudaError_t launch_readout_tc<P>(const Geometry&, const SlotTable&, const ReadoutWeightsTC&,            \
+                                            const P::T*, float*, cudaStream_t);
+NRX_INSTANTIATE(PolBF16)
+NRX_INSTANTIATE(PolFP16)
+NRX_INSTANTIATE(PolFP8)
+template cudaError_t launch_to_f32<__nv_bfloat16>(const __nv_bfloat16*, float*, size_t, cudaStream_t);
+template cudaError_t launch_to_f32<__half>(const __half*, float*, size_t, cudaStream_t);

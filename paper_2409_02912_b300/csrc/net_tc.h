@@ -23,10 +23,31 @@
 // with h_v = ReLU(W1 S_v + b1) and g_u = sum_{v != u} h_v, the aggregate is
 // a_u = W2 g_u + (U-1) b2, so Win_a a_u = (Win_a W2) g_u + (U-1) Win_a b2.
 // in_c holds Win_a W2 (formed in FP64 on the host) and cb2 = Win_a b2.
+// Precision policies: T = activation storage / depthwise type; split = BF16
+// weights as hi + lo images; fp8 = E4M3 MMA operands (per-row activation
+// scales, per-output-channel weight scales) over FP16 storage.
+struct PolBF16 {
+  using T = __nv_bfloat16;
+  static constexpr bool split = true, fp8 = false;
+};
+struct PolFP16 {
+  using T = __half;
+  static constexpr bool split = false, fp8 = false;
+};
+struct PolFP8 {
+  using T = __half;
+  static constexpr bool split = false, fp8 = true;
+};
+
 struct IterWeightsTC {
   const uint4* mp1;
   const uint4* in_s;   // input layer, columns acting on S
   const uint4* in_c;   // Win_a W2, acting on g
+  const float* mp1_sc;   // E4M3 per-output-channel scales (FP8 policy only)
+  const float* in_s_sc;
+  const float* in_c_sc;
+  const float* pw1_sc[4];
+  const float* pw2_sc[4];
   const float* mp1_b;
   const float* in_b;
   const float* cb2;    // [C] Win_a b2
@@ -42,6 +63,7 @@ struct IterWeightsTC {
 
 struct ReadoutWeightsTC {
   const uint4* ro1;
+  const float* ro1_sc;  // E4M3 scales (FP8 policy only)
   const float* ro1_b;
   const float* ro2;    // [m_max][C] FP32
   const float* ro2_b;
@@ -51,21 +73,21 @@ struct ReadoutWeightsTC {
 // blob_it: per iteration {mp1w, mp1b, mp2w, mp2b, inw, inb} then per block
 // {dw1, pw1w, pw1b, dw2, pw2w, pw2b} (host pointers into the blob).  FP32
 // device tensors (biases, taps, PE columns, readout head) are taken from the
-// FP32 upload.  Only C = 64 is supported.  bf16 selects the operand type
-// (BF16 with split weights, else FP16).
-nrx_status upload_tc_weights(bool bf16, int C, int R, int N_it, const std::vector<const float*>& blob_it,
+// FP32 upload.  Only C = 64 is supported.  mode: 0 FP16, 1 BF16 (split
+// weights), 2 FP8 (E4M3 with per-output-channel scales).
+nrx_status upload_tc_weights(int mode, int C, int R, int N_it, const std::vector<const float*>& blob_it,
                              const float* ro1w, const std::vector<IterWeightsF32>& it32, const float* ro1_b_dev,
                              const float* ro2_dev, const float* ro2_b_dev, std::vector<IterWeightsTC>* out,
                              void** dev_alloc, ReadoutWeightsTC* ro, int** err_word);
 
-// T = __nv_bfloat16 or __half (operand and activation storage type).
-template <typename T>
-cudaError_t launch_mp_tc(const Geometry& g, const IterWeightsTC& w, const T* state, T* z, cudaStream_t st);
-template <typename T>
-cudaError_t launch_block_tc(const Geometry& g, const IterWeightsTC& w, int r, const T* z_in, T* z_out, T* state,
-                            bool last, cudaStream_t st);
-template <typename T>
-cudaError_t launch_readout_tc(const Geometry& g, const SlotTable& tab, const ReadoutWeightsTC& w, const T* state,
-                              float* llr, cudaStream_t st);
+template <typename P>
+cudaError_t launch_mp_tc(const Geometry& g, const IterWeightsTC& w, const typename P::T* state, typename P::T* z,
+                         cudaStream_t st);
+template <typename P>
+cudaError_t launch_block_tc(const Geometry& g, const IterWeightsTC& w, int r, const typename P::T* z_in,
+                            typename P::T* z_out, typename P::T* state, bool last, cudaStream_t st);
+template <typename P>
+cudaError_t launch_readout_tc(const Geometry& g, const SlotTable& tab, const ReadoutWeightsTC& w,
+                              const typename P::T* state, float* llr, cudaStream_t st);
 template <typename T>
 cudaError_t launch_to_f32(const T* in, float* out, size_t n, cudaStream_t st);

@@ -187,9 +187,10 @@ nrx_status prepare(nrx_ctx* ctx, int32_t n_slots, const nrx_slot_cfg* cfgs, cons
   return NRX_OK;
 }
 
-template <typename T>
+template <typename P>
 nrx_status run_tc(nrx_ctx* ctx, const Geometry& g, const SlotTable& tab, int its, const float2* y, float* llr,
                   cudaStream_t st, int* launches) {
+  using T = typename P::T;
   cudaError_t e;
   T* S = static_cast<T*>(ctx->state);
   T* za = static_cast<T*>(ctx->z_a);
@@ -204,7 +205,7 @@ nrx_status run_tc(nrx_ctx* ctx, const Geometry& g, const SlotTable& tab, int its
     const IterWeightsTC& w = ctx->it16[k];
     {
       KernelTimer kt(ctx, K_MP, st);
-      e = launch_mp_tc<T>(g, w, S, za, st);
+      e = launch_mp_tc<P>(g, w, S, za, st);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "message_passing");
     ++*launches;
@@ -214,7 +215,7 @@ nrx_status run_tc(nrx_ctx* ctx, const Geometry& g, const SlotTable& tab, int its
       const bool last = r == ctx->R - 1;
       {
         KernelTimer kt(ctx, K_BLOCK, st);
-        e = launch_block_tc<T>(g, w, r, zin, zout, S, last, st);
+        e = launch_block_tc<P>(g, w, r, zin, zout, S, last, st);
       }
       if (e != cudaSuccess) return cuda_fail(ctx, e, "residual_block");
       ++*launches;
@@ -225,7 +226,7 @@ nrx_status run_tc(nrx_ctx* ctx, const Geometry& g, const SlotTable& tab, int its
   }
   {
     KernelTimer kt(ctx, K_READOUT, st);
-    e = launch_readout_tc<T>(g, tab, ctx->ro_tc, S, llr, st);
+    e = launch_readout_tc<P>(g, tab, ctx->ro_tc, S, llr, st);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "readout");
   ++*launches;
@@ -276,9 +277,11 @@ nrx_status run_nrx(nrx_ctx* ctx, const Geometry& g, const SlotTable& tab, int it
     if (e != cudaSuccess) return cuda_fail(ctx, e, "readout_f32");
     ++launches;
   } else if (ctx->prec == NRX_BF16) {
-    if (run_tc<__nv_bfloat16>(ctx, g, tab, its, y, llr, st, &launches) != NRX_OK) return NRX_ECUDA;
+    if (run_tc<PolBF16>(ctx, g, tab, its, y, llr, st, &launches) != NRX_OK) return NRX_ECUDA;
+  } else if (ctx->prec == NRX_FP16) {
+    if (run_tc<PolFP16>(ctx, g, tab, its, y, llr, st, &launches) != NRX_OK) return NRX_ECUDA;
   } else {
-    if (run_tc<__half>(ctx, g, tab, its, y, llr, st, &launches) != NRX_OK) return NRX_ECUDA;
+    if (run_tc<PolFP8>(ctx, g, tab, its, y, llr, st, &launches) != NRX_OK) return NRX_ECUDA;
   }
   ctx->last_geo = g;
   ctx->have_state = true;
@@ -407,7 +410,8 @@ nrx_status nrx_create(const void* weights, size_t weights_bytes, int32_t num_rx_
   if ((num_rx_ant != 1 && num_rx_ant != 2 && num_rx_ant != 4 && num_rx_ant != 8) || max_users < 1 || max_users > NRX_MAX_USERS || max_prb < 1 ||
       max_prb > 275 || max_slots < 1 || max_slots > NRX_MAX_LAUNCH_SLOTS)
     return NRX_EINVAL;
-  if (precision != NRX_FP32 && precision != NRX_BF16 && precision != NRX_FP16) return NRX_EINVAL;
+  if (precision != NRX_FP32 && precision != NRX_BF16 && precision != NRX_FP16 && precision != NRX_FP8)
+    return NRX_EINVAL;
   int32_t hdr[8];
   memcpy(hdr, weights, sizeof(hdr));
   const int B = hdr[2], C = hdr[3], R = hdr[4], N_it = hdr[5], m_max = hdr[6];
@@ -543,7 +547,8 @@ nrx_status nrx_create(const void* weights, size_t weights_bytes, int32_t num_rx_
     }
   }
   if (precision != NRX_FP32) {
-    nrx_status st = upload_tc_weights(precision == NRX_BF16, C, R, N_it, blob_it, ro1w, ctx->it32, ctx->ro1_b,
+    const int mode = precision == NRX_BF16 ? 1 : precision == NRX_FP8 ? 2 : 0;
+    nrx_status st = upload_tc_weights(mode, C, R, N_it, blob_it, ro1w, ctx->it32, ctx->ro1_b,
                                       ctx->ro2, ctx->ro2_b, &ctx->it16, &ctx->w_tc, &ctx->ro_tc, &ctx->d_err);
     if (st != NRX_OK) {
       nrx_destroy(ctx);

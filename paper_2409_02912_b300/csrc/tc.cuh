@@ -131,6 +131,31 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// D[tmem] (+)= A * B^T with 8-bit operands (kind::f8f6f4), M=128, N, K=32.
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Instruction descriptor of kind::f8f6f4: E4M3 A and B (K-major), FP32 D.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// K = 64 GEMM tile of 8-bit operands stored in the first 64 bytes of each
+// 128-byte swizzled row: 2 MMAs of K = 32 stepping 32 B inside the atom.
+__device__ __forceinline__ void mma_k64_f8(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr, bool accumulate_first) {
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+    mma_f8(d_tmem, desc_sw128(a_saddr + 32 * k), desc_sw128(b_saddr + 32 * k), idesc_e4m3_f32(128, 64),
+           (k > 0 || accumulate_first) ? 1u : 0u);
+}
+
 // Arrive on `bar` once all previously issued MMAs of this thread complete.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))

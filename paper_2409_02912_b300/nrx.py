@@ -16,8 +16,8 @@ import numpy as np
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libnrx.so")
 
 NRX_OK, NRX_EINVAL, NRX_ENOMEM, NRX_ECUDA, NRX_ETIMEDOUT, NRX_EUNSUPPORTED = range(6)
-NRX_FP32, NRX_BF16, NRX_FP16 = 0, 1, 2
-PRECISIONS = {"fp32": NRX_FP32, "bf16": NRX_BF16, "fp16": NRX_FP16}
+NRX_FP32, NRX_BF16, NRX_FP16, NRX_FP8 = 0, 1, 2, 3
+PRECISIONS = {"fp32": NRX_FP32, "bf16": NRX_BF16, "fp16": NRX_FP16, "fp8": NRX_FP8}
 
 EXPORTED = (
     "nrx_create", "nrx_destroy", "nrx_llr_count", "nrx_detect_batch", "nrx_detect", "lmmse_detect_batch",

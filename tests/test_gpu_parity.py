@@ -206,3 +206,47 @@ def test_tc_context_rejects_c32(prec):
     with pytest.raises(nrx.NrxError) as e:
         _receiver(w.net, synth.workload_slots(w, 1), prec)
     assert e.value.status == nrx.NRX_EUNSUPPORTED
+
+
+# FP8 (E4M3 operands): error is reported, not bounded by the specification.
+# These sanity bounds come from a CPU emulation of the same quantisation
+# (worst 0.16-0.25, sign agreement >= 0.991 on LLRs above 5% of the maximum).
+FP8_WORST = 0.35
+FP8_SIGN = 0.98
+
+
+@pytest.mark.parametrize("workload", ["mu2_4rx_24prb", "mu4_4rx_273prb"])
+def test_nrx_fp8_error_report(workload):
+    w, slots = H.slots_for(workload)
+    rx = _receiver(w.net, slots, "fp8")
+    y, dmrs, bits, _ = H.device_inputs(slots)
+    llr = rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits).cpu().numpy()
+    rx.nrx_check()
+    assert np.all(np.isfinite(llr))
+    refs = H.oracle_nrx(slots, H.weights64(w.net), w.net)
+    errs = H.rel_errors(llr, refs, slots)
+    g, _ = H.split(llr, slots)
+    agree = []
+    for gs, ref, s in zip(g, refs, slots):
+        r, _ = H.split(ref, [s])
+        for gu, ru in zip(gs, r[0]):
+            big = np.abs(ru) > 0.05 * np.max(np.abs(ru))
+            agree.append(np.mean(np.sign(gu[big]) == np.sign(ru[big])))
+    print(f"FP8 {workload}: worst {max(errs):.4f} median {np.median(errs):.4f} sign agreement {min(agree):.4f}")
+    assert max(errs) <= FP8_WORST and min(agree) >= FP8_SIGN, (errs, agree)
+
+
+@pytest.mark.parametrize("case", TC_EDGE[:2])
+def test_fp8_edge_geometries_finite(case):
+    U, B, prb, dmrs, R, N_it, bits = case
+    net = synth.NetConfig(num_rx_ant=B, channels=64, res_blocks=R, iterations=N_it, m_max=6)
+    rng = np.random.Generator(np.random.PCG64(93))
+    slots = [synth.make_slot(synth.SlotConfig(num_prb=prb, num_users=U, num_rx_ant=B, dmrs_symbols=dmrs,
+                                              bits_per_symbol=bits, snr_db=8.0, num_taps=5, delay_spread_s=150e-9,
+                                              doppler_hz=200.0, ula=False), rng) for _ in range(2)]
+    rx = _receiver(net, slots, "fp8")
+    y, d, b, _ = H.device_inputs(slots)
+    llr = rx.nrx_detect_batch(y, d, dmrs, b).cpu().numpy()
+    rx.nrx_check()
+    errs = H.rel_errors(llr, H.oracle_nrx(slots, H.weights64(net), net), slots)
+    assert np.all(np.isfinite(llr)) and max(errs) <= FP8_WORST, errs
