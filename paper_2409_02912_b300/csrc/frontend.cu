@@ -162,7 +162,7 @@ template <int C, int B, typename OutT>
 cudaError_t launch_si(const Geometry& g, const SlotTable& tab, const float2* y, const float* w_pw, const float* b_pw,
                       const float* k_dw, OutT* s_out, cudaStream_t st) {
   const size_t smem = state_init_smem_bytes(C, B);
-  cudaFuncSetAttribute(k_state_init<C, B, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ensure_smem<k_state_init<C, B, OutT>>((int)smem);
   int per_sm = (int)((228 * 1024) / (smem + 1024));
   if (per_sm > 4) per_sm = 4;
   if (per_sm < 1) per_sm = 1;

@@ -5,7 +5,24 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "common.cuh"
+
+// Raise `Kernel`'s dynamic shared-memory limit to `bytes` once per device (the
+// attribute is per device; later launches skip the driver call, which also
+// keeps the launch sequence free of non-stream calls during graph capture).
+template <auto Kernel>
+inline cudaError_t ensure_smem(int bytes) {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 constexpr int kStateInitTile = 16;  // subcarriers per StateInit CTA
 

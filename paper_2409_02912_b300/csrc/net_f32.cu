@@ -318,10 +318,6 @@ __global__ void __launch_bounds__(kThreads) k_readout_f32(Geometry g, SlotTable 
   }
 }
 
-template <typename K>
-cudaError_t set_smem(K kernel, size_t bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
 
 }  // namespace
 
@@ -330,12 +326,12 @@ cudaError_t launch_mp_f32(const Geometry& g, const IterWeightsF32& w, const floa
   if (g.C == 64) {
     using Cf = MpCfg<64>;
     const size_t smem = sizeof(float) * 2 * Cf::ROWS * Cf::LD;
-    set_smem(k_mp_f32<64>, smem);
+    ensure_smem<k_mp_f32<64>>((int)smem);
     k_mp_f32<64><<<dim3((n_re + Cf::kRE - 1) / Cf::kRE, g.n_slots), kThreads, smem, st>>>(g, w, state, z);
   } else if (g.C == 32) {
     using Cf = MpCfg<32>;
     const size_t smem = sizeof(float) * 2 * Cf::ROWS * Cf::LD;
-    set_smem(k_mp_f32<32>, smem);
+    ensure_smem<k_mp_f32<32>>((int)smem);
     k_mp_f32<32><<<dim3((n_re + Cf::kRE - 1) / Cf::kRE, g.n_slots), kThreads, smem, st>>>(g, w, state, z);
   } else {
     return cudaErrorInvalidValue;
@@ -348,13 +344,13 @@ cudaError_t launch_block_f32(const Geometry& g, const IterWeightsF32& w, int r, 
   if (g.C == 64) {
     using Cf = BlkCfg<64>;
     const size_t smem = sizeof(float) * Cf::smem_floats;
-    set_smem(k_block_f32<64>, smem);
+    ensure_smem<k_block_f32<64>>((int)smem);
     k_block_f32<64><<<dim3((g.S + Cf::kTW - 1) / Cf::kTW, g.U, g.n_slots), kThreads, smem, st>>>(
         g, w.dw1[r], w.pw1_t[r], w.pw1_b[r], w.dw2[r], w.pw2_t[r], w.pw2_b[r], z_in, z_out, state, last ? 1 : 0);
   } else if (g.C == 32) {
     using Cf = BlkCfg<32>;
     const size_t smem = sizeof(float) * Cf::smem_floats;
-    set_smem(k_block_f32<32>, smem);
+    ensure_smem<k_block_f32<32>>((int)smem);
     k_block_f32<32><<<dim3((g.S + Cf::kTW - 1) / Cf::kTW, g.U, g.n_slots), kThreads, smem, st>>>(
         g, w.dw1[r], w.pw1_t[r], w.pw1_b[r], w.dw2[r], w.pw2_t[r], w.pw2_b[r], z_in, z_out, state, last ? 1 : 0);
   } else {

@@ -956,10 +956,6 @@ __global__ void k_to_f32(const T* __restrict__ in, float* __restrict__ out, size
     out[i] = (float)in[i];
 }
 
-template <typename K>
-void set_smem(K kernel, int bytes) {
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
 
 uint16_t f32_to_bf16_rn(float f) {
   uint32_t u;
@@ -1144,7 +1140,7 @@ cudaError_t launch_mp_tc(const Geometry& g, const IterWeightsTC& w, const typena
   const int tps = (NRX_SYMBOLS * g.S + nre - 1) / nre;
   const int tiles = g.n_slots * tps;
   const int smem = MpLayout<P>::DYN;
-  set_smem(k_mp_tc<P>, smem);
+  ensure_smem<k_mp_tc<P>>(smem);
   const int grid = grid_for(smem, 2, tiles);
   k_mp_tc<P><<<grid, kThreads, smem, st>>>(g, w, state, z, nre, tps);
   return cudaGetLastError();
@@ -1157,7 +1153,7 @@ cudaError_t launch_block_tc(const Geometry& g, const IterWeightsTC& w, int r, co
   const int tps = (g.S + BlkLayout<P>::TW - 1) / BlkLayout<P>::TW;
   const int tiles = g.n_slots * g.U * tps;
   const int smem = BlkLayout<P>::DYN;
-  set_smem(k_block_tc<P>, smem);
+  ensure_smem<k_block_tc<P>>(smem);
   const int grid = grid_for(smem, 2, tiles);
   k_block_tc<P><<<grid, kThreads, smem, st>>>(g, w.pw1[r], w.pw2[r], w.pw1_b[r], w.pw2_b[r], w.dw1[r], w.dw2[r],
                                                w.pw1_sc[r], w.pw2_sc[r], z_in, z_out, state, last ? 1 : 0, w.err);
@@ -1171,7 +1167,7 @@ cudaError_t launch_readout_tc(const Geometry& g, const SlotTable& tab, const Rea
   const int tpsu = (g.n_data + 127) / 128;
   const int tiles = g.n_slots * g.U * tpsu;
   const int smem = RoLayout<P>::DYN;
-  set_smem(k_readout_tc<P>, smem);
+  ensure_smem<k_readout_tc<P>>(smem);
   const int grid = grid_for(smem, 4, tiles);
   k_readout_tc<P><<<grid, 128, smem, st>>>(g, tab, w, state, llr, tpsu);
   return cudaGetLastError();

@@ -250,3 +250,23 @@ def test_fp8_edge_geometries_finite(case):
     rx.nrx_check()
     errs = H.rel_errors(llr, H.oracle_nrx(slots, H.weights64(net), net), slots)
     assert np.all(np.isfinite(llr)) and max(errs) <= FP8_WORST, errs
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+def test_cuda_graph_replay_matches_direct_call(prec):
+    """nrx_detect_batch allocates nothing and never synchronises, so its launch
+    sequence can be captured in a CUDA graph; replay gives the same LLRs."""
+    import torch
+    w, slots = H.slots_for("mu2_4rx_24prb", 2)
+    rx = _receiver(w.net, slots, prec)
+    y, dmrs, bits, _ = H.device_inputs(slots)
+    out = rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits)  # first call sets kernel attributes
+    ref = out.clone()
+    out.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits, out=out)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    rx.nrx_check()
