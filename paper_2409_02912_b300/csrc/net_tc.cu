@@ -592,6 +592,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
   const int rcol = row >> 4, rt = row & 15;
   const uint32_t* zw = reinterpret_cast<const uint32_t*>(sm + L::ZB);
   unsigned char* const a_tile = sm + L::A;
+  // Tile-independent decode of this thread's items in the coalesced write-out
+  // (item = 16 bytes of one output row; rows ordered symbol-major, then subcarrier).
+  constexpr int kOutItems = NRX_SYMBOLS * L::TW * 8;
+  constexpr int kOutIt = (kOutItems + kThreads - 1) / kThreads;
+  int out_off[kOutIt], out_x[kOutIt], out_sr[kOutIt];
+#pragma unroll
+  for (int it = 0; it < kOutIt; ++it) {
+    const int i = tid + it * kThreads;
+    const int c8 = i & 7, x = (i >> 3) % L::TW, t = (i >> 3) / L::TW;
+    out_x[it] = i < kOutItems ? x : 1 << 20;  // never inside the grid when i is past the items
+    out_off[it] = (t * S + x) * C64 + c8 * 8;
+    out_sr[it] = x * NRX_SYMBOLS + t;
+  }
+  const int out_c8 = tid & 7;
   const int cpc = cp >> 2, cpl = cp & 3;  // 16-byte chunk and word within it of this channel pair
   bool timed_out = false;
 
@@ -778,30 +792,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
     // Step 2: + residual (+ state), coalesced: 8 threads per row, rows ordered
     // symbol-major then subcarrier (each warp moves 4 consecutive 128-byte rows).
     {
-      constexpr int kItems = NRX_SYMBOLS * L::TW * 8;
-      constexpr int kIt = (kItems + kThreads - 1) / kThreads;
       T* out = last ? state : z_out;
-      uint4 rq[kIt], sq[kIt];
+      const size_t tbase = (base + (size_t)s0) * C64;
+      uint4 rq[kOutIt], sq[kOutIt];
 #pragma unroll
-      for (int it = 0; it < kIt; ++it) {
-        const int i = tid + it * kThreads;
-        const int c8 = i & 7, x = (i >> 3) % L::TW, t = (i >> 3) / L::TW, s = s0 + x;
+      for (int it = 0; it < kOutIt; ++it) {
         rq[it] = make_uint4(0, 0, 0, 0);
         sq[it] = make_uint4(0, 0, 0, 0);
-        if (i < kItems && s < S) {
-          const size_t off = (base + (size_t)t * S + s) * C64 + c8 * 8;
-          rq[it] = __ldg(reinterpret_cast<const uint4*>(z_in + off));
-          if (last) sq[it] = *reinterpret_cast<const uint4*>(state + off);  // plain load: written here
+        if (s0 + out_x[it] < S) {
+          rq[it] = __ldg(reinterpret_cast<const uint4*>(z_in + tbase + out_off[it]));
+          if (last) sq[it] = *reinterpret_cast<const uint4*>(state + tbase + out_off[it]);  // written here
         }
       }
 #pragma unroll
-      for (int it = 0; it < kIt; ++it) {
-        const int i = tid + it * kThreads;
-        const int c8 = i & 7, x = (i >> 3) % L::TW, t = (i >> 3) / L::TW, s = s0 + x;
-        if (i >= kItems || s >= S) continue;
-        const int sr = x * NRX_SYMBOLS + t;
+      for (int it = 0; it < kOutIt; ++it) {
+        if (s0 + out_x[it] >= S) continue;
+        const int sr = out_sr[it];
         const float4* src = reinterpret_cast<const float4*>(sr < 128 ? sm + L::A + sr * 256 : sm + L::ZB + (sr - 128) * 256);
-        const float4 a = src[(2 * c8) ^ (sr & 7)], b = src[(2 * c8 + 1) ^ (sr & 7)];
+        const float4 a = src[(2 * out_c8) ^ (sr & 7)], b = src[(2 * out_c8 + 1) ^ (sr & 7)];
         float o[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
         const uint32_t rw[4] = {rq[it].x, rq[it].y, rq[it].z, rq[it].w};
         const uint32_t sw[4] = {sq[it].x, sq[it].y, sq[it].z, sq[it].w};
@@ -816,7 +824,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
             o[2 * k + 1] += g2.y;
           }
         }
-        *reinterpret_cast<uint4*>(out + (base + (size_t)t * S + s) * C64 + c8 * 8) = pack8<T>(o);
+        *reinterpret_cast<uint4*>(out + tbase + out_off[it]) = pack8<T>(o);
       }
     }
     tc::tc_fence_before();

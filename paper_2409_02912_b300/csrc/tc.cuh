@@ -57,8 +57,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
   if (mbar_test_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t i = 1; i < (1u << 28); ++i) {
+    __nanosleep(32);  // yield issue slots to the other warps while the MMAs run
     if (mbar_test_wait(bar, parity)) return true;
-    if ((i & 1023) == 0 && globaltimer() - t0 > limit_ns) return false;
+    if ((i & 255) == 0 && globaltimer() - t0 > limit_ns) return false;
   }
   return false;
 }
