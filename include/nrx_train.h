@@ -1,0 +1,147 @@
+/*
+ * nrx_train.h - C ABI of the NRX training kernels (same library, libnrx.so).
+ *
+ * Training scheme (Sec. II-B): empirical risk minimisation of the binary
+ * cross-entropy between the LLRs of ReadoutLLRs and the transmitted bits,
+ * plus gamma times the mean-squared error of a second read-out head
+ * (ReadoutChEst) against the true channel ("double read-out"), with the
+ * read-outs applied after every CGNN iteration and the losses summed
+ * (multi-loss, Sec. II-B), Var-MCS masking of the LLR outputs (Sec. III) and
+ * per-sample random MCS-to-user association with SNR offsets (Sec. IV-A).
+ * Weights are updated with Adam.
+ *
+ * These are the layer-level building blocks of that scheme: each call runs
+ * one forward or backward step of one layer kind over a batch of REs on the
+ * caller's stream (FP32 CUDA-core arithmetic, FP32 activations).  The caller
+ * composes them into the network's forward pass with saved activations and
+ * the reverse pass (see the Python trainer), and owns every buffer.
+ *
+ * Common conventions
+ *   - All pointers are device pointers unless stated; float32 unless stated.
+ *   - Activations of one layer are row-major matrices [rows][width]; a row is
+ *     one RE of one user of one slot, rows ordered [slot][user][symbol t (14)]
+ *     [subcarrier s] — so a "plane" (slot, user) is a 14 x S grid.
+ *   - stream is a cudaStream_t (NULL = legacy default stream).
+ *   - Calls return once the work is enqueued.  NRX_EINVAL: bad argument,
+ *     nothing launched.  NRX_ECUDA: the launch failed.
+ *   - No call allocates memory.
+ */
+#ifndef NRX_TRAIN_H_
+#define NRX_TRAIN_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "nrx.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * Network input features (Sec. II-A) of every user of n_slots slots of one
+ * geometry: x [n_slots][U][14][S][4B+2] with the feature order of nrx.h
+ * (Re/Im y per antenna, Re/Im interpolated LS estimate per antenna, dt, df).
+ *   y     complex64 [n_slots][B][14][S]
+ *   cfgs  host array [n_slots]; num_prb, num_users and DMRS symbols taken from
+ *         cfgs[0] (all slots must agree), dmrs_seq per slot (device).
+ * 1 <= n_slots <= 64, 1 <= num_rx_ant <= 8.
+ */
+nrx_status nrx_train_features(int32_t n_slots, int32_t num_rx_ant, const void* y, const nrx_slot_cfg* cfgs,
+                              float* x, void* stream);
+
+/*
+ * Strided matrix product with epilogue:
+ *   C[m][n] = act(sum_k A(m,k) B(k,n) + bias[n] + R[m][n])       (accumulate = 0)
+ *   C[m][n] += sum_k A(m,k) B(k,n)                                (accumulate != 0)
+ * with A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn], C row stride ldc,
+ * R row stride ldr.  act is ReLU when relu != 0.  bias and R may be NULL; R may
+ * equal C (in-place residual add).  One call covers a dense layer y = W x + b
+ * (B(k,n) = W[n][k]), its input gradient dx = dy W (B(k,n) = W[k][n]) and its
+ * weight gradient dW += dy^T x (A(m,k) = dy[k][m], accumulate = 1).
+ * split_k (>= 1) splits the K range over CTAs; split_k > 1 requires
+ * accumulate.  Accumulation uses float atomics (summation order varies).
+ */
+nrx_status nrx_train_gemm(int32_t M, int32_t N, int32_t K, const float* A, int64_t sam, int64_t sak, const float* B,
+                          int64_t sbk, int64_t sbn, const float* bias, const float* R, int64_t ldr, float* C,
+                          int64_t ldc, int32_t relu, int32_t accumulate, int32_t split_k, void* stream);
+
+/* out[n] += sum_m X[m*ldx + n], n < N (bias gradients). */
+nrx_status nrx_train_colsum(int32_t M, int32_t N, const float* X, int64_t ldx, float* out, void* stream);
+
+/*
+ * Depthwise 3x3 layer over `planes` grids of 14 x S with C channels,
+ * X, Y [planes][14][S][C], taps k [C][3][3], zero "same" padding:
+ *   Y[t][s][c] = act(sum_{i,j} k[c][i][j] X[t+i-1][s+j-1][c])
+ * flip != 0 reads the taps as k[c][2-i][2-j] (the adjoint: with flip, the call
+ * maps an output gradient to the input gradient).  act is ReLU when relu != 0.
+ * X and Y must not overlap.
+ */
+nrx_status nrx_train_dw3(int32_t planes, int32_t S, int32_t C, const float* X, const float* k, int32_t flip,
+                         int32_t relu, float* Y, void* stream);
+
+/* Tap gradient of nrx_train_dw3: gk[c][i][j] += sum G[t][s][c] X[t+i-1][s+j-1][c]
+ * over all planes, t, s (zero padding).  Float atomics. */
+nrx_status nrx_train_dw3_wgrad(int32_t planes, int32_t S, int32_t C, const float* X, const float* G, float* gk,
+                               void* stream);
+
+/* ReLU backward, in place: G[i] = 0 where Y[i] <= 0 (Y the ReLU output). */
+nrx_status nrx_train_relu_mask(int64_t n, float* G, const float* Y, void* stream);
+
+/*
+ * Message aggregation of the CGNN (Sec. II-A): for m, a [n_slots][U][per_user],
+ *   a[sl][u][e] = sum_{v != u} m[sl][v][e].
+ * The map is symmetric, so the same call maps the gradient of a to the
+ * gradient of m.  1 <= U <= 4; m and a must differ.
+ */
+nrx_status nrx_train_aggregate(int32_t n_slots, int32_t num_users, int64_t per_user, const float* m, float* a,
+                               void* stream);
+
+/* y[i] += alpha * x[i], i < n. */
+nrx_status nrx_train_axpy(int64_t n, float alpha, const float* x, float* y, void* stream);
+
+/*
+ * Masked BCE of one LLR read-out (Sec. II-B; LLR sign of Eq. 2, so
+ * P(b=1) = sigmoid(l)):
+ *   *loss += scale * sum (softplus(l) - b l)     (FP64 accumulation)
+ *   grad   = scale * (sigmoid(l) - b)             on counted entries, else 0
+ * over the data REs (DMRS symbols of cfg skipped) and the first m_u outputs of
+ * each user (Var-MCS masking, Sec. III).
+ *   llr, grad             [n_slots][U][14][S][m_max]
+ *   bits                  uint8 [n_slots][U][n_data][m_max], n_data REs in the
+ *                         order symbol (DMRS skipped) then subcarrier; entries
+ *                         at j >= m_u are ignored
+ *   bits_per_symbol_dev   device int32 [n_slots][U] (m_u)
+ *   cfg                   host; num_prb, num_users, DMRS symbols of the batch
+ * 2 <= m_max <= 8.
+ */
+nrx_status nrx_train_bce(int32_t n_slots, const nrx_slot_cfg* cfg, int32_t m_max, const float* llr,
+                         const uint8_t* bits, const int32_t* bits_per_symbol_dev, float scale, float* grad,
+                         double* loss, void* stream);
+
+/*
+ * Squared error of the channel-estimate read-out (Sec. II-B, double read-out):
+ *   *loss += scale * sum_i (h_hat[i] - h[i])^2;  grad[i] = 2 scale (h_hat[i] - h[i]).
+ */
+nrx_status nrx_train_mse(int64_t n, const float* h_hat, const float* h, float scale, float* grad, double* loss,
+                         void* stream);
+
+/* Asynchronous zero fill of `bytes` bytes at ptr (gradient and loss reset). */
+nrx_status nrx_train_zero(int64_t bytes, void* ptr, void* stream);
+
+/* Asynchronous device-to-device copy of `bytes` bytes (src and dst must not overlap). */
+nrx_status nrx_train_copy(int64_t bytes, void* dst, const void* src, void* stream);
+
+/*
+ * One Adam step on n FP32 weights, in place:
+ *   m1 = b1 m1 + (1-b1) g;  m2 = b2 m2 + (1-b2) g^2;  w -= lr_t m1 / (sqrt(m2) + eps)
+ * lr_t is the caller's bias-corrected step size lr sqrt(1-b2^t) / (1-b1^t).
+ */
+nrx_status nrx_train_adam(int64_t n, float* w, const float* g, float* m1, float* m2, float lr_t, float beta1,
+                          float beta2, float eps, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NRX_TRAIN_H_ */

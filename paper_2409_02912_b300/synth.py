@@ -343,3 +343,82 @@ def zero_like_residual(net: NetConfig, weights: Dict[str, np.ndarray]) -> Dict[s
 def stack_batch(slots: Sequence[Slot]) -> np.ndarray:
     """Contiguous complex64 [n_slots, B, 14, S] grid of same-shaped slots."""
     return np.stack([s.y for s in slots]).astype(np.complex64)
+
+
+# ----------------------------------------------------------------------------
+# Training data (Sec. II-B, Sec. IV-A)
+# ----------------------------------------------------------------------------
+
+
+def chest_layout(net: NetConfig) -> List[tuple]:
+    """(name, shape) of the training-only channel-estimate read-out
+    (ReadoutChEst, Sec. II-B): a two-layer MLP from the state to the 2B reals
+    [Re h_0, Im h_0, ..., Re h_{B-1}, Im h_{B-1}] of the user's channel."""
+    C, B2 = net.channels, 2 * net.num_rx_ant
+    return [("chest.1.w", (C, C)), ("chest.1.b", (C,)), ("chest.2.w", (B2, C)), ("chest.2.b", (B2,))]
+
+
+def make_chest_weights(net: NetConfig, seed: int = 43) -> Dict[str, np.ndarray]:
+    """Seeded He-normal initialisation of the ReadoutChEst head (float32)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = {}
+    for name, shape in chest_layout(net):
+        v = 0.01 * rng.standard_normal(shape) if name.endswith(".b") else \
+            np.sqrt(2.0 / shape[1]) * rng.standard_normal(shape)
+        out[name] = v.astype(np.float32)
+    return out
+
+
+def snr_offset_db(bits_per_symbol: Sequence[int]) -> float:
+    """SNR offset of a training sample (Sec. IV-A: samples with higher MCS and
+    more active users are drawn at higher SNR so they do not dominate the
+    batch loss).  The paper gives no values; this build uses +3 dB per two bits
+    of the users' mean modulation order above QPSK and +1 dB per additional
+    active user."""
+    m = float(np.mean(bits_per_symbol))
+    return 3.0 * (m - 2.0) / 2.0 + 1.0 * (len(bits_per_symbol) - 1)
+
+
+def training_slot(w: Workload, rng: np.random.Generator) -> Slot:
+    """One training sample: an i.i.d. uniform modulation order per user from
+    ``w.mcs_choices`` (random MCS-to-user association, Sec. IV-A), SNR uniform
+    in ``w.snr_db_range`` plus ``snr_offset_db``, channel draws as
+    ``draw_slot_config``."""
+    c = draw_slot_config(w, rng)
+    c = dataclasses.replace(c, snr_db=c.snr_db + snr_offset_db(c.bits_per_symbol))
+    return make_slot(c, rng)
+
+
+@dataclasses.dataclass
+class TrainingBatch:
+    """Same-geometry slots with their labels in the layouts the trainer reads."""
+
+    y: np.ndarray        # complex64 [n, B, 14, S]
+    dmrs: np.ndarray     # complex64 [n, n_dmrs, S/2]
+    bits: np.ndarray     # uint8 [n, U, n_data, m_max] (zero beyond m_u)
+    m_u: np.ndarray      # int32 [n, U]
+    h: np.ndarray        # float32 [n, U, 14, S, 2B]: true channel, Re/Im per antenna
+    dmrs_symbols: tuple
+    noise_var: np.ndarray  # float64 [n]
+
+
+def training_batch(slots: Sequence[Slot], m_max: int) -> TrainingBatch:
+    """Stack same-geometry slots into a ``TrainingBatch``."""
+    s0 = slots[0].cfg
+    n, U, S, B = len(slots), s0.num_users, s0.num_subcarriers, s0.num_rx_ant
+    n_data = s0.num_data_symbols * S
+    bits = np.zeros((n, U, n_data, m_max), dtype=np.uint8)
+    m_u = np.zeros((n, U), dtype=np.int32)
+    h = np.zeros((n, U, NUM_SYMBOLS, S, 2 * B), dtype=np.float32)
+    for i, sl in enumerate(slots):
+        assert sl.cfg.num_subcarriers == S and sl.cfg.num_users == U and sl.cfg.dmrs_symbols == s0.dmrs_symbols
+        for u in range(U):
+            m = sl.cfg.bits_per_symbol[u]
+            m_u[i, u] = m
+            bits[i, u, :, :m] = sl.bits[u]
+            hu = np.transpose(sl.h[u], (1, 2, 0))  # [14, S, B]
+            h[i, u, :, :, 0::2] = hu.real
+            h[i, u, :, :, 1::2] = hu.imag
+    return TrainingBatch(y=stack_batch(slots), dmrs=np.stack([s.dmrs for s in slots]), bits=bits, m_u=m_u, h=h,
+                         dmrs_symbols=tuple(s0.dmrs_symbols),
+                         noise_var=np.array([s.cfg.noise_var for s in slots]))

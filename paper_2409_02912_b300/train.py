@@ -1,0 +1,365 @@
+"""NRX training on the GPU (Sec. II-B): forward pass with saved activations,
+hand-written reverse pass and Adam, composed from the layer kernels of
+``include/nrx_train.h``.
+
+Loss: for every CGNN iteration k (multi-loss), the masked BCE of
+ReadoutLLRs(S^(k)) against the bits (mean over the batch's counted bits) plus
+gamma times the MSE of ReadoutChEst(S^(k)) against the true channel (mean over
+slot, user, antenna and RE of |h_hat - h|^2), summed over k.
+
+This module only marshals arguments and orders the launches: every arithmetic
+step (features, dense and depthwise layers and their gradients, aggregation,
+losses, Adam) runs in the CUDA kernels of ``libnrx.so``.  torch provides the
+device memory and the stream.  The FP32 master weights live in one flat device
+vector in the inference blob order followed by the ReadoutChEst head, so the
+trained network exports directly as a weight blob for ``nrx_create``.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import struct
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import nrx, synth
+
+TRAIN_EXPORTED = (
+    "nrx_train_features", "nrx_train_gemm", "nrx_train_colsum", "nrx_train_dw3", "nrx_train_dw3_wgrad",
+    "nrx_train_relu_mask", "nrx_train_aggregate", "nrx_train_axpy", "nrx_train_bce", "nrx_train_mse",
+    "nrx_train_zero", "nrx_train_copy", "nrx_train_adam",
+)
+
+_configured = False
+
+
+def load():
+    """``libnrx.so`` with the training entry points' signatures set."""
+    global _configured
+    lib = nrx.load()
+    if _configured:
+        return lib
+    P, I32, I64, F32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    CFG = ctypes.POINTER(nrx.nrx_slot_cfg)
+    sig = {
+        "nrx_train_features": [I32, I32, P, CFG, P, P],
+        "nrx_train_gemm": [I32, I32, I32, P, I64, I64, P, I64, I64, P, P, I64, P, I64, I32, I32, I32, P],
+        "nrx_train_colsum": [I32, I32, P, I64, P, P],
+        "nrx_train_dw3": [I32, I32, I32, P, P, I32, I32, P, P],
+        "nrx_train_dw3_wgrad": [I32, I32, I32, P, P, P, P],
+        "nrx_train_relu_mask": [I64, P, P, P],
+        "nrx_train_aggregate": [I32, I32, I64, P, P, P],
+        "nrx_train_axpy": [I64, F32, P, P, P],
+        "nrx_train_bce": [I32, CFG, I32, P, P, P, F32, P, P, P],
+        "nrx_train_mse": [I64, P, P, F32, P, P, P],
+        "nrx_train_zero": [I64, P, P],
+        "nrx_train_copy": [I64, P, P, P],
+        "nrx_train_adam": [I64, P, P, P, P, F32, F32, F32, F32, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    _configured = True
+    return lib
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+class _Ops:
+    """Thin wrappers: one C call each, raising on a non-OK status."""
+
+    def __init__(self, stream_ptr):
+        self.lib = load()
+        self.st = stream_ptr
+
+    def _ok(self, st, what):
+        if st != nrx.NRX_OK:
+            raise nrx.NrxError(st, what)
+
+    def gemm(self, M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias=None, R=None, ldr=0, relu=False,
+             accumulate=False, split_k=1):
+        self._ok(self.lib.nrx_train_gemm(M, N, K, A, sam, sak, B, sbk, sbn, bias, R, ldr, C, ldc, int(relu),
+                                         int(accumulate), split_k, self.st), "nrx_train_gemm")
+
+    def colsum(self, M, N, X, ldx, out):
+        self._ok(self.lib.nrx_train_colsum(M, N, X, ldx, out, self.st), "nrx_train_colsum")
+
+    def dw3(self, planes, S, C, X, k, Y, flip=False, relu=False):
+        self._ok(self.lib.nrx_train_dw3(planes, S, C, X, k, int(flip), int(relu), Y, self.st), "nrx_train_dw3")
+
+    def dw3_wgrad(self, planes, S, C, X, G, gk):
+        self._ok(self.lib.nrx_train_dw3_wgrad(planes, S, C, X, G, gk, self.st), "nrx_train_dw3_wgrad")
+
+    def relu_mask(self, n, G, Y):
+        self._ok(self.lib.nrx_train_relu_mask(n, G, Y, self.st), "nrx_train_relu_mask")
+
+    def aggregate(self, n_slots, U, per_user, m, a):
+        self._ok(self.lib.nrx_train_aggregate(n_slots, U, per_user, m, a, self.st), "nrx_train_aggregate")
+
+    def axpy(self, n, alpha, x, y):
+        self._ok(self.lib.nrx_train_axpy(n, alpha, x, y, self.st), "nrx_train_axpy")
+
+    def zero(self, nbytes, p):
+        self._ok(self.lib.nrx_train_zero(nbytes, p, self.st), "nrx_train_zero")
+
+    def copy(self, nbytes, dst, src):
+        self._ok(self.lib.nrx_train_copy(nbytes, dst, src, self.st), "nrx_train_copy")
+
+
+class Trainer:
+    """FP32 training state of one network (master weights, gradients, Adam
+    moments) on the current CUDA device.
+
+    ``loss_and_grad(batch)`` runs the forward and reverse passes and leaves the
+    gradient in ``self.g``; ``step(batch)`` adds the Adam update.
+    """
+
+    def __init__(self, net: synth.NetConfig, weights: Dict[str, np.ndarray],
+                 chest: Optional[Dict[str, np.ndarray]] = None, lr: float = 1e-3, gamma: float = 1.0,
+                 beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        import torch
+        self.torch = torch
+        self.net = net
+        self.lr, self.gamma, self.beta1, self.beta2, self.eps = lr, gamma, beta1, beta2, eps
+        chest = synth.make_chest_weights(net) if chest is None else chest
+        self.layout = synth.weight_layout(net) + synth.chest_layout(net)
+        self.offset: Dict[str, int] = {}
+        flat = []
+        o = 0
+        for name, shape in self.layout:
+            src = weights[name] if name in weights else chest[name]
+            a = np.ascontiguousarray(src, dtype=np.float32).reshape(-1)
+            assert a.size == int(np.prod(shape)), name
+            self.offset[name] = o
+            flat.append(a)
+            o += a.size
+        self.n_blob = sum(int(np.prod(s)) for _, s in synth.weight_layout(net))
+        self.n_total = o
+        dev = torch.device("cuda")
+        self.w = torch.from_numpy(np.concatenate(flat)).to(dev)
+        self.g = torch.zeros_like(self.w)
+        self.m1 = torch.zeros_like(self.w)
+        self.m2 = torch.zeros_like(self.w)
+        self.t = 0
+        self._bufs: Dict[tuple, dict] = {}
+        self.loss_dev = torch.zeros(2 * net.iterations, dtype=torch.float64, device=dev)
+
+    # -- weights ------------------------------------------------------------
+    def _wp(self, name: str) -> int:
+        return self.w.data_ptr() + 4 * self.offset[name]
+
+    def _gp(self, name: str) -> int:
+        return self.g.data_ptr() + 4 * self.offset[name]
+
+    def weights(self) -> Dict[str, np.ndarray]:
+        """Current master weights (float32 numpy, inference and head)."""
+        host = self.w.cpu().numpy()
+        return {n: host[self.offset[n]:self.offset[n] + int(np.prod(s))].reshape(s).copy() for n, s in self.layout}
+
+    def grads(self) -> Dict[str, np.ndarray]:
+        host = self.g.cpu().numpy()
+        return {n: host[self.offset[n]:self.offset[n] + int(np.prod(s))].reshape(s).copy() for n, s in self.layout}
+
+    def blob(self) -> bytes:
+        """Inference weight blob (nrx.h layout) of the current weights."""
+        net = self.net
+        hdr = struct.pack("<8i", synth.WEIGHT_MAGIC, synth.WEIGHT_VERSION, net.num_rx_ant, net.channels,
+                          net.res_blocks, net.iterations, net.m_max, self.n_blob)
+        return hdr + self.w[:self.n_blob].cpu().numpy().tobytes()
+
+    # -- buffers ------------------------------------------------------------
+    def _buffers(self, n, U, S):
+        key = (n, U, S)
+        if key in self._bufs:
+            return self._bufs[key]
+        torch = self.torch
+        net = self.net
+        C, F, R, K = net.channels, net.in_features, net.res_blocks, net.iterations
+        M = n * U * 14 * S
+        e = lambda w: torch.empty((M, w), dtype=torch.float32, device="cuda")  # noqa: E731
+        b = {"x": e(F), "P0": e(C), "S": [e(C) for _ in range(K + 1)],
+             "h1": [e(C) for _ in range(K)], "msg": [e(C) for _ in range(K)], "a": [e(C) for _ in range(K)],
+             "z": [[e(C) for _ in range(R + 1)] for _ in range(K)],
+             "d1": [[e(C) for _ in range(R)] for _ in range(K)],
+             "p1": [[e(C) for _ in range(R)] for _ in range(K)],
+             "d2": [[e(C) for _ in range(R)] for _ in range(K)],
+             "r1": [e(C) for _ in range(K)], "l": [e(net.m_max) for _ in range(K)],
+             "c1": [e(C) for _ in range(K)], "hh": [e(2 * net.num_rx_ant) for _ in range(K)],
+             "gS": e(C), "gz": e(C), "t1": e(C), "t2": e(C), "gl": e(net.m_max),
+             "ghh": e(2 * net.num_rx_ant)}
+        self._bufs = {key: b}  # keep one shape resident
+        return b
+
+    # -- forward / backward -------------------------------------------------
+    def loss_and_grad(self, batch: "DeviceBatch", stream=None) -> Dict[str, List[float]]:
+        """Forward + reverse pass over one batch; gradient left in ``self.g``.
+        Returns the per-iteration BCE and MSE means and the total loss."""
+        torch = self.torch
+        net = self.net
+        st = nrx._stream_ptr(stream)
+        ops = _Ops(st)
+        lib = ops.lib
+        n, U, S = batch.n, batch.U, batch.S
+        C, F, R, K, B = net.channels, net.in_features, net.res_blocks, net.iterations, net.num_rx_ant
+        mm = net.m_max
+        M = n * U * 14 * S
+        planes = n * U
+        bf = self._buffers(n, U, S)
+        p = lambda t: t.data_ptr()  # noqa: E731
+        wp, gp = self._wp, self._gp
+        split = max(1, min(1184, math.ceil(M / 128)))
+
+        ops.zero(4 * self.n_total, self.g.data_ptr())
+        ops.zero(8 * 2 * K, self.loss_dev.data_ptr())
+
+        def dense(X, ldx, name, in_dim, out_dim, Y, relu=False, R_=None, bias=True):
+            ops.gemm(M, out_dim, in_dim, X, ldx, 1, wp(name + ".w"), 1, in_dim, Y, out_dim,
+                     bias=wp(name + ".b") if bias else None, R=R_, ldr=out_dim if R_ else 0, relu=relu)
+
+        def dense_bwd(G, X, ldx, name, in_dim, out_dim, gX=None, accumulate_into_gX=False):
+            """G [M][out] gradient of y = W x + b: dW += G^T X, db += colsum G,
+            gX (=|+=) G W."""
+            ops.gemm(out_dim, in_dim, M, G, 1, out_dim, X, ldx, 1, gp(name + ".w"), in_dim,
+                     accumulate=True, split_k=split)
+            ops.colsum(M, out_dim, G, out_dim, gp(name + ".b"))
+            if gX is not None:
+                ops.gemm(M, in_dim, out_dim, G, out_dim, 1, wp(name + ".w"), in_dim, 1, gX, in_dim,
+                         R=gX if accumulate_into_gX else None, ldr=in_dim if accumulate_into_gX else 0)
+
+        # ---- forward ----
+        self._ok(lib.nrx_train_features(n, B, batch.y.data_ptr(), batch.cfgs, p(bf["x"]), st), "features")
+        dense(p(bf["x"]), F, "init.pw", F, C, p(bf["P0"]))
+        ops.dw3(planes, S, C, p(bf["P0"]), wp("init.dw"), p(bf["S"][0]), relu=True)
+        for k in range(K):
+            q = f"it{k}."
+            Sk = p(bf["S"][k])
+            dense(Sk, C, q + "mp1", C, C, p(bf["h1"][k]), relu=True)
+            dense(p(bf["h1"][k]), C, q + "mp2", C, C, p(bf["msg"][k]))
+            ops.aggregate(n, U, 14 * S * C, p(bf["msg"][k]), p(bf["a"][k]))
+            z0 = p(bf["z"][k][0])
+            W_in, D_in = wp(q + "in.w"), 2 * C + 2
+            ops.gemm(M, C, C, Sk, C, 1, W_in, 1, D_in, z0, C, bias=wp(q + "in.b"))
+            ops.gemm(M, C, C, p(bf["a"][k]), C, 1, W_in + 4 * C, 1, D_in, z0, C, R=z0, ldr=C)
+            ops.gemm(M, C, 2, p(bf["x"]) + 4 * 4 * B, F, 1, W_in + 4 * 2 * C, 1, D_in, z0, C, R=z0, ldr=C)
+            for r in range(R):
+                bq = f"{q}blk{r}."
+                zr, zn = p(bf["z"][k][r]), p(bf["z"][k][r + 1])
+                ops.dw3(planes, S, C, zr, wp(bq + "dw1"), p(bf["d1"][k][r]))
+                dense(p(bf["d1"][k][r]), C, bq + "pw1", C, C, p(bf["p1"][k][r]), relu=True)
+                ops.dw3(planes, S, C, p(bf["p1"][k][r]), wp(bq + "dw2"), p(bf["d2"][k][r]), relu=True)
+                dense(p(bf["d2"][k][r]), C, bq + "pw2", C, C, zn, R_=zr)
+            # S^(k+1) = S^(k) + z_R
+            ops.copy(4 * M * C, p(bf["S"][k + 1]), Sk)
+            ops.axpy(M * C, 1.0, p(bf["z"][k][R]), p(bf["S"][k + 1]))
+            # read-outs after iteration k (multi-loss)
+            Sn = p(bf["S"][k + 1])
+            dense(Sn, C, "ro1", C, C, p(bf["r1"][k]), relu=True)
+            dense(p(bf["r1"][k]), C, "ro2", C, mm, p(bf["l"][k]))
+            if self.gamma > 0:
+                dense(Sn, C, "chest.1", C, C, p(bf["c1"][k]), relu=True)
+                dense(p(bf["c1"][k]), C, "chest.2", C, 2 * B, p(bf["hh"][k]))
+
+        # ---- reverse ----
+        gS, gz, t1, t2 = p(bf["gS"]), p(bf["gz"]), p(bf["t1"]), p(bf["t2"])
+        ops.zero(4 * M * C, gS)
+        n_bits = float(batch.n_bits)
+        n_mse = float(n * U * 14 * S * B)
+        for k in reversed(range(K)):
+            q = f"it{k}."
+            Sn = p(bf["S"][k + 1])
+            # LLR read-out k
+            gl = p(bf["gl"])
+            self._ok(lib.nrx_train_bce(n, batch.cfgs, mm, p(bf["l"][k]), batch.bits.data_ptr(),
+                                       batch.m_u.data_ptr(), 1.0 / n_bits, gl,
+                                       self.loss_dev.data_ptr() + 8 * k, st), "bce")
+            dense_bwd(gl, p(bf["r1"][k]), C, "ro2", C, mm, gX=t1)
+            ops.relu_mask(M * C, t1, p(bf["r1"][k]))
+            dense_bwd(t1, Sn, C, "ro1", C, C, gX=gS, accumulate_into_gX=True)
+            if self.gamma > 0:
+                ghh = p(bf["ghh"])
+                self._ok(lib.nrx_train_mse(M * 2 * B, p(bf["hh"][k]), batch.h.data_ptr(), self.gamma / n_mse, ghh,
+                                           self.loss_dev.data_ptr() + 8 * (K + k), st), "mse")
+                dense_bwd(ghh, p(bf["c1"][k]), C, "chest.2", C, 2 * B, gX=t1)
+                ops.relu_mask(M * C, t1, p(bf["c1"][k]))
+                dense_bwd(t1, Sn, C, "chest.1", C, C, gX=gS, accumulate_into_gX=True)
+            # CNN update: S^(k+1) = S^(k) + z_R; gradient of z_R is gS
+            ops.copy(4 * M * C, gz, gS)
+            for r in reversed(range(R)):
+                bq = f"{q}blk{r}."
+                d1, p1, d2 = p(bf["d1"][k][r]), p(bf["p1"][k][r]), p(bf["d2"][k][r])
+                dense_bwd(gz, d2, C, bq + "pw2", C, C, gX=t1)
+                ops.relu_mask(M * C, t1, d2)
+                ops.dw3(planes, S, C, t1, wp(bq + "dw2"), t2, flip=True)
+                ops.dw3_wgrad(planes, S, C, p1, t1, gp(bq + "dw2"))
+                ops.relu_mask(M * C, t2, p1)
+                dense_bwd(t2, d1, C, bq + "pw1", C, C, gX=t1)
+                ops.dw3(planes, S, C, t1, wp(bq + "dw1"), t2, flip=True)
+                ops.dw3_wgrad(planes, S, C, p(bf["z"][k][r]), t1, gp(bq + "dw1"))
+                ops.axpy(M * C, 1.0, t2, gz)
+            # z0 = in([S, a, PE])
+            Sk, ak = p(bf["S"][k]), p(bf["a"][k])
+            W_in, G_in, D_in = wp(q + "in.w"), gp(q + "in.w"), 2 * C + 2
+            ops.gemm(M, C, C, gz, C, 1, W_in, D_in, 1, gS, C, R=gS, ldr=C)
+            ops.gemm(M, C, C, gz, C, 1, W_in + 4 * C, D_in, 1, t1, C)  # gradient of a
+            ops.gemm(C, C, M, gz, 1, C, Sk, C, 1, G_in, D_in, accumulate=True, split_k=split)
+            ops.gemm(C, C, M, gz, 1, C, ak, C, 1, G_in + 4 * C, D_in, accumulate=True, split_k=split)
+            ops.gemm(C, 2, M, gz, 1, C, p(bf["x"]) + 4 * 4 * B, F, 1, G_in + 4 * 2 * C, D_in, accumulate=True,
+                     split_k=split)
+            ops.colsum(M, C, gz, C, gp(q + "in.b"))
+            # messages: a = sum over the other users (symmetric)
+            ops.aggregate(n, U, 14 * S * C, t1, t2)
+            dense_bwd(t2, p(bf["h1"][k]), C, q + "mp2", C, C, gX=t1)
+            ops.relu_mask(M * C, t1, p(bf["h1"][k]))
+            dense_bwd(t1, Sk, C, q + "mp1", C, C, gX=gS, accumulate_into_gX=True)
+        # StateInit: S0 = ReLU(DW(P0)), P0 = PW(x)
+        ops.relu_mask(M * C, gS, p(bf["S"][0]))
+        ops.dw3(planes, S, C, gS, wp("init.dw"), t1, flip=True)
+        ops.dw3_wgrad(planes, S, C, p(bf["P0"]), gS, gp("init.dw"))
+        dense_bwd(t1, p(bf["x"]), F, "init.pw", F, C)
+
+        ld = self.loss_dev.cpu().numpy()
+        bce = [float(v) for v in ld[:K]]
+        mse = [float(v) / self.gamma for v in ld[K:]] if self.gamma > 0 else [0.0] * K
+        return {"bce": bce, "mse": mse, "loss": float(sum(bce) + self.gamma * sum(mse))}
+
+    def step(self, batch: "DeviceBatch", stream=None) -> Dict[str, List[float]]:
+        """One training step: loss, gradient, Adam update of the master weights."""
+        out = self.loss_and_grad(batch, stream)
+        self.t += 1
+        lr_t = self.lr * math.sqrt(1.0 - self.beta2 ** self.t) / (1.0 - self.beta1 ** self.t)
+        lib = load()
+        st = lib.nrx_train_adam(self.n_total, self.w.data_ptr(), self.g.data_ptr(), self.m1.data_ptr(),
+                                self.m2.data_ptr(), lr_t, self.beta1, self.beta2, self.eps, nrx._stream_ptr(stream))
+        self._ok(st, "adam")
+        return out
+
+    @staticmethod
+    def _ok(st, what):
+        if st != nrx.NRX_OK:
+            raise nrx.NrxError(st, what)
+
+
+class DeviceBatch:
+    """A ``synth.TrainingBatch`` resident on the GPU, with its slot configs."""
+
+    def __init__(self, tb: synth.TrainingBatch):
+        import torch
+        dev = torch.device("cuda")
+        self.n, self.B = tb.y.shape[0], tb.y.shape[1]
+        self.S = tb.y.shape[3]
+        self.U = tb.m_u.shape[1]
+        assert self.n <= 64, "at most 64 slots per batch"
+        self.y = torch.from_numpy(np.ascontiguousarray(tb.y)).to(dev)
+        self.dmrs = torch.from_numpy(np.ascontiguousarray(tb.dmrs)).to(dev)
+        self.bits = torch.from_numpy(np.ascontiguousarray(tb.bits)).to(dev)
+        self.m_u = torch.from_numpy(np.ascontiguousarray(tb.m_u)).to(dev)
+        self.h = torch.from_numpy(np.ascontiguousarray(tb.h)).to(dev)
+        self.dmrs_symbols = tb.dmrs_symbols
+        self.n_data = (14 - len(tb.dmrs_symbols)) * self.S
+        self.n_bits = int(self.n_data * tb.m_u.sum())
+        self.cfgs = nrx.make_cfgs(self.n, self.S // 12, self.U, tb.dmrs_symbols,
+                                  [self.dmrs[i].data_ptr() for i in range(self.n)], tb.noise_var)

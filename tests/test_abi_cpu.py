@@ -1,6 +1,7 @@
 """The C-ABI library loads, exports every symbol include/nrx.h declares, and
 its host-side validation works without a GPU (no compute calls here)."""
 import ctypes
+import glob
 import os
 import re
 
@@ -8,7 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2409_02912_b300 import build as nrx_build
-from paper_2409_02912_b300 import nrx, synth
+from paper_2409_02912_b300 import nrx, synth, train
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -20,14 +21,35 @@ def lib():
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "nrx.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?(?:nrx_status|void|size_t|int32_t|char\s*\*|char)\s*\*?\s*(\w+)\s*\(",
-                                 text, flags=re.M)))
+    names = set()
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(
+            r"^\s*(?:const\s+)?(?:nrx_status|void|size_t|int32_t|char\s*\*|char)\s*\*?\s*(\w+)\s*\(",
+            text, flags=re.M))
+    return sorted(names)
 
 
 def test_header_declares_the_binding_exports():
-    assert sorted(nrx.EXPORTED) == declared_functions()
+    assert sorted(nrx.EXPORTED + train.TRAIN_EXPORTED) == declared_functions()
+
+
+def test_training_entry_points_validate_without_a_gpu(lib):
+    """Host-side argument checks of the training ABI run before any launch."""
+    tl = train.load()
+    assert tl.nrx_train_gemm(0, 4, 4, 1, 4, 1, 1, 1, 4, None, None, 0, 1, 4, 0, 0, 1, None) == nrx.NRX_EINVAL
+    # split K without accumulation, accumulation with an epilogue
+    assert tl.nrx_train_gemm(4, 4, 4, 1, 4, 1, 1, 1, 4, None, None, 0, 1, 4, 0, 0, 2, None) == nrx.NRX_EINVAL
+    assert tl.nrx_train_gemm(4, 4, 4, 1, 4, 1, 1, 1, 4, 1, None, 0, 1, 4, 0, 1, 1, None) == nrx.NRX_EINVAL
+    assert tl.nrx_train_aggregate(1, 5, 16, 1, 2, None) == nrx.NRX_EINVAL
+    assert tl.nrx_train_aggregate(1, 2, 16, 1, 1, None) == nrx.NRX_EINVAL
+    assert tl.nrx_train_dw3(0, 12, 4, 1, 1, 0, 0, 2, None) == nrx.NRX_EINVAL
+    assert tl.nrx_train_adam(0, 1, 1, 1, 1, 1e-3, 0.9, 0.999, 1e-8, None) == nrx.NRX_EINVAL
+    assert tl.nrx_train_zero(0, None, None) == nrx.NRX_OK
+    assert tl.nrx_train_zero(-1, None, None) == nrx.NRX_EINVAL
+    cfg = nrx.make_cfgs(1, 4, 2, (2, 11), [0], [1.0])
+    assert tl.nrx_train_features(1, 2, 1, cfg, 1, None) == nrx.NRX_EINVAL   # null DMRS pointer
+    assert tl.nrx_train_bce(1, cfg, 9, 1, 1, 1, 1.0, 1, 1, None) == nrx.NRX_EINVAL
 
 
 def test_library_exports_every_declared_symbol(lib):

@@ -1,0 +1,200 @@
+"""Training path on the GPU (Sec. II-B): the layer kernels against plain
+definitions, the trainer's loss and gradient against the FP64 training oracle
+(torch autograd, pinned by finite differences), Adam against its definition,
+the exported blob against the inference path, and a short training run."""
+import numpy as np
+import pytest
+
+from oracle import nrx_oracle as O
+from oracle import nrx_train_oracle as TO
+from paper_2409_02912_b300 import nrx, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from paper_2409_02912_b300 import train  # noqa: E402
+
+# FP32 kernels with float-atomic reductions against FP64: the gradient of each
+# tensor must match to 1e-4 of its norm (FP32 unit roundoff 6e-8 times the
+# depth and reduction lengths of these small cases, with margin).
+TOL_GRAD = 1e-4
+TOL_LOSS = 1e-5
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _slots(net, U, bits, n, prb, dmrs, seed, snr=6.0):
+    out = []
+    for i in range(n):
+        rng = np.random.Generator(np.random.PCG64(seed * 100 + i))
+        cfg = synth.SlotConfig(num_prb=prb, num_users=U, num_rx_ant=net.num_rx_ant, dmrs_symbols=dmrs,
+                               bits_per_symbol=tuple(bits[:U]), snr_db=snr, num_taps=6, delay_spread_s=200e-9,
+                               doppler_hz=150.0, ula=True)
+        out.append(synth.make_slot(cfg, rng))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Layer kernels against their definitions
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (130, 70, 37), (64, 64, 64), (300, 9, 130)])
+def test_gemm_strided_epilogues(M, N, K):
+    rng = np.random.Generator(np.random.PCG64(M * 7 + N))
+    ops = train._Ops(torch.cuda.current_stream().cuda_stream)
+    A = rng.standard_normal((M, K + 3)).astype(np.float32)        # row stride K+3
+    W = rng.standard_normal((N, K)).astype(np.float32)            # B(k,n) = W[n][k]
+    bias = rng.standard_normal(N).astype(np.float32)
+    Rm = rng.standard_normal((M, N)).astype(np.float32)
+    dA, dW, db, dR = _t(A), _t(W), _t(bias), _t(Rm)
+    out = torch.empty((M, N), device="cuda")
+    ops.gemm(M, N, K, dA.data_ptr(), K + 3, 1, dW.data_ptr(), 1, K, out.data_ptr(), N, bias=db.data_ptr(),
+             R=dR.data_ptr(), ldr=N, relu=True)
+    ref = np.maximum(A[:, :K].astype(np.float64) @ W.T.astype(np.float64) + bias + Rm, 0.0)
+    assert np.max(np.abs(out.cpu().numpy() - ref)) < 1e-5 * max(1.0, np.max(np.abs(ref)))
+    # transposed operand (weight-gradient form), split K with atomics, into a strided slice
+    G = rng.standard_normal((K, M)).astype(np.float32)            # A(m,k) = G[k][m]
+    X = rng.standard_normal((K, N)).astype(np.float32)
+    acc0 = rng.standard_normal((M, N + 5)).astype(np.float32)
+    dG, dX, dacc = _t(G), _t(X), _t(acc0)
+    ops.gemm(M, N, K, dG.data_ptr(), 1, M, dX.data_ptr(), N, 1, dacc.data_ptr(), N + 5, accumulate=True,
+             split_k=3)
+    ref2 = acc0.astype(np.float64)
+    ref2[:, :N] += G.T.astype(np.float64) @ X.astype(np.float64)
+    assert np.max(np.abs(dacc.cpu().numpy() - ref2)) < 1e-5 * max(1.0, np.max(np.abs(ref2)))
+
+
+@pytest.mark.parametrize("planes,S,C", [(1, 12, 1), (3, 24, 5), (2, 36, 64)])
+def test_depthwise_forward_adjoint_and_tap_gradient(planes, S, C):
+    rng = np.random.Generator(np.random.PCG64(planes * 31 + S + C))
+    ops = train._Ops(torch.cuda.current_stream().cuda_stream)
+    X = rng.standard_normal((planes, 14, S, C)).astype(np.float32)
+    G = rng.standard_normal((planes, 14, S, C)).astype(np.float32)
+    k = rng.standard_normal((C, 3, 3)).astype(np.float32)
+    dX, dG, dk = _t(X), _t(G), _t(k)
+    Y = torch.empty_like(dX)
+    ops.dw3(planes, S, C, dX.data_ptr(), dk.data_ptr(), Y.data_ptr())
+    ref = np.stack([O.depthwise3x3(X[p].astype(np.float64), k) for p in range(planes)])
+    assert np.max(np.abs(Y.cpu().numpy() - ref)) < 1e-5 * np.max(np.abs(ref))
+    # adjoint: <DW(X), G> == <X, DW^T(G)>
+    ops.dw3(planes, S, C, dG.data_ptr(), dk.data_ptr(), Y.data_ptr(), flip=True)
+    lhs = np.sum(ref * G.astype(np.float64))
+    rhs = np.sum(X.astype(np.float64) * Y.cpu().numpy().astype(np.float64))
+    assert abs(lhs - rhs) < 1e-4 * max(1.0, abs(lhs))
+    # tap gradient: d<DW(X), G>/dk[c,i,j] = sum G * shifted X (brute force)
+    gk = torch.zeros((C, 3, 3), device="cuda")
+    ops.dw3_wgrad(planes, S, C, dX.data_ptr(), dG.data_ptr(), gk.data_ptr())
+    Xp = np.zeros((planes, 16, S + 2, C))
+    Xp[:, 1:-1, 1:-1] = X
+    refk = np.zeros((C, 3, 3))
+    for i in range(3):
+        for j in range(3):
+            refk[:, i, j] = np.sum(G * Xp[:, i:i + 14, j:j + S], axis=(0, 1, 2))
+    assert np.max(np.abs(gk.cpu().numpy() - refk)) < 1e-4 * max(1.0, np.max(np.abs(refk)))
+
+
+@pytest.mark.parametrize("U", [1, 2, 3, 4])
+def test_aggregate_is_sum_over_other_users(U):
+    rng = np.random.Generator(np.random.PCG64(U))
+    ops = train._Ops(torch.cuda.current_stream().cuda_stream)
+    m = rng.standard_normal((2, U, 14, 12, 8)).astype(np.float32)
+    dm = _t(m)
+    a = torch.empty_like(dm)
+    ops.aggregate(2, U, 14 * 12 * 8, dm.data_ptr(), a.data_ptr())
+    ref = np.stack([O.aggregate(m[s].astype(np.float64), list(range(U))) for s in range(2)])
+    assert np.max(np.abs(a.cpu().numpy() - ref)) < 1e-5
+
+
+def test_adam_kernel_matches_definition():
+    rng = np.random.Generator(np.random.PCG64(29))
+    n = 10007
+    w, g = rng.standard_normal(n), rng.standard_normal(n)
+    m1, m2 = 0.1 * rng.standard_normal(n), np.abs(rng.standard_normal(n))
+    t, lr = 7, 3e-3
+    ref_w, ref_m1, ref_m2 = TO.adam_step(w, g, m1, m2, t, lr)
+    dw, dg, dm1, dm2 = (_t(v.astype(np.float32)) for v in (w, g, m1, m2))
+    lr_t = lr * np.sqrt(1 - 0.999 ** t) / (1 - 0.9 ** t)
+    lib = train.load()
+    st = lib.nrx_train_adam(n, dw.data_ptr(), dg.data_ptr(), dm1.data_ptr(), dm2.data_ptr(), lr_t, 0.9, 0.999,
+                            1e-8, torch.cuda.current_stream().cuda_stream)
+    assert st == nrx.NRX_OK
+    assert np.max(np.abs(dm1.cpu().numpy() - ref_m1)) < 1e-6
+    assert np.max(np.abs(dm2.cpu().numpy() - ref_m2)) < 1e-5
+    assert np.max(np.abs(dw.cpu().numpy() - ref_w)) < 1e-6
+
+
+# ----------------------------------------------------------------------------
+# Loss and gradient against the FP64 training oracle
+# ----------------------------------------------------------------------------
+
+GRAD_CASES = [
+    # (B, C, R, N_it, m_max, U, bits, prb, dmrs, n_slots, gamma)
+    (2, 8, 1, 2, 4, 2, (2, 4), 2, (2, 11), 2, 0.5),
+    (2, 16, 2, 2, 6, 4, (2, 4, 6, 4), 1, (2, 11), 1, 1.0),
+    (4, 8, 2, 1, 4, 1, (4,), 3, (2,), 2, 0.0),
+    (1, 8, 1, 3, 2, 3, (2, 2, 2), 2, (3, 12), 1, 2.0),
+]
+
+
+@pytest.mark.parametrize("case", GRAD_CASES, ids=[f"B{c[0]}C{c[1]}U{c[5]}" for c in GRAD_CASES])
+def test_trainer_loss_and_gradient_match_oracle(case):
+    B, C, R, K, mm, U, bits, prb, dmrs, n, gamma = case
+    net = synth.NetConfig(num_rx_ant=B, channels=C, res_blocks=R, iterations=K, m_max=mm)
+    W = synth.make_weights(net, seed=5)
+    Wc = synth.make_chest_weights(net, seed=6)
+    sl = _slots(net, U, bits, n, prb, dmrs, seed=C + U)
+    ref_loss, ref_g = TO.training_grads(sl, W, Wc, K, R, gamma)
+    tr = train.Trainer(net, W, Wc, gamma=gamma)
+    out = tr.loss_and_grad(train.DeviceBatch(synth.training_batch(sl, mm)))
+    assert abs(out["loss"] - ref_loss) < TOL_LOSS * max(1.0, abs(ref_loss))
+    ref_total, ref_bce, ref_mse = TO.training_loss(sl, W, Wc, K, R, gamma)
+    assert np.allclose(out["bce"], ref_bce, rtol=TOL_LOSS)
+    if gamma > 0:
+        assert np.allclose(out["mse"], ref_mse, rtol=TOL_LOSS)
+    g = tr.grads()
+    for name, ref in ref_g.items():
+        nrm = np.linalg.norm(ref)
+        err = np.linalg.norm(g[name] - ref)
+        if nrm == 0.0:
+            assert err == 0.0, name
+        else:
+            assert err <= TOL_GRAD * nrm, (name, err / nrm)
+
+
+def test_exported_blob_runs_the_same_network_in_the_inference_path():
+    """The trainer's FP32 weights, exported as a blob, give inference LLRs whose
+    masked BCE equals the trainer's last-iteration BCE."""
+    net = synth.NetConfig(num_rx_ant=4, channels=64, res_blocks=2, iterations=2, m_max=6)
+    W = synth.make_weights(net, seed=8)
+    sl = _slots(net, 2, (2, 6), 3, 4, (2, 11), seed=4)
+    tr = train.Trainer(net, W, gamma=0.0)
+    out = tr.loss_and_grad(train.DeviceBatch(synth.training_batch(sl, 6)))
+    rx = nrx.Receiver(tr.blob(), 4, 2, 4, max_slots=3, precision="fp32")
+    y = _t(synth.stack_batch(sl))
+    dm = _t(np.stack([s.dmrs for s in sl]))
+    llr = rx.nrx_detect_batch(y, dm, (2, 11), [[2, 6]] * 3).cpu().numpy().astype(np.float64)
+    bits = np.concatenate([np.concatenate([s.bits[0].reshape(-1), s.bits[1].reshape(-1)]) for s in sl])
+    bce = float(np.mean(TO.softplus(llr) - bits * llr))
+    assert abs(bce - out["bce"][-1]) < 1e-5 * bce
+
+
+def test_training_reduces_the_loss():
+    """A few hundred Adam steps on fresh random slots lower the BCE of a
+    randomly initialised NRX (2 users, 4 Rx, QPSK/16-QAM mix)."""
+    w = synth.Workload(name="train_mu2", seed_base=50, batch=8, num_prb=4, num_users=2, num_rx_ant=4,
+                       dmrs_symbols=(2, 11), mcs_choices=(2, 4), snr_db_range=(5.0, 15.0), num_taps=8,
+                       delay_spread_range_s=(30e-9, 200e-9), doppler_range_hz=(0.0, 200.0), ula=True,
+                       net=synth.NetConfig(num_rx_ant=4, channels=32, res_blocks=1, iterations=2, m_max=4))
+    tr = train.Trainer(w.net, synth.make_weights(w.net, seed=1), lr=2e-3, gamma=0.5)
+    rng = np.random.Generator(np.random.PCG64(77))
+    val = train.DeviceBatch(synth.training_batch([synth.training_slot(w, rng) for _ in range(8)], 4))
+    before = tr.loss_and_grad(val)["bce"][-1]
+    for _ in range(300):
+        tr.step(train.DeviceBatch(synth.training_batch([synth.training_slot(w, rng) for _ in range(8)], 4)))
+    after = tr.loss_and_grad(val)["bce"][-1]
+    assert np.isfinite(after) and after < 0.75 * before, (before, after)
