@@ -102,11 +102,13 @@ nrx_status nrx_train_axpy(int64_t n, float alpha, const float* x, float* y, void
 
 /*
  * Masked BCE of one LLR read-out (Sec. II-B; LLR sign of Eq. 2, so
- * P(b=1) = sigmoid(l)):
- *   *loss += scale * sum (softplus(l) - b l)     (FP64 accumulation)
- *   grad   = scale * (sigmoid(l) - b)             on counted entries, else 0
+ * P(b=1) = sigmoid(l)), as a mean over the counted bits:
+ *   *loss += weight / n_bits * sum (softplus(l) - b l)     (FP64 accumulation)
+ *   grad   = weight / n_bits * (sigmoid(l) - b)             on counted entries, else 0
  * over the data REs (DMRS symbols of cfg skipped) and the first m_u outputs of
- * each user (Var-MCS masking, Sec. III).
+ * each user (Var-MCS masking, Sec. III); n_bits = n_data * sum of m_u over the
+ * batch, computed on the device from bits_per_symbol_dev (so a captured graph
+ * stays valid when the modulation orders of the batch change).
  *   llr, grad             [n_slots][U][14][S][m_max]
  *   bits                  uint8 [n_slots][U][n_data][m_max], n_data REs in the
  *                         order symbol (DMRS skipped) then subcarrier; entries
@@ -116,7 +118,7 @@ nrx_status nrx_train_axpy(int64_t n, float alpha, const float* x, float* y, void
  * 2 <= m_max <= 8.
  */
 nrx_status nrx_train_bce(int32_t n_slots, const nrx_slot_cfg* cfg, int32_t m_max, const float* llr,
-                         const uint8_t* bits, const int32_t* bits_per_symbol_dev, float scale, float* grad,
+                         const uint8_t* bits, const int32_t* bits_per_symbol_dev, float weight, float* grad,
                          double* loss, void* stream);
 
 /*
@@ -129,16 +131,21 @@ nrx_status nrx_train_mse(int64_t n, const float* h_hat, const float* h, float sc
 /* Asynchronous zero fill of `bytes` bytes at ptr (gradient and loss reset). */
 nrx_status nrx_train_zero(int64_t bytes, void* ptr, void* stream);
 
-/* Asynchronous device-to-device copy of `bytes` bytes (src and dst must not overlap). */
+/* Asynchronous copy of `bytes` bytes between any two of device, pinned-host or
+ * pageable-host memory (direction inferred from the unified address space;
+ * pageable host memory makes the copy synchronous).  src and dst must not
+ * overlap.  Used for the gradient-path copies and the batch uploads. */
 nrx_status nrx_train_copy(int64_t bytes, void* dst, const void* src, void* stream);
 
 /*
  * One Adam step on n FP32 weights, in place:
  *   m1 = b1 m1 + (1-b1) g;  m2 = b2 m2 + (1-b2) g^2;  w -= lr_t m1 / (sqrt(m2) + eps)
- * lr_t is the caller's bias-corrected step size lr sqrt(1-b2^t) / (1-b1^t).
+ * lr_t points to one float in device memory: the caller's bias-corrected step
+ * size lr sqrt(1-b2^t) / (1-b1^t), read when the kernel runs (so a captured
+ * CUDA graph of the training step picks up each step's value).
  */
-nrx_status nrx_train_adam(int64_t n, float* w, const float* g, float* m1, float* m2, float lr_t, float beta1,
-                          float beta2, float eps, void* stream);
+nrx_status nrx_train_adam(int64_t n, float* w, const float* g, float* m1, float* m2, const float* lr_t,
+                          float beta1, float beta2, float eps, void* stream);
 
 #ifdef __cplusplus
 }

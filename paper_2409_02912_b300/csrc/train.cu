@@ -209,12 +209,21 @@ __global__ void k_axpy(size_t n, float alpha, const float* __restrict__ x, float
     y[i] = fmaf(alpha, x[i], y[i]);
 }
 
-// Masked BCE on the logits of Eq. 2 (Sec. II-B): data REs, first m_u bits.
-//   loss += scale * (softplus(l) - b l); grad = scale * (sigmoid(l) - b).
+// Masked BCE on the logits of Eq. 2 (Sec. II-B): data REs, first m_u bits,
+// normalised by the number of counted bits n_bits = n_data * sum m_u:
+//   loss += weight/n_bits * (softplus(l) - b l); grad = weight/n_bits * (sigmoid(l) - b).
 // l, grad: [n][U][14][S][m_max]; bits: [n][U][n_data][m_max]; m: [n][U].
 __global__ void k_bce(Geometry g, const float* __restrict__ l, const uint8_t* __restrict__ bits,
-                      const int32_t* __restrict__ m_u, float scale, float* __restrict__ grad,
+                      const int32_t* __restrict__ m_u, float weight, float* __restrict__ grad,
                       double* __restrict__ loss) {
+  __shared__ float s_scale;
+  if (threadIdx.x == 0) {
+    long long sum_m = 0;
+    for (int i = 0; i < g.n_slots * g.U; ++i) sum_m += m_u[i];
+    s_scale = sum_m > 0 ? (float)((double)weight / ((double)g.n_data * (double)sum_m)) : 0.f;
+  }
+  __syncthreads();
+  const float scale = s_scale;
   const size_t total = (size_t)g.n_slots * g.U * NRX_SYMBOLS * g.S * g.m_max;
   double part = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
@@ -256,7 +265,8 @@ __global__ void k_mse(size_t n, const float* __restrict__ h_hat, const float* __
 
 // Adam on FP32 master weights (bias-corrected step sizes passed in).
 __global__ void k_adam(size_t n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m1,
-                       float* __restrict__ m2, float lr_t, float b1, float b2, float eps) {
+                       float* __restrict__ m2, const float* __restrict__ lr_t_dev, float b1, float b2, float eps) {
+  const float lr_t = *lr_t_dev;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float a = b1 * m1[i] + (1.f - b1) * gi;
@@ -366,7 +376,7 @@ nrx_status nrx_train_axpy(int64_t n, float alpha, const float* x, float* y, void
 }
 
 nrx_status nrx_train_bce(int32_t n_slots, const nrx_slot_cfg* cfg, int32_t m_max, const float* llr,
-                         const uint8_t* bits, const int32_t* bits_per_symbol_dev, float scale, float* grad,
+                         const uint8_t* bits, const int32_t* bits_per_symbol_dev, float weight, float* grad,
                          double* loss, void* stream) {
   if (n_slots < 1 || !cfg || m_max < 2 || m_max > 8 || !llr || !bits || !bits_per_symbol_dev || !grad || !loss)
     return NRX_EINVAL;
@@ -383,7 +393,7 @@ nrx_status nrx_train_bce(int32_t n_slots, const nrx_slot_cfg* cfg, int32_t m_max
   for (int t = 0, di = 0; t < NRX_SYMBOLS; ++t)
     if (t != g.td0 && t != g.td1) g.data_t[di++] = (int8_t)t;
   const size_t n = (size_t)n_slots * g.U * NRX_SYMBOLS * g.S * m_max;
-  k_bce<<<blocks_for(n), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(g, llr, bits, bits_per_symbol_dev, scale,
+  k_bce<<<blocks_for(n), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(g, llr, bits, bits_per_symbol_dev, weight,
                                                                           grad, loss);
   return to_status(cudaGetLastError());
 }
@@ -405,13 +415,12 @@ nrx_status nrx_train_zero(int64_t bytes, void* ptr, void* stream) {
 nrx_status nrx_train_copy(int64_t bytes, void* dst, const void* src, void* stream) {
   if (bytes < 0 || (bytes > 0 && (!dst || !src))) return NRX_EINVAL;
   if (bytes == 0) return NRX_OK;
-  return to_status(
-      cudaMemcpyAsync(dst, src, (size_t)bytes, cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+  return to_status(cudaMemcpyAsync(dst, src, (size_t)bytes, cudaMemcpyDefault, static_cast<cudaStream_t>(stream)));
 }
 
-nrx_status nrx_train_adam(int64_t n, float* w, const float* g, float* m1, float* m2, float lr_t, float beta1,
-                          float beta2, float eps, void* stream) {
-  if (n < 1 || !w || !g || !m1 || !m2) return NRX_EINVAL;
+nrx_status nrx_train_adam(int64_t n, float* w, const float* g, float* m1, float* m2, const float* lr_t,
+                          float beta1, float beta2, float eps, void* stream) {
+  if (n < 1 || !w || !g || !m1 || !m2 || !lr_t) return NRX_EINVAL;
   k_adam<<<blocks_for((size_t)n), kThreads, 0, static_cast<cudaStream_t>(stream)>>>((size_t)n, w, g, m1, m2, lr_t,
                                                                                    beta1, beta2, eps);
   return to_status(cudaGetLastError());

@@ -55,7 +55,7 @@ def load():
         "nrx_train_mse": [I64, P, P, F32, P, P, P],
         "nrx_train_zero": [I64, P, P],
         "nrx_train_copy": [I64, P, P, P],
-        "nrx_train_adam": [I64, P, P, P, P, F32, F32, F32, F32, P],
+        "nrx_train_adam": [I64, P, P, P, P, P, F32, F32, F32, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -147,6 +147,11 @@ class Trainer:
         self.t = 0
         self._bufs: Dict[tuple, dict] = {}
         self.loss_dev = torch.zeros(2 * net.iterations, dtype=torch.float64, device=dev)
+        self.lr_t_dev = torch.zeros(1, dtype=torch.float32, device=dev)
+        self._lr_host = torch.zeros(1, dtype=torch.float32).pin_memory()
+        self._graph = None
+        self._graph_shape = None
+        self._static = None
 
     # -- weights ------------------------------------------------------------
     def _wp(self, name: str) -> int:
@@ -163,6 +168,25 @@ class Trainer:
     def grads(self) -> Dict[str, np.ndarray]:
         host = self.g.cpu().numpy()
         return {n: host[self.offset[n]:self.offset[n] + int(np.prod(s))].reshape(s).copy() for n, s in self.layout}
+
+    def save(self, path: str):
+        """Checkpoint (weights, Adam moments, step count, hyper-parameters) to
+        an ``.npz`` file."""
+        net = self.net
+        np.savez(path, w=self.w.cpu().numpy(), m1=self.m1.cpu().numpy(), m2=self.m2.cpu().numpy(),
+                 t=np.int64(self.t), net=np.array([net.num_rx_ant, net.channels, net.res_blocks, net.iterations,
+                                                   net.m_max], dtype=np.int64))
+
+    def restore(self, path: str):
+        """Resume from a ``save`` checkpoint of the same network shape."""
+        z = np.load(path)
+        net = self.net
+        want = [net.num_rx_ant, net.channels, net.res_blocks, net.iterations, net.m_max]
+        if list(z["net"]) != want or z["w"].size != self.n_total:
+            raise ValueError(f"checkpoint is for network {list(z['net'])}, not {want}")
+        for dst, key in ((self.w, "w"), (self.m1, "m1"), (self.m2, "m2")):
+            dst.copy_(self.torch.from_numpy(z[key]))
+        self.t = int(z["t"])
 
     def blob(self) -> bytes:
         """Inference weight blob (nrx.h layout) of the current weights."""
@@ -195,12 +219,12 @@ class Trainer:
         return b
 
     # -- forward / backward -------------------------------------------------
-    def loss_and_grad(self, batch: "DeviceBatch", stream=None) -> Dict[str, List[float]]:
-        """Forward + reverse pass over one batch; gradient left in ``self.g``.
-        Returns the per-iteration BCE and MSE means and the total loss."""
-        torch = self.torch
+    def _enqueue(self, batch: "DeviceBatch", st, adam: bool):
+        """Enqueue one step on stream `st` with no host synchronisation (so it
+        can be captured into a CUDA graph): zero the gradient and the loss
+        words, forward pass with saved activations, losses, reverse pass, and
+        with `adam` the update (step size read from ``self.lr_t_dev``)."""
         net = self.net
-        st = nrx._stream_ptr(stream)
         ops = _Ops(st)
         lib = ops.lib
         n, U, S = batch.n, batch.U, batch.S
@@ -266,7 +290,6 @@ class Trainer:
         # ---- reverse ----
         gS, gz, t1, t2 = p(bf["gS"]), p(bf["gz"]), p(bf["t1"]), p(bf["t2"])
         ops.zero(4 * M * C, gS)
-        n_bits = float(batch.n_bits)
         n_mse = float(n * U * 14 * S * B)
         for k in reversed(range(K)):
             q = f"it{k}."
@@ -274,8 +297,7 @@ class Trainer:
             # LLR read-out k
             gl = p(bf["gl"])
             self._ok(lib.nrx_train_bce(n, batch.cfgs, mm, p(bf["l"][k]), batch.bits.data_ptr(),
-                                       batch.m_u.data_ptr(), 1.0 / n_bits, gl,
-                                       self.loss_dev.data_ptr() + 8 * k, st), "bce")
+                                       batch.m_u.data_ptr(), 1.0, gl, self.loss_dev.data_ptr() + 8 * k, st), "bce")
             dense_bwd(gl, p(bf["r1"][k]), C, "ro2", C, mm, gX=t1)
             ops.relu_mask(M * C, t1, p(bf["r1"][k]))
             dense_bwd(t1, Sn, C, "ro1", C, C, gX=gS, accumulate_into_gX=True)
@@ -320,22 +342,62 @@ class Trainer:
         ops.dw3(planes, S, C, gS, wp("init.dw"), t1, flip=True)
         ops.dw3_wgrad(planes, S, C, p(bf["P0"]), gS, gp("init.dw"))
         dense_bwd(t1, p(bf["x"]), F, "init.pw", F, C)
+        if adam:
+            ops.copy(4, self.lr_t_dev.data_ptr(), self._lr_host.data_ptr())
+            self._ok(lib.nrx_train_adam(self.n_total, self.w.data_ptr(), self.g.data_ptr(), self.m1.data_ptr(),
+                                        self.m2.data_ptr(), self.lr_t_dev.data_ptr(), self.beta1, self.beta2,
+                                        self.eps, st), "adam")
 
+    def _read_loss(self) -> Dict[str, List[float]]:
+        K = self.net.iterations
         ld = self.loss_dev.cpu().numpy()
         bce = [float(v) for v in ld[:K]]
         mse = [float(v) / self.gamma for v in ld[K:]] if self.gamma > 0 else [0.0] * K
         return {"bce": bce, "mse": mse, "loss": float(sum(bce) + self.gamma * sum(mse))}
 
+    def _advance(self):
+        """Step counter and this step's bias-corrected Adam step size (written
+        to pinned host memory; the enqueued copy moves it to the device)."""
+        self.t += 1
+        self._lr_host[0] = self.lr * math.sqrt(1.0 - self.beta2 ** self.t) / (1.0 - self.beta1 ** self.t)
+
+    def loss_and_grad(self, batch: "DeviceBatch", stream=None) -> Dict[str, List[float]]:
+        """Forward + reverse pass over one batch; gradient left in ``self.g``.
+        Returns the per-iteration BCE and MSE means and the total loss."""
+        self._enqueue(batch, nrx._stream_ptr(stream), adam=False)
+        return self._read_loss()
+
     def step(self, batch: "DeviceBatch", stream=None) -> Dict[str, List[float]]:
         """One training step: loss, gradient, Adam update of the master weights."""
-        out = self.loss_and_grad(batch, stream)
-        self.t += 1
-        lr_t = self.lr * math.sqrt(1.0 - self.beta2 ** self.t) / (1.0 - self.beta1 ** self.t)
-        lib = load()
-        st = lib.nrx_train_adam(self.n_total, self.w.data_ptr(), self.g.data_ptr(), self.m1.data_ptr(),
-                                self.m2.data_ptr(), lr_t, self.beta1, self.beta2, self.eps, nrx._stream_ptr(stream))
-        self._ok(st, "adam")
-        return out
+        self._advance()
+        self._enqueue(batch, nrx._stream_ptr(stream), adam=True)
+        return self._read_loss()
+
+    def graph_step(self, tb: synth.TrainingBatch) -> Dict[str, List[float]]:
+        """``step`` through a CUDA graph of the whole launch sequence: the
+        batch is uploaded into fixed device buffers and the graph captured on
+        the first call (per batch shape) is replayed, so the host issues one
+        launch per step instead of a few hundred."""
+        torch = self.torch
+        shape = (tb.y.shape, tb.m_u.shape, tb.bits.shape, tb.dmrs_symbols)
+        if self._graph is None or self._graph_shape != shape:
+            self._graph = None
+            self._static = DeviceBatch(tb)
+            self._graph_shape = shape
+            self.step(self._static)  # eager step: the buffers exist before capture
+            g = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                with torch.cuda.graph(g, stream=side):
+                    self._enqueue(self._static, side.cuda_stream, adam=True)
+            torch.cuda.current_stream().wait_stream(side)
+            self._graph = g
+            return self._read_loss()
+        self._static.load(tb)
+        self._advance()
+        self._graph.replay()
+        return self._read_loss()
 
     @staticmethod
     def _ok(st, what):
@@ -360,6 +422,25 @@ class DeviceBatch:
         self.h = torch.from_numpy(np.ascontiguousarray(tb.h)).to(dev)
         self.dmrs_symbols = tb.dmrs_symbols
         self.n_data = (14 - len(tb.dmrs_symbols)) * self.S
-        self.n_bits = int(self.n_data * tb.m_u.sum())
         self.cfgs = nrx.make_cfgs(self.n, self.S // 12, self.U, tb.dmrs_symbols,
                                   [self.dmrs[i].data_ptr() for i in range(self.n)], tb.noise_var)
+        self._pinned = None
+
+    def load(self, tb: synth.TrainingBatch, stream=None):
+        """Upload a batch of the same shape into these buffers (through pinned
+        staging, asynchronous on the stream; the staging is reused, so the
+        caller synchronises before the next load, as ``graph_step`` does by
+        reading the loss)."""
+        import torch
+        pairs = [(self.y, tb.y), (self.dmrs, tb.dmrs), (self.bits, tb.bits), (self.m_u, tb.m_u), (self.h, tb.h)]
+        if self._pinned is None:
+            self._pinned = [torch.empty(d.shape, dtype=d.dtype).pin_memory() for d, _ in pairs]
+        lib = load()
+        st = nrx._stream_ptr(stream)
+        for (dev, src), pin in zip(pairs, self._pinned):
+            assert tuple(src.shape) == tuple(dev.shape), "batch shape differs from the captured one"
+            pin.numpy()[...] = src
+            r = lib.nrx_train_copy(dev.numel() * dev.element_size(), dev.data_ptr(), pin.data_ptr(), st)
+            if r != nrx.NRX_OK:
+                raise nrx.NrxError(r, "nrx_train_copy")
+        self.dmrs_symbols = tb.dmrs_symbols

@@ -44,7 +44,8 @@ def test_training_entry_points_validate_without_a_gpu(lib):
     assert tl.nrx_train_aggregate(1, 5, 16, 1, 2, None) == nrx.NRX_EINVAL
     assert tl.nrx_train_aggregate(1, 2, 16, 1, 1, None) == nrx.NRX_EINVAL
     assert tl.nrx_train_dw3(0, 12, 4, 1, 1, 0, 0, 2, None) == nrx.NRX_EINVAL
-    assert tl.nrx_train_adam(0, 1, 1, 1, 1, 1e-3, 0.9, 0.999, 1e-8, None) == nrx.NRX_EINVAL
+    assert tl.nrx_train_adam(0, 1, 1, 1, 1, 1, 0.9, 0.999, 1e-8, None) == nrx.NRX_EINVAL
+    assert tl.nrx_train_adam(4, 1, 1, 1, 1, None, 0.9, 0.999, 1e-8, None) == nrx.NRX_EINVAL
     assert tl.nrx_train_zero(0, None, None) == nrx.NRX_OK
     assert tl.nrx_train_zero(-1, None, None) == nrx.NRX_EINVAL
     cfg = nrx.make_cfgs(1, 4, 2, (2, 11), [0], [1.0])

@@ -118,10 +118,10 @@ def test_adam_kernel_matches_definition():
     t, lr = 7, 3e-3
     ref_w, ref_m1, ref_m2 = TO.adam_step(w, g, m1, m2, t, lr)
     dw, dg, dm1, dm2 = (_t(v.astype(np.float32)) for v in (w, g, m1, m2))
-    lr_t = lr * np.sqrt(1 - 0.999 ** t) / (1 - 0.9 ** t)
+    lr_t = torch.tensor([lr * np.sqrt(1 - 0.999 ** t) / (1 - 0.9 ** t)], dtype=torch.float32).cuda()
     lib = train.load()
-    st = lib.nrx_train_adam(n, dw.data_ptr(), dg.data_ptr(), dm1.data_ptr(), dm2.data_ptr(), lr_t, 0.9, 0.999,
-                            1e-8, torch.cuda.current_stream().cuda_stream)
+    st = lib.nrx_train_adam(n, dw.data_ptr(), dg.data_ptr(), dm1.data_ptr(), dm2.data_ptr(), lr_t.data_ptr(), 0.9,
+                            0.999, 1e-8, torch.cuda.current_stream().cuda_stream)
     assert st == nrx.NRX_OK
     assert np.max(np.abs(dm1.cpu().numpy() - ref_m1)) < 1e-6
     assert np.max(np.abs(dm2.cpu().numpy() - ref_m2)) < 1e-5
@@ -198,3 +198,26 @@ def test_training_reduces_the_loss():
         tr.step(train.DeviceBatch(synth.training_batch([synth.training_slot(w, rng) for _ in range(8)], 4)))
     after = tr.loss_and_grad(val)["bce"][-1]
     assert np.isfinite(after) and after < 0.75 * before, (before, after)
+
+
+def test_graph_step_matches_eager_steps():
+    """The captured training step (one graph replay per step, batches of
+    different modulation orders uploaded into fixed buffers) follows the
+    eager launch sequence step for step."""
+    net = synth.NetConfig(num_rx_ant=2, channels=16, res_blocks=1, iterations=2, m_max=4)
+    w = synth.Workload(name="graph_check", seed_base=51, batch=3, num_prb=2, num_users=2, num_rx_ant=2,
+                       dmrs_symbols=(2, 11), mcs_choices=(2, 4), snr_db_range=(0.0, 10.0), num_taps=4,
+                       delay_spread_range_s=(50e-9, 100e-9), doppler_range_hz=(0.0, 100.0), ula=False, net=net)
+    rng = np.random.Generator(np.random.PCG64(3))
+    batches = [synth.training_batch([synth.training_slot(w, rng) for _ in range(3)], 4) for _ in range(4)]
+    assert len({tuple(b.m_u.reshape(-1)) for b in batches}) > 1
+    W = synth.make_weights(net, seed=9)
+    eager = train.Trainer(net, W, lr=1e-2, gamma=0.5)
+    graph = train.Trainer(net, W, lr=1e-2, gamma=0.5)
+    for tb in batches:
+        a = eager.step(train.DeviceBatch(tb))
+        b = graph.graph_step(tb)
+        assert abs(a["loss"] - b["loss"]) < 1e-4 * abs(a["loss"]), (a, b)
+    wa, wb = eager.w.cpu().numpy(), graph.w.cpu().numpy()
+    assert np.max(np.abs(wa - wb)) < 1e-4 * np.max(np.abs(wa))
+    assert graph.t == eager.t == 4
