@@ -208,6 +208,25 @@ nrx_status nrx_detect_noalloc(const void* weights_header, const float* weights_d
                               void* stream);
 
 /*
+ * PUSCH DMRS base sequences per TS 38.211 (the standard-compliant pilots of
+ * Sec. II): for each slot i and DMRS symbol l,
+ *   c_init = (2^17 (14 n_s + l + 1)(2 N_ID + 1) + 2 N_ID + n_SCID) mod 2^31
+ *   (Sec. 6.4.1.1.1.1, transform precoding disabled, CDM groups 0 and 1),
+ *   c(n) the length-31 Gold sequence of Sec. 5.2.1 (Nc = 1600),
+ *   r(m) = ((1 - 2 c(2m)) + j (1 - 2 c(2m+1))) / sqrt(2),  m < 6 num_prb,
+ * with the allocation starting at common resource block 0 (comb position m
+ * carries r(m)).  Output: device complex64 [n_slots][num_dmrs_symbols][6 num_prb],
+ * the dmrs_seq layout of nrx_slot_cfg.
+ *   slot_numbers  host int32 [n_slots], each 0..159 (n_s within the frame)
+ *   dmrs_symbols  host int32 [num_dmrs_symbols], each 0..13
+ * 1 <= n_slots <= 64, 0 <= n_id <= 65535, n_scid in {0, 1}, 1 <= num_prb <= 275.
+ * Errors: NRX_EINVAL, NRX_ECUDA.
+ */
+nrx_status nrx_dmrs_gold(int32_t n_slots, const int32_t* slot_numbers, int32_t n_id, int32_t n_scid,
+                         int32_t num_prb, int32_t num_dmrs_symbols, const int32_t* dmrs_symbols, void* out,
+                         void* stream);
+
+/*
  * Synchronise `stream` and report device-side failures of the previous calls:
  * NRX_ETIMEDOUT if a kernel's bounded wait for its tensor-core work gave up
  * (the kernel then skipped its remaining tiles; the word is cleared), NRX_ECUDA

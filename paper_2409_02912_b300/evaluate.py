@@ -1,0 +1,94 @@
+"""Matched-BLER comparison of the receivers (NRX in each precision, LS+LMMSE)
+on coded synthetic slots: BLER over an SNR grid and the SNR at 10% BLER,
+the operating point at which the paper compares receivers (Sec. IV).
+
+Every step runs in ``libnrx.so`` (detection and Viterbi decoding); this
+module draws the slots (``synth``), calls the receivers and counts errors.
+"""
+from __future__ import annotations
+
+import dataclasses
+import os
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+from . import bler, nrx, synth
+
+WEIGHTS_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights")
+# Trained by ``python -m paper_2409_02912_b300.train`` on 2-user, 4-Rx slots
+# with QPSK / 16-QAM (the mu2_4rx_24prb network: C=64, R=2, N_it=2, m_max=4).
+TRAINED_MU2 = os.path.join(WEIGHTS_DIR, "nrx_mu2_4rx_c64_r2_it2.bin")
+
+
+@dataclasses.dataclass(frozen=True)
+class Sweep:
+    """Coded-slot SNR sweep: geometry of the mu2_4rx_24prb workload, fixed
+    modulation order for both users, config-2 channel distributions."""
+
+    num_prb: int = 24
+    num_users: int = 2
+    num_rx_ant: int = 4
+    dmrs_symbols: tuple = (2, 11)
+    bits: int = 4
+    snrs: tuple = (2.0, 4.0, 6.0, 8.0, 10.0, 12.0, 14.0)
+    slots_per_point: int = 32
+    n_info: int = 1024
+    seed: int = 900
+
+
+def sweep_batches(sw: Sweep):
+    out = []
+    for k, snr in enumerate(sw.snrs):
+        cfgs, seeds = [], []
+        for i in range(sw.slots_per_point):
+            seed = sw.seed * 100_000 + k * 1_000 + i
+            rng = np.random.Generator(np.random.PCG64(seed))
+            cfgs.append(synth.SlotConfig(num_prb=sw.num_prb, num_users=sw.num_users, num_rx_ant=sw.num_rx_ant,
+                                         dmrs_symbols=sw.dmrs_symbols, bits_per_symbol=(sw.bits,) * sw.num_users,
+                                         snr_db=float(snr), num_taps=12,
+                                         delay_spread_s=float(rng.uniform(10e-9, 300e-9)),
+                                         doppler_hz=float(rng.uniform(0.0, 400.0)), ula=True))
+            seeds.append(seed + 7)
+        out.append(bler.coded_batch(cfgs, seeds, n_info=sw.n_info))
+    return out
+
+
+def compare(blob: bytes, precisions: Sequence[str] = ("fp32", "bf16", "fp16", "fp8"), sw: Sweep = Sweep(),
+            batches=None, untrained_blob: Optional[bytes] = None) -> Dict[str, dict]:
+    """BLER curves and SNR at 10% BLER of the NRX (each precision) and of
+    LS+LMMSE on the same coded slots."""
+    import torch
+    batches = sweep_batches(sw) if batches is None else batches
+    n = sw.slots_per_point
+    dev = [(torch.from_numpy(synth.stack_batch(b.slots)).cuda(),
+            torch.from_numpy(np.stack([s.dmrs for s in b.slots])).cuda()) for b in batches]
+    res: Dict[str, dict] = {}
+
+    def run(name, rx, fn):
+        curve = []
+        for b, (y, dm) in zip(batches, dev):
+            llr = fn(rx, b, y, dm)
+            e, nb, _, _ = bler.block_errors(llr, b)
+            curve.append(e / max(nb, 1))
+        res[name] = {"bler": curve, "snr_at_10pct": bler.snr_at_bler(sw.snrs, curve, 0.1)}
+
+    def nrx_fn(rx, b, y, dm):
+        return rx.nrx_detect_batch(y, dm, sw.dmrs_symbols, b.bits)
+
+    def lmmse_fn(rx, b, y, dm):
+        return rx.lmmse_detect_batch(y, dm, sw.dmrs_symbols, b.bits, b.noise_vars)
+
+    for p in precisions:
+        rx = nrx.Receiver(blob, sw.num_rx_ant, sw.num_users, sw.num_prb, max_slots=n, precision=p)
+        run(f"nrx_{p}", rx, nrx_fn)
+        if p == precisions[0]:
+            run("lmmse", rx, lmmse_fn)
+        rx.close()
+    if untrained_blob is not None:
+        rx = nrx.Receiver(untrained_blob, sw.num_rx_ant, sw.num_users, sw.num_prb, max_slots=n, precision="fp32")
+        run("nrx_untrained", rx, nrx_fn)
+        rx.close()
+    res["_sweep"] = {"snrs": list(sw.snrs), "blocks_per_point": int(batches[0].info.shape[0]),
+                     "slots_per_point": n, "num_prb": sw.num_prb, "bits": sw.bits}
+    return res

@@ -23,7 +23,7 @@ EXPORTED = (
     "nrx_create", "nrx_destroy", "nrx_llr_count", "nrx_detect_batch", "nrx_detect", "lmmse_detect_batch",
     "lmmse_detect", "nrx_detect_batch_host", "nrx_copy_state", "nrx_get_net", "nrx_last_launch_count",
     "nrx_last_error", "nrx_status_string", "nrx_profile", "nrx_profile_read", "nrx_detect_noalloc",
-    "nrx_check",
+    "nrx_check", "nrx_dmrs_gold",
 )
 KERNEL_KINDS = 5
 
@@ -91,6 +91,8 @@ def load() -> ctypes.CDLL:
     lib.nrx_check.restype = ctypes.c_int
     lib.nrx_detect_noalloc.argtypes = [P, P, P, CFG, P, P, P]
     lib.nrx_detect_noalloc.restype = ctypes.c_int
+    lib.nrx_dmrs_gold.argtypes = [I32, P, I32, I32, I32, I32, P, P, P]
+    lib.nrx_dmrs_gold.restype = ctypes.c_int
     lib.nrx_status_string.argtypes = [ctypes.c_int]
     lib.nrx_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -269,4 +271,19 @@ def nrx_detect_noalloc(weights_blob: bytes, weights_dev, y, dmrs, dmrs_symbols, 
                                 _stream_ptr(stream))
     if st != NRX_OK:
         raise NrxError(st, "nrx_detect_noalloc")
+    return out
+
+
+def nrx_dmrs_gold(slot_numbers, n_id: int, num_prb: int, dmrs_symbols, n_scid: int = 0, out=None, stream=None):
+    """TS 38.211 DMRS base sequences on the device: complex64 cuda
+    [n_slots, n_dmrs, 6 num_prb] (the ``dmrs`` argument of the detect calls)."""
+    import torch
+    sn = _bits_array(slot_numbers).reshape(-1)
+    ds = _bits_array(dmrs_symbols).reshape(-1)
+    if out is None:
+        out = torch.empty((sn.size, ds.size, 6 * num_prb), dtype=torch.complex64, device="cuda")
+    st = load().nrx_dmrs_gold(sn.size, sn.ctypes.data, n_id, n_scid, num_prb, ds.size, ds.ctypes.data,
+                              out.data_ptr(), _stream_ptr(stream))
+    if st != NRX_OK:
+        raise NrxError(st, "nrx_dmrs_gold")
     return out

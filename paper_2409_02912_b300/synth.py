@@ -66,6 +66,9 @@ class SlotConfig:
     delay_spread_s: float
     doppler_hz: float
     ula: bool
+    n_id: int = -1          # DMRS scrambling identity; -1: seeded random QPSK pilots
+    slot_number: int = 0    # slot index within the frame (Gold-sequence DMRS only)
+    n_scid: int = 0
 
     @property
     def num_subcarriers(self) -> int:
@@ -244,13 +247,22 @@ class Slot:
     x: np.ndarray          # complex128 [U, 14, S]: transmitted grid
 
 
+def slot_dmrs(cfg: SlotConfig, rng: np.random.Generator) -> np.ndarray:
+    """DMRS base sequence r(m) of each DMRS symbol (complex64 [n_dmrs, S/2]):
+    TS 38.211 Gold-sequence pilots when ``cfg.n_id >= 0``, else seeded random
+    unit-modulus QPSK."""
+    S = cfg.num_subcarriers
+    if cfg.n_id >= 0:
+        return dmrs_gold(cfg.num_prb, cfg.dmrs_symbols, cfg.slot_number, cfg.n_id, cfg.n_scid)
+    qpsk = (1.0 - 2.0 * rng.integers(0, 2, size=(len(cfg.dmrs_symbols), S // 2, 2))) / np.sqrt(2.0)
+    return (qpsk[..., 0] + 1j * qpsk[..., 1]).astype(np.complex64)
+
+
 def make_slot(cfg: SlotConfig, rng: np.random.Generator, channel: np.ndarray | None = None) -> Slot:
     """Generate one received slot (Eq. 1).  ``channel`` overrides the TDL draw
     (shape [U, B, 14, S]); used by tests that need e.g. a flat channel."""
     S = cfg.num_subcarriers
-    n_dmrs = len(cfg.dmrs_symbols)
-    qpsk = (1.0 - 2.0 * rng.integers(0, 2, size=(n_dmrs, S // 2, 2))) / np.sqrt(2.0)
-    dmrs = (qpsk[..., 0] + 1j * qpsk[..., 1]).astype(np.complex64)
+    dmrs = slot_dmrs(cfg, rng)
     n_data = cfg.num_data_symbols * S
     bits = [rng.integers(0, 2, size=(n_data, m), dtype=np.uint8) for m in cfg.bits_per_symbol]
     x = transmit_grid(cfg, dmrs, bits)
@@ -422,3 +434,129 @@ def training_batch(slots: Sequence[Slot], m_max: int) -> TrainingBatch:
     return TrainingBatch(y=stack_batch(slots), dmrs=np.stack([s.dmrs for s in slots]), bits=bits, m_u=m_u, h=h,
                          dmrs_symbols=tuple(s0.dmrs_symbols),
                          noise_var=np.array([s.cfg.noise_var for s in slots]))
+
+
+# ----------------------------------------------------------------------------
+# Channel code for BLER evaluation
+# ----------------------------------------------------------------------------
+# The paper reports LDPC TBLER; this build measures BLER with the textbook
+# rate-1/2, constraint-length-7 convolutional code (generators 133 and 171
+# octal), zero-tail terminated, and a seeded random interleaver per block.
+
+CONV_K = 7
+CONV_G = (0o133, 0o171)
+CONV_TAIL = CONV_K - 1
+
+
+def conv_encode(info: np.ndarray) -> np.ndarray:
+    """Encode info bits (uint8 [..., n]) with 6 zero tail bits: output uint8
+    [..., 2 (n + 6)], the two generator outputs of each step interleaved
+    (c0(t), c1(t)).  Generator bit 6 (the MSB of the octal value) multiplies
+    the current input, bit 0 the input six steps back."""
+    info = np.asarray(info, dtype=np.uint8)
+    n = info.shape[-1]
+    u = np.concatenate([info, np.zeros(info.shape[:-1] + (CONV_TAIL,), dtype=np.uint8)], axis=-1)
+    pad = np.concatenate([np.zeros(info.shape[:-1] + (CONV_TAIL,), dtype=np.uint8), u], axis=-1)
+    out = np.zeros(info.shape[:-1] + (2 * (n + CONV_TAIL),), dtype=np.uint8)
+    for j, g in enumerate(CONV_G):
+        acc = np.zeros(u.shape, dtype=np.uint8)
+        for d in range(CONV_K):  # tap on u[t - d] when bit (6 - d) of g is set
+            if (g >> (CONV_K - 1 - d)) & 1:
+                acc ^= pad[..., CONV_TAIL - d:CONV_TAIL - d + u.shape[-1]]
+        out[..., j::2] = acc
+    return out
+
+
+def interleaver(n_coded: int, seed: int = 7) -> np.ndarray:
+    """Seeded random interleaver: coded bit i of a block is sent at position
+    perm[i] of the block's span (int32 [n_coded])."""
+    return np.random.Generator(np.random.PCG64(seed)).permutation(n_coded).astype(np.int32)
+
+
+@dataclasses.dataclass
+class CodedUser:
+    info: np.ndarray        # uint8 [n_blocks, n_info]
+    block_offset: np.ndarray  # int64 [n_blocks]: first bit of each block in the user's bit stream
+
+
+def coded_bits(n_bits: int, n_info: int, perm: np.ndarray, rng: np.random.Generator):
+    """Fill a user's bit stream of n_bits (RE-major, then bit index: the LLR
+    order of the receivers) with as many interleaved code blocks as fit, then
+    random filler bits.  Returns (bits uint8 [n_bits], CodedUser)."""
+    n_coded = 2 * (n_info + CONV_TAIL)
+    nb = n_bits // n_coded
+    info = rng.integers(0, 2, size=(nb, n_info), dtype=np.uint8)
+    stream = rng.integers(0, 2, size=n_bits, dtype=np.uint8)
+    if nb:
+        cw = conv_encode(info)
+        blocks = np.zeros_like(cw)
+        blocks[:, perm] = cw
+        stream[:nb * n_coded] = blocks.reshape(-1)
+    return stream, CodedUser(info=info, block_offset=np.arange(nb, dtype=np.int64) * n_coded)
+
+
+def make_coded_slot(cfg: SlotConfig, rng: np.random.Generator, n_info: int, perm: np.ndarray):
+    """A slot whose users carry interleaved convolutional code blocks (see
+    ``coded_bits``).  Returns (Slot, [CodedUser per user])."""
+    S = cfg.num_subcarriers
+    n_data = cfg.num_data_symbols * S
+    dmrs = slot_dmrs(cfg, rng)
+    bits, users = [], []
+    for m in cfg.bits_per_symbol:
+        stream, cu = coded_bits(n_data * m, n_info, perm, rng)
+        bits.append(stream.reshape(n_data, m))
+        users.append(cu)
+    x = transmit_grid(cfg, dmrs, bits)
+    h = tdl_channel(cfg, rng)
+    n0 = cfg.noise_var
+    noise = np.sqrt(n0 / 2.0) * (rng.standard_normal((cfg.num_rx_ant, NUM_SYMBOLS, S))
+                                + 1j * rng.standard_normal((cfg.num_rx_ant, NUM_SYMBOLS, S)))
+    y = np.einsum("ubts,uts->bts", h, x) + noise
+    return Slot(cfg=cfg, y=y.astype(np.complex64), dmrs=dmrs, bits=bits, h=h, x=x), users
+
+
+# ----------------------------------------------------------------------------
+# TS 38.211 pseudo-random sequence and PUSCH DMRS
+# ----------------------------------------------------------------------------
+
+GOLD_NC = 1600
+
+
+def gold_sequence(c_init: int, length: int) -> np.ndarray:
+    """Pseudo-random sequence c(n), n < length, of TS 38.211 Sec. 5.2.1:
+    c(n) = x1(n + Nc) xor x2(n + Nc), Nc = 1600, with
+    x1(n+31) = x1(n+3) xor x1(n), x1(0) = 1, x1(1..30) = 0, and
+    x2(n+31) = x2(n+3) xor x2(n+2) xor x2(n+1) xor x2(n), x2(i) = bit i of c_init.
+    Computed 28 entries at a time (each new entry depends on entries at least
+    28 positions back)."""
+    total = GOLD_NC + length
+    x1 = np.zeros(total + 31, dtype=np.uint8)
+    x2 = np.zeros(total + 31, dtype=np.uint8)
+    x1[0] = 1
+    x2[:31] = [(c_init >> i) & 1 for i in range(31)]
+    n = 0
+    while n < total:
+        k = min(28, total - n)
+        x1[n + 31:n + 31 + k] = x1[n + 3:n + 3 + k] ^ x1[n:n + k]
+        x2[n + 31:n + 31 + k] = x2[n + 3:n + 3 + k] ^ x2[n + 2:n + 2 + k] ^ x2[n + 1:n + 1 + k] ^ x2[n:n + k]
+        n += k
+    return (x1[GOLD_NC:total] ^ x2[GOLD_NC:total]).astype(np.uint8)
+
+
+def dmrs_c_init(slot_number: int, symbol: int, n_id: int, n_scid: int = 0) -> int:
+    """c_init of the PUSCH DMRS sequence (TS 38.211 Sec. 6.4.1.1.1.1, transform
+    precoding disabled, CDM groups 0 and 1): (2^17 (14 n_s + l + 1)(2 N_ID + 1)
+    + 2 N_ID + n_SCID) mod 2^31."""
+    return (2 ** 17 * (14 * slot_number + symbol + 1) * (2 * n_id + 1) + 2 * n_id + n_scid) % (2 ** 31)
+
+
+def dmrs_gold(num_prb: int, dmrs_symbols: Sequence[int], slot_number: int, n_id: int, n_scid: int = 0) -> np.ndarray:
+    """r(m) = ((1 - 2c(2m)) + j (1 - 2c(2m+1))) / sqrt(2), m < 6 num_prb, per DMRS
+    symbol (complex64 [n_dmrs, 6 num_prb]); the allocation starts at common
+    resource block 0, so comb position m carries r(m)."""
+    M = 6 * num_prb
+    out = np.zeros((len(dmrs_symbols), M), dtype=np.complex64)
+    for d, l in enumerate(dmrs_symbols):
+        c = gold_sequence(dmrs_c_init(slot_number, l, n_id, n_scid), 2 * M).astype(np.float64)
+        out[d] = ((1.0 - 2.0 * c[0::2]) + 1j * (1.0 - 2.0 * c[1::2])) / np.sqrt(2.0)
+    return out

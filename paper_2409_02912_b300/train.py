@@ -444,3 +444,96 @@ class DeviceBatch:
             if r != nrx.NRX_OK:
                 raise nrx.NrxError(r, "nrx_train_copy")
         self.dmrs_symbols = tb.dmrs_symbols
+
+
+# ----------------------------------------------------------------------------
+# Training driver
+# ----------------------------------------------------------------------------
+
+
+def _make_batch(args):
+    """Worker: one seeded training batch (runs in a spawned process)."""
+    wl, seed = args
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return synth.training_batch([synth.training_slot(wl, rng) for _ in range(wl.batch)], wl.net.m_max)
+
+
+def fit(workload: synth.Workload, seconds: float, lr: float = 2e-3, lr_final: float = 5e-5, gamma: float = 1.0,
+        seed: int = 1, resume: Optional[str] = None, workers: Optional[int] = None, log_every: int = 2000,
+        trainer: Optional[Trainer] = None) -> Trainer:
+    """Train for a wall-clock budget on fresh random batches of ``workload``
+    (random MCS association and SNR offsets, Sec. IV-A), with an exponential
+    learning-rate decay from lr to lr_final over the budget.  Batches are
+    generated by a pool of spawned CPU workers, at most 48 ahead of the GPU;
+    each step is one CUDA-graph replay.  The read-out layers start at zero
+    (LLRs and channel estimates 0, i.e. BCE ln 2) unless resuming."""
+    import multiprocessing as mp
+    import os
+    import time
+    net = workload.net
+    if trainer is None:
+        W = synth.make_weights(net, seed=seed)
+        Wc = synth.make_chest_weights(net, seed=seed + 1)
+        for k in ("ro2.w", "ro2.b"):
+            W[k][...] = 0.0
+        Wc["chest.2.w"][...] = 0.0
+        trainer = Trainer(net, W, Wc, lr=lr, gamma=gamma)
+    if resume:
+        trainer.restore(resume)
+    nw = workers or max(2, min(14, (os.cpu_count() or 4) - 2))
+    pool = mp.get_context("spawn").Pool(nw)
+    try:
+        seed0 = 1_000_003 * (seed + 1) + trainer.t
+        window = [pool.apply_async(_make_batch, ((workload, seed0 + i),)) for i in range(48)]
+        nxt = seed0 + 48
+        t0 = time.time()
+        hist = []
+        while time.time() - t0 < seconds:
+            tb = window.pop(0).get(timeout=300)
+            window.append(pool.apply_async(_make_batch, ((workload, nxt),)))
+            nxt += 1
+            frac = min(1.0, (time.time() - t0) / seconds)
+            trainer.lr = lr * (lr_final / lr) ** frac
+            hist.append(trainer.graph_step(tb)["loss"])
+            if log_every and len(hist) % log_every == 0:
+                print(f"step {trainer.t} {time.time() - t0:.0f}s lr {trainer.lr:.2e} "
+                      f"loss {np.mean(hist[-log_every:]):.4f}", flush=True)
+    finally:
+        pool.terminate()
+        pool.join()
+    return trainer
+
+
+def main(argv=None):
+    import argparse
+    ap = argparse.ArgumentParser(description="Train the NRX on synthetic slots (Sec. II-B)")
+    ap.add_argument("--workload", default="mu2_4rx_24prb", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--prb", type=int, default=8, help="PRBs of the training slots (the net is size-agnostic)")
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--mcs", default="2,4", help="modulation orders drawn per user")
+    ap.add_argument("--seconds", type=float, default=600.0)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--lr-final", type=float, default=5e-5)
+    ap.add_argument("--gamma", type=float, default=1.0)
+    ap.add_argument("--resume", default=None)
+    ap.add_argument("--checkpoint", default=None, help="write an .npz checkpoint here")
+    ap.add_argument("--out", required=True, help="write the inference weight blob here")
+    a = ap.parse_args(argv)
+    base = synth.WORKLOADS[a.workload]
+    wl = dataclasses_replace(base, num_prb=a.prb, batch=a.batch,
+                             mcs_choices=tuple(int(v) for v in a.mcs.split(",")))
+    tr = fit(wl, a.seconds, lr=a.lr, lr_final=a.lr_final, gamma=a.gamma, resume=a.resume)
+    if a.checkpoint:
+        tr.save(a.checkpoint)
+    with open(a.out, "wb") as f:
+        f.write(tr.blob())
+    print(f"trained {tr.t} steps -> {a.out}")
+
+
+def dataclasses_replace(obj, **kw):
+    import dataclasses
+    return dataclasses.replace(obj, **kw)
+
+
+if __name__ == "__main__":
+    main()

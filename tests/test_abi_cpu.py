@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2409_02912_b300 import build as nrx_build
-from paper_2409_02912_b300 import nrx, synth, train
+from paper_2409_02912_b300 import bler, nrx, synth, train
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -31,7 +31,7 @@ def declared_functions():
 
 
 def test_header_declares_the_binding_exports():
-    assert sorted(nrx.EXPORTED + train.TRAIN_EXPORTED) == declared_functions()
+    assert sorted(nrx.EXPORTED + train.TRAIN_EXPORTED + bler.EVAL_EXPORTED) == declared_functions()
 
 
 def test_training_entry_points_validate_without_a_gpu(lib):
@@ -51,6 +51,16 @@ def test_training_entry_points_validate_without_a_gpu(lib):
     cfg = nrx.make_cfgs(1, 4, 2, (2, 11), [0], [1.0])
     assert tl.nrx_train_features(1, 2, 1, cfg, 1, None) == nrx.NRX_EINVAL   # null DMRS pointer
     assert tl.nrx_train_bce(1, cfg, 9, 1, 1, 1, 1.0, 1, 1, None) == nrx.NRX_EINVAL
+    el = bler.load()
+    assert el.nrx_conv_decode(1, 4097, 1, 1, None, 1, None) == nrx.NRX_EINVAL
+    assert el.nrx_conv_decode(1, 0, 1, 1, None, 1, None) == nrx.NRX_EINVAL
+    assert el.nrx_conv_decode(1, 64, None, 1, None, 1, None) == nrx.NRX_EINVAL
+    assert el.nrx_conv_decode(0, 64, None, None, None, None, None) == nrx.NRX_OK
+    sn = np.array([0, 160], dtype=np.int32)
+    ds = np.array([2, 11], dtype=np.int32)
+    assert lib.nrx_dmrs_gold(2, sn.ctypes.data, 1, 0, 4, 2, ds.ctypes.data, 1, None) == nrx.NRX_EINVAL
+    assert lib.nrx_dmrs_gold(1, sn.ctypes.data, 65536, 0, 4, 2, ds.ctypes.data, 1, None) == nrx.NRX_EINVAL
+    assert lib.nrx_dmrs_gold(1, sn.ctypes.data, 1, 2, 4, 2, ds.ctypes.data, 1, None) == nrx.NRX_EINVAL
 
 
 def test_library_exports_every_declared_symbol(lib):
