@@ -353,6 +353,19 @@ def run_ours(args, rank, world, local):
         extras["e2e"] = {"value": res_step / e2e_s, "unit": UNIT,
                          "h2d_bytes_per_step": int(y_h.numel() * 8 + d_h.numel() * 8),
                          "d2h_bytes_per_step": int(n_llr * 4)}
+        # matched BLER: the trained network on a coded sweep of the 24-PRB two-user workload
+        from paper_2409_02912_b300 import evaluate
+        with open(evaluate.TRAINED_MU2, "rb") as f:
+            q = evaluate.compare(f.read())
+        snr10 = {k: v["snr_at_10pct"] for k, v in q.items() if not k.startswith("_")}
+        ref10 = snr10.get("nrx_fp32")
+        extras["quality"] = {
+            "workload": "mu2_4rx_24prb coded sweep: 2 users x 16-QAM, 4 Rx, (133,171) K=7 code, 1024-bit blocks",
+            "weights": os.path.basename(evaluate.TRAINED_MU2),
+            "snr_db_at_10pct_bler": snr10,
+            "delta_vs_fp32_db": {k: (None if v is None or ref10 is None else v - ref10) for k, v in snr10.items()},
+            "bler": {k: v["bler"] for k, v in q.items() if not k.startswith("_")},
+            "snrs_db": q["_sweep"]["snrs"], "blocks_per_point": q["_sweep"]["blocks_per_point"]}
         # CPU baseline: the FP64 oracle on one slot of the same workload
         W64 = {k: v.astype(np.float64) for k, v in synth.make_weights(net).items()}
         secs = oracle_slot_seconds(slots[:1], W64, net)

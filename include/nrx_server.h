@@ -1,0 +1,122 @@
+/*
+ * nrx_server.h - Real-time serving loop for the NRX (same library, libnrx.so).
+ *
+ * The paper's deployment constraint (Sec. IV-A) is a per-slot latency budget
+ * under real-time operation with intra-frame parallelism only.  This server
+ * takes PUSCH slots as they arrive (several cells, each slot with its own PRB
+ * count and user count), groups pending slots of equal geometry into batches
+ * on the fly (continuous batching), and runs each batch through the NRX, or,
+ * when the NRX cannot finish a slot before its deadline, through the LS+LMMSE
+ * receiver of Fig. 3 (fallback).  The paper has no counterpart of this loop.
+ *
+ * Design:
+ *   - one NRX context (nrx.h) and one CUDA stream per PRB bucket; batches of
+ *     one bucket run in order on its stream, buckets run concurrently;
+ *   - admission by device-memory budget: at creation each bucket gets the
+ *     largest batch capacity (<= max_batch, halving) whose context and
+ *     staging fit in what remains of hbm_budget_bytes; at run time a request
+ *     whose bucket queue is full is rejected (backpressure);
+ *   - a worker thread dispatches, for each idle bucket, the pending slots of
+ *     one user count, earliest deadline first, as many as the measured
+ *     execution time allows before the earliest deadline; if not even one
+ *     slot can finish in time with the NRX, the pending slots of that key go
+ *     to LS+LMMSE;
+ *   - execution times per (bucket, users, batch size, receiver) are measured
+ *     at creation (calibration launches) and tracked with an exponential
+ *     moving average of the CUDA-event times of served batches;
+ *   - completion times come from CUDA events (converted to the host's
+ *     steady clock through a reference event), not from polling.
+ * A slot's LLRs do not depend on which other slots share its batch (every
+ * kernel works per slot), so serving is batch-invariant bit for bit.
+ *
+ * Threading: submit, poll and stats may be called from any one host thread
+ * at a time while the worker runs; the server owns its CUDA streams.
+ */
+#ifndef NRX_SERVER_H_
+#define NRX_SERVER_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "nrx.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nrx_server nrx_server;
+
+#define NRX_SERVER_MAX_BUCKETS 8
+
+typedef struct {
+  int32_t num_buckets;                          /* 1..8 */
+  int32_t bucket_prb[NRX_SERVER_MAX_BUCKETS];   /* the PRB counts served (each 1..275) */
+  int32_t max_users;                            /* 1..4 */
+  int32_t max_batch;                            /* slots per launch, 1..64 */
+  int32_t queue_capacity;                       /* pending slots per bucket before rejection, >= 1 */
+  int32_t num_dmrs_symbols;                     /* 1 or 2 */
+  int32_t dmrs_symbols[2];
+  int32_t precision;                            /* nrx_precision of the NRX contexts */
+  double deadline_us;                           /* latency budget of a slot from its arrival */
+  size_t hbm_budget_bytes;                      /* device memory the server may take */
+} nrx_server_cfg;
+
+typedef struct {
+  int32_t num_prb;              /* must equal one bucket_prb */
+  int32_t num_users;            /* 1..max_users */
+  int32_t bits_per_symbol[4];   /* m_u of users 0..num_users-1 (2, 4 or 6, <= m_max) */
+  float noise_var;              /* N0 (used by the LMMSE fallback) */
+  const void* y_host;           /* pinned host complex64 [B][14][12 num_prb] */
+  const void* dmrs_host;        /* pinned host complex64 [n_dmrs][6 num_prb] */
+  float* llr_host;              /* pinned host float32, nrx_llr_count floats (written on completion) */
+  int64_t arrival_ns;           /* arrival time on the steady clock (nrx_server_now_ns); 0 = now */
+} nrx_request;
+
+typedef struct {
+  uint64_t ticket;
+  int32_t receiver;             /* 0 NRX, 1 LS+LMMSE fallback, -1 rejected (queue full) */
+  int32_t status;               /* nrx_status of the batch */
+  int32_t batch_size;           /* slots in the launch that served it */
+  int32_t bucket;
+  int64_t arrival_ns;
+  int64_t done_ns;              /* LLRs in llr_host (D2H copy complete) */
+} nrx_completion;
+
+typedef struct {
+  int64_t submitted, served_nrx, served_lmmse, rejected, launches;
+  int32_t bucket_batch_capacity[NRX_SERVER_MAX_BUCKETS];  /* after admission */
+  size_t device_bytes;          /* device memory taken by the server */
+} nrx_server_stats;
+
+/* Create the server: contexts per bucket (weights blob as nrx_create),
+ * admission against hbm_budget_bytes, calibration launches, worker thread.
+ * Errors: NRX_EINVAL (bad config or blob), NRX_ENOMEM (not even batch 1 of a
+ * bucket fits the budget or the device), NRX_ECUDA. */
+nrx_status nrx_server_create(const void* weights, size_t weights_bytes, int32_t num_rx_ant,
+                             const nrx_server_cfg* cfg, nrx_server** out);
+
+/* Stop the worker after the in-flight batches finish and free everything. */
+void nrx_server_destroy(nrx_server* srv);
+
+/* The server's clock (steady clock, ns) for nrx_request.arrival_ns. */
+int64_t nrx_server_now_ns(void);
+
+/* Queue one slot; *ticket identifies its completion.  A full bucket queue
+ * produces a completion with receiver = -1 instead.  NRX_EINVAL for a
+ * request that matches no bucket or is malformed (nothing queued). */
+nrx_status nrx_server_submit(nrx_server* srv, const nrx_request* req, uint64_t* ticket);
+
+/* Move up to max_out completions into out (oldest first); *n receives the count. */
+nrx_status nrx_server_poll(nrx_server* srv, nrx_completion* out, int32_t max_out, int32_t* n);
+
+/* Block until every submitted slot has completed (or timeout_ms passed:
+ * NRX_ETIMEDOUT). */
+nrx_status nrx_server_drain(nrx_server* srv, int32_t timeout_ms);
+
+nrx_status nrx_server_get_stats(const nrx_server* srv, nrx_server_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NRX_SERVER_H_ */

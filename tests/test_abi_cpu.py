@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2409_02912_b300 import build as nrx_build
-from paper_2409_02912_b300 import bler, nrx, synth, train
+from paper_2409_02912_b300 import bler, nrx, server, synth, train
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -25,13 +25,14 @@ def declared_functions():
     for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
         text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
         names |= set(re.findall(
-            r"^\s*(?:const\s+)?(?:nrx_status|void|size_t|int32_t|char\s*\*|char)\s*\*?\s*(\w+)\s*\(",
+            r"^\s*(?:const\s+)?(?:nrx_status|void|size_t|int32_t|int64_t|char\s*\*|char)\s*\*?\s*(\w+)\s*\(",
             text, flags=re.M))
     return sorted(names)
 
 
 def test_header_declares_the_binding_exports():
-    assert sorted(nrx.EXPORTED + train.TRAIN_EXPORTED + bler.EVAL_EXPORTED) == declared_functions()
+    assert sorted(nrx.EXPORTED + train.TRAIN_EXPORTED + bler.EVAL_EXPORTED + server.SERVER_EXPORTED) == \
+        declared_functions()
 
 
 def test_training_entry_points_validate_without_a_gpu(lib):
@@ -112,3 +113,25 @@ def test_create_without_gpu_fails_loudly(lib):
     assert _create(lib, blob) == nrx.NRX_ECUDA
     with pytest.raises(nrx.NrxError):
         nrx.Receiver(blob, 2, 1, 4)
+
+
+def test_server_structs_and_validation(lib):
+    """ctypes layouts of the serving ABI and its host-side config checks."""
+    import ctypes
+    assert ctypes.sizeof(server.nrx_request) == 64
+    assert server.nrx_request.arrival_ns.offset == 56
+    assert ctypes.sizeof(server.nrx_completion) == 40
+    sl = server.load()
+    net = synth.WORKLOADS["su_2rx_4prb"].net
+    blob = synth.pack_weights(net, synth.make_weights(net))
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    h = ctypes.c_void_p()
+    for field, bad in (("num_buckets", 0), ("max_users", 5), ("max_batch", 65), ("queue_capacity", 0),
+                       ("num_dmrs_symbols", 3), ("deadline_us", 0.0)):
+        c = server.nrx_server_cfg(num_buckets=1, max_users=1, max_batch=1, queue_capacity=4, num_dmrs_symbols=1,
+                                  precision=0, deadline_us=500.0, hbm_budget_bytes=1 << 30)
+        c.bucket_prb[0] = 4
+        c.dmrs_symbols[0] = 2
+        setattr(c, field, bad)
+        assert sl.nrx_server_create(buf, len(blob), 2, ctypes.byref(c), ctypes.byref(h)) == nrx.NRX_EINVAL, field
+    assert sl.nrx_server_now_ns() > 0

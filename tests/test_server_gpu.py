@@ -1,0 +1,115 @@
+"""Serving loop on the GPU: batch invariance (a slot's LLRs are the same
+served alone, in a mixed batch, or through the direct entry point), the
+LS+LMMSE fallback when the deadline cannot be met, admission by the memory
+budget, and a short real-time load run."""
+import numpy as np
+import pytest
+
+from paper_2409_02912_b300 import nrx, server, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+NET = synth.WORKLOADS["mu2_4rx_24prb"].net  # B=4, C=64, m_max=4
+
+
+def _slots(prb, U, n, seed):
+    out = []
+    for i in range(n):
+        rng = np.random.Generator(np.random.PCG64(seed + i))
+        cfg = synth.SlotConfig(num_prb=prb, num_users=U, num_rx_ant=4, dmrs_symbols=(2, 11),
+                               bits_per_symbol=tuple(int(rng.choice([2, 4])) for _ in range(U)),
+                               snr_db=float(rng.uniform(0, 20)), num_taps=8, delay_spread_s=1e-7,
+                               doppler_hz=100.0, ula=True)
+        out.append(synth.make_slot(cfg, rng))
+    return out
+
+
+def _pinned(sl):
+    n_llr = sl.cfg.num_data_symbols * sl.cfg.num_subcarriers * sum(sl.cfg.bits_per_symbol)
+    return (torch.from_numpy(sl.y).pin_memory(), torch.from_numpy(sl.dmrs).pin_memory(),
+            torch.zeros(n_llr, dtype=torch.float32).pin_memory())
+
+
+def _serve(srv, slots):
+    bufs = [_pinned(s) for s in slots]
+    for s, (y, d, l) in zip(slots, bufs):
+        srv.submit(server.make_request(s, y, d, l))
+    srv.drain(20000)
+    comps = sorted(srv.poll(), key=lambda c: c.ticket)
+    return [b[2].numpy().copy() for b in bufs], comps
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_llrs_do_not_depend_on_batch_company(precision):
+    blob = synth.pack_weights(NET, synth.make_weights(NET))
+    srv = server.Server(blob, 4, [4, 8], max_users=2, max_batch=8, precision=precision, deadline_us=1e7)
+    try:
+        slots = _slots(8, 2, 6, seed=300)
+        alone = []
+        for s in slots:
+            out, c1 = _serve(srv, [s])
+            assert c1[0].receiver == 0 and c1[0].batch_size == 1
+            alone.append(out[0])
+        mixed, c2 = _serve(srv, slots)
+        assert all(c.receiver == 0 for c in c2)
+        assert max(c.batch_size for c in c2) > 1
+        for a, m in zip(alone, mixed):
+            assert np.array_equal(a, m)
+        rx = nrx.Receiver(blob, 4, 2, 8, max_slots=1, precision=precision)
+        y = torch.from_numpy(synth.stack_batch(slots[:1])).cuda()
+        d = torch.from_numpy(np.stack([slots[0].dmrs])).cuda()
+        direct = rx.nrx_detect_batch(y, d, (2, 11), [slots[0].cfg.bits_per_symbol]).cpu().numpy()
+        assert np.array_equal(direct, alone[0])
+    finally:
+        srv.close()
+
+
+def test_unmeetable_deadline_falls_back_to_lmmse():
+    blob = synth.pack_weights(NET, synth.make_weights(NET))
+    srv = server.Server(blob, 4, [4], max_users=3, max_batch=4, precision="fp16", deadline_us=1.0)
+    try:
+        slots = _slots(4, 3, 5, seed=400)
+        out, comps = _serve(srv, slots)
+        assert all(c.receiver == 1 for c in comps)
+        rx = nrx.Receiver(blob, 4, 3, 4, max_slots=1, precision="fp16")
+        for s, o in zip(slots, out):
+            y = torch.from_numpy(synth.stack_batch([s])).cuda()
+            d = torch.from_numpy(np.stack([s.dmrs])).cuda()
+            ref = rx.lmmse_detect_batch(y, d, (2, 11), [s.cfg.bits_per_symbol], [s.cfg.noise_var]).cpu().numpy()
+            assert np.array_equal(ref, o)
+        assert srv.stats()["served_lmmse"] == 5
+    finally:
+        srv.close()
+
+
+def test_admission_by_memory_budget():
+    blob = synth.pack_weights(NET, synth.make_weights(NET))
+    with pytest.raises(nrx.NrxError):
+        server.Server(blob, 4, [273], max_users=4, max_batch=8, hbm_budget_bytes=1 << 20)
+    big = server.Server(blob, 4, [273, 24], max_users=4, max_batch=8, hbm_budget_bytes=8 << 30)
+    full = big.stats()
+    big.close()
+    assert full["bucket_batch_capacity"] == [8, 8]
+    small = server.Server(blob, 4, [273], max_users=4, max_batch=8, hbm_budget_bytes=full["device_bytes"] // 3)
+    try:
+        cap = small.stats()["bucket_batch_capacity"][0]
+        assert 1 <= cap < 8 and small.stats()["device_bytes"] <= full["device_bytes"] // 3
+    finally:
+        small.close()
+
+
+def test_short_load_run_completes_every_slot():
+    blob = synth.pack_weights(NET, synth.make_weights(NET))
+    srv = server.Server(blob, 4, [24, 51], max_users=4, max_batch=8, precision="bf16", deadline_us=2000.0)
+    try:
+        spec = server.LoadSpec(cells=4, prb_choices=(24, 51), mcs=(2, 4), slots_per_s_per_cell=1000.0,
+                               seconds=0.3, pool_per_key=2)
+        r = server.run_load(srv, spec)
+        assert r["served_nrx"] + r["served_lmmse"] + r["rejected"] == r["offered_slots"] > 0
+        assert r["latency_us"]["all_p50"] is not None and r["latency_us"]["all_p50"] > 0
+    finally:
+        srv.close()
