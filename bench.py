@@ -333,6 +333,18 @@ def run_ours(args, rank, world, local):
             cmp[f"nrx_{other}"] = {"value": res_step / (1e-3 * statistics.mean(ts)), "unit": UNIT,
                                    "ms_per_step": statistics.mean(ts)}
             rx2.close()
+        # Var-IO heads (Sec. III) on the same slots: same active weights, same work
+        import dataclasses
+        net_v = dataclasses.replace(net, var_io=True)
+        rxv = nrx.Receiver(synth.pack_weights(net_v, synth.make_weights(net_v)), net.num_rx_ant, w.num_users,
+                           w.num_prb, n, precision)
+        f = lambda: rxv.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits, out=llr, stream=stream)
+        for _ in range(3):
+            f()
+        ts = timed(f, max(5, args.steps // 2))
+        cmp[f"nrx_{precision}_var_io"] = {"value": res_step / (1e-3 * statistics.mean(ts)), "unit": UNIT,
+                                          "ms_per_step": statistics.mean(ts)}
+        rxv.close()
         f = lambda: rx.lmmse_detect_batch(y, dmrs, w.dmrs_symbols, bits, nv, out=llr, stream=stream)
         for _ in range(3):
             f()
@@ -366,6 +378,17 @@ def run_ours(args, rank, world, local):
             "delta_vs_fp32_db": {k: (None if v is None or ref10 is None else v - ref10) for k, v in snr10.items()},
             "bler": {k: v["bler"] for k, v in q.items() if not k.startswith("_")},
             "snrs_db": q["_sweep"]["snrs"], "blocks_per_point": q["_sweep"]["blocks_per_point"]}
+        # serving loop under the multi-cell load (16 cells, PRB 24/51/106/273, 1-4 users, Poisson
+        # arrivals of one slot per 0.5 ms per cell, 0.5 ms deadline) and at a quarter of it
+        from paper_2409_02912_b300 import server as nrx_server
+        serving = {}
+        for name, cells in (("cells16", 16), ("cells4", 4)):
+            srv = nrx_server.Server(blob, net.num_rx_ant, (24, 51, 106, 273), max_users=4, max_batch=8,
+                                    precision=precision, deadline_us=500.0, hbm_budget_bytes=24 << 30)
+            spec = nrx_server.LoadSpec(cells=cells, seconds=2.0)
+            serving[name] = nrx_server.run_load(srv, spec)
+            srv.close()
+        extras["serving"] = serving
         # CPU baseline: the FP64 oracle on one slot of the same workload
         W64 = {k: v.astype(np.float64) for k, v in synth.make_weights(net).items()}
         secs = oracle_slot_seconds(slots[:1], W64, net)

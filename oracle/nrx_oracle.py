@@ -24,7 +24,8 @@ What is computed, with the passage each part follows:
   CNN update) and ReadoutLLRs (Sec. II-A), in the depthwise-separable layout
   of this build (see the layer list in ``nrx_forward``).
 * Var-MCS masking: user u keeps the first m_u of the m_max LLR outputs
-  (Sec. III, masking of higher-order LLRs).
+  (Sec. III, masking of higher-order LLRs); or, for a Var-IO network (Sec.
+  III), user u runs the StateInit and ReadoutLLRs of its own modulation order.
 * LLR sign: ln P(b=1|y)/P(b=0|y), Eq. 2.
 * LMMSE equalisation with unbiased scaling and max-log demapping over the
   user's matched Gray QAM constellation (the "LS + LMMSE" baseline, Fig. 3).
@@ -237,6 +238,24 @@ def cnn_update(S_u: np.ndarray, a_u: np.ndarray, pe_u: np.ndarray, W: Dict[str, 
     return S_u + z
 
 
+def head_weights(W: Dict[str, np.ndarray], m: int) -> Dict[str, np.ndarray]:
+    """Var-IO (Sec. III): a network with modulation-specific input and output
+    layers keeps, for order m, StateInit under "init.m{m}.*" and ReadoutLLRs
+    (m outputs) under "ro.m{m}.*"; this returns W with that pair under the
+    single-head names.  A single-head network is returned unchanged."""
+    if "init.pw.w" in W:
+        return W
+    out = dict(W)
+    out["init.pw.w"] = W[f"init.m{m}.pw.w"]
+    out["init.pw.b"] = W[f"init.m{m}.pw.b"]
+    out["init.dw"] = W[f"init.m{m}.dw"]
+    out["ro1.w"] = W[f"ro.m{m}.1.w"]
+    out["ro1.b"] = W[f"ro.m{m}.1.b"]
+    out["ro2.w"] = W[f"ro.m{m}.2.w"]
+    out["ro2.b"] = W[f"ro.m{m}.2.b"]
+    return out
+
+
 def readout(S_u: np.ndarray, W: Dict[str, np.ndarray]) -> np.ndarray:
     """ReadoutLLRs (Sec. II-A): l = W_o2 ReLU(W_o1 S + b_o1) + b_o2, [.., m_max]."""
     return dense(relu(dense(S_u, W["ro1.w"], W["ro1.b"])), W["ro2.w"], W["ro2.b"])
@@ -248,13 +267,16 @@ def readout(S_u: np.ndarray, W: Dict[str, np.ndarray]) -> np.ndarray:
 
 
 def nrx_states(y: np.ndarray, dmrs: np.ndarray, num_users: int, dmrs_symbols: Sequence[int],
-               W: Dict[str, np.ndarray], iterations: int, res_blocks: int) -> List[np.ndarray]:
+               W: Dict[str, np.ndarray], iterations: int, res_blocks: int,
+               bits_per_symbol: Sequence[int] | None = None) -> List[np.ndarray]:
     """States after StateInit and after each CGNN iteration: list of
-    [U, 14, S, C] arrays (entry k = S^(k))."""
+    [U, 14, S, C] arrays (entry k = S^(k)).  A Var-IO network needs the users'
+    modulation orders to pick each user's StateInit."""
     S = y.shape[2]
     H = channel_estimate(y, dmrs, num_users, dmrs_symbols)
     pes = [positional_encoding(u, S, dmrs_symbols) for u in range(num_users)]
-    state = np.stack([state_init(input_features(y, H[u], pes[u]), W) for u in range(num_users)])
+    Wu = [W if bits_per_symbol is None else head_weights(W, bits_per_symbol[u]) for u in range(num_users)]
+    state = np.stack([state_init(input_features(y, H[u], pes[u]), Wu[u]) for u in range(num_users)])
     out = [state]
     active = list(range(num_users))
     for k in range(iterations):
@@ -290,8 +312,8 @@ def nrx_forward(y: np.ndarray, dmrs: np.ndarray, num_users: int, dmrs_symbols: S
 
     Layers: StateInit; N_it x [messages, aggregate over other users, CNN
     update]; ReadoutLLRs; masking to each user's modulation order."""
-    states = nrx_states(y, dmrs, num_users, dmrs_symbols, W, iterations, res_blocks)
-    llr = [readout(states[-1][u], W) for u in range(num_users)]
+    states = nrx_states(y, dmrs, num_users, dmrs_symbols, W, iterations, res_blocks, bits_per_symbol)
+    llr = [readout(states[-1][u], head_weights(W, bits_per_symbol[u])) for u in range(num_users)]
     return pack_llrs(llr, bits_per_symbol, dmrs_symbols)
 
 

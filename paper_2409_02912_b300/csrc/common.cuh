@@ -30,6 +30,7 @@ struct SlotTable {
   float noise_var[NRX_MAX_LAUNCH_SLOTS];
   int8_t bits[NRX_MAX_LAUNCH_SLOTS][NRX_MAX_USERS];  // m_u per slot and user
   int32_t llr_off[NRX_MAX_LAUNCH_SLOTS][NRX_MAX_USERS];  // float offset of user u's LLRs
+  int8_t head[NRX_MAX_LAUNCH_SLOTS][NRX_MAX_USERS];  // Var-IO head of the user's modulation order (0 otherwise)
 };
 
 // ---------------------------------------------------------------------------

@@ -31,10 +31,7 @@ __device__ __forceinline__ void store_pair<__half>(__half* p, float a, float b) 
 
 template <int C, int B, typename OutT>
 __global__ void __launch_bounds__(256) k_state_init(Geometry g, SlotTable tab, const float2* __restrict__ y,
-                                                    const float* __restrict__ w_pw,  // [C][F]
-                                                    const float* __restrict__ b_pw,  // [C]
-                                                    const float* __restrict__ k_dw,  // [C][9]
-                                                    OutT* __restrict__ s_out) {
+                                                    InitWeights wts, OutT* __restrict__ s_out) {
   constexpr int F = 4 * B + 2;
   constexpr int TW = kStateInitTile;
   constexpr int EW = TW + 2;
@@ -50,12 +47,7 @@ __global__ void __launch_bounds__(256) k_state_init(Geometry g, SlotTable tab, c
   float* h = bias + C;  // [NRE][C], float4 chunk q of row r stored at q ^ (r & (NQ - 1))
 
   const int tid = threadIdx.x;
-  for (int i = tid; i < F * C; i += 256) {
-    const int c = i % C, f = i / C;
-    wt[f * C + c] = __ldg(w_pw + c * F + f);
-  }
-  for (int i = tid; i < 9 * C; i += 256) kd[i] = __ldg(k_dw + i);
-  for (int i = tid; i < C; i += 256) bias[i] = __ldg(b_pw + i);
+  int loaded = -1;  // head whose weights are in shared memory
   const int S = g.S;
   const int tps = (S + TW - 1) / TW;
   const int n_tiles = g.n_slots * g.U * tps;
@@ -63,7 +55,20 @@ __global__ void __launch_bounds__(256) k_state_init(Geometry g, SlotTable tab, c
     const int su = tile / tps, u = su % g.U, sl = su / g.U;
     const int s0 = (tile % tps) * TW - 1;
     const float2* ys = y + (size_t)sl * B * NRX_SYMBOLS * S;
-    __syncthreads();  // previous tile's readers of hf and h are done
+    __syncthreads();  // previous tile's readers of hf, h and the weights are done
+    const int head = tab.head[sl][u];
+    if (head != loaded) {  // uniform over the CTA
+      const float* w_pw = pick_head(wts.w_pw, head);
+      const float* k_dw = pick_head(wts.k_dw, head);
+      const float* b_pw = pick_head(wts.b_pw, head);
+      for (int i = tid; i < F * C; i += 256) {
+        const int c = i % C, f = i / C;
+        wt[f * C + c] = __ldg(w_pw + c * F + f);
+      }
+      for (int i = tid; i < 9 * C; i += 256) kd[i] = __ldg(k_dw + i);
+      for (int i = tid; i < C; i += 256) bias[i] = __ldg(b_pw + i);
+      loaded = head;
+    }
     for (int i = tid; i < g.n_dmrs * B * EW; i += 256) {
       const int e = i % EW, b = (i / EW) % B, d = i / (EW * B);
       const int s = s0 + e;
@@ -159,8 +164,8 @@ int sm_count() {
 }
 
 template <int C, int B, typename OutT>
-cudaError_t launch_si(const Geometry& g, const SlotTable& tab, const float2* y, const float* w_pw, const float* b_pw,
-                      const float* k_dw, OutT* s_out, cudaStream_t st) {
+cudaError_t launch_si(const Geometry& g, const SlotTable& tab, const float2* y, const InitWeights& w, OutT* s_out,
+                      cudaStream_t st) {
   const size_t smem = state_init_smem_bytes(C, B);
   ensure_smem<k_state_init<C, B, OutT>>((int)smem);
   int per_sm = (int)((228 * 1024) / (smem + 1024));
@@ -168,37 +173,36 @@ cudaError_t launch_si(const Geometry& g, const SlotTable& tab, const float2* y, 
   if (per_sm < 1) per_sm = 1;
   const int tiles = g.n_slots * g.U * ((g.S + kStateInitTile - 1) / kStateInitTile);
   const int grid = tiles < per_sm * sm_count() ? tiles : per_sm * sm_count();
-  k_state_init<C, B, OutT><<<grid, 256, smem, st>>>(g, tab, y, w_pw, b_pw, k_dw, s_out);
+  k_state_init<C, B, OutT><<<grid, 256, smem, st>>>(g, tab, y, w, s_out);
   return cudaGetLastError();
 }
 
 template <int C, typename OutT>
-cudaError_t launch_si_b(const Geometry& g, const SlotTable& tab, const float2* y, const float* w_pw,
-                        const float* b_pw, const float* k_dw, OutT* s_out, cudaStream_t st) {
+cudaError_t launch_si_b(const Geometry& g, const SlotTable& tab, const float2* y, const InitWeights& w, OutT* s_out,
+                        cudaStream_t st) {
   switch (g.B) {
-    case 1: return launch_si<C, 1, OutT>(g, tab, y, w_pw, b_pw, k_dw, s_out, st);
-    case 2: return launch_si<C, 2, OutT>(g, tab, y, w_pw, b_pw, k_dw, s_out, st);
-    case 4: return launch_si<C, 4, OutT>(g, tab, y, w_pw, b_pw, k_dw, s_out, st);
-    case 8: return launch_si<C, 8, OutT>(g, tab, y, w_pw, b_pw, k_dw, s_out, st);
+    case 1: return launch_si<C, 1, OutT>(g, tab, y, w, s_out, st);
+    case 2: return launch_si<C, 2, OutT>(g, tab, y, w, s_out, st);
+    case 4: return launch_si<C, 4, OutT>(g, tab, y, w, s_out, st);
+    case 8: return launch_si<C, 8, OutT>(g, tab, y, w, s_out, st);
   }
   return cudaErrorInvalidValue;
 }
 }  // namespace
 
 template <typename OutT>
-cudaError_t launch_state_init(const Geometry& g, const SlotTable& tab, const float2* y, const float* w_pw,
-                              const float* b_pw, const float* k_dw, OutT* s_out, cudaStream_t st) {
-  if (g.C == 64) return launch_si_b<64, OutT>(g, tab, y, w_pw, b_pw, k_dw, s_out, st);
-  if (g.C == 32) return launch_si_b<32, OutT>(g, tab, y, w_pw, b_pw, k_dw, s_out, st);
+cudaError_t launch_state_init(const Geometry& g, const SlotTable& tab, const float2* y, const InitWeights& w,
+                              OutT* s_out, cudaStream_t st) {
+  if (g.C == 64) return launch_si_b<64, OutT>(g, tab, y, w, s_out, st);
+  if (g.C == 32) return launch_si_b<32, OutT>(g, tab, y, w, s_out, st);
   return cudaErrorInvalidValue;
 }
-template cudaError_t launch_state_init<float>(const Geometry&, const SlotTable&, const float2*, const float*,
-                                              const float*, const float*, float*, cudaStream_t);
+template cudaError_t launch_state_init<float>(const Geometry&, const SlotTable&, const float2*, const InitWeights&,
+                                              float*, cudaStream_t);
 template cudaError_t launch_state_init<__nv_bfloat16>(const Geometry&, const SlotTable&, const float2*,
-                                                      const float*, const float*, const float*, __nv_bfloat16*,
-                                                      cudaStream_t);
-template cudaError_t launch_state_init<__half>(const Geometry&, const SlotTable&, const float2*, const float*,
-                                               const float*, const float*, __half*, cudaStream_t);
+                                                      const InitWeights&, __nv_bfloat16*, cudaStream_t);
+template cudaError_t launch_state_init<__half>(const Geometry&, const SlotTable&, const float2*, const InitWeights&,
+                                               __half*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // LS + LMMSE + max-log.  Per data RE: H = interpolated LS estimates [B x U],

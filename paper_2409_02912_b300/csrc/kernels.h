@@ -58,11 +58,36 @@ struct IterWeightsF32 {
   const float* pw2_b[4];
 };
 
+// Modulation-specific input / output layers (Var-IO, Sec. III): up to three
+// heads (QPSK, 16-QAM, 64-QAM), selected per user by SlotTable::head.  A
+// single-head network fills entry 0 only.
+constexpr int kMaxHeads = 3;
+
+// Entry h of a per-head parameter array without dynamic indexing (which
+// would copy the kernel parameter struct to local memory).
+template <typename T>
+__device__ __forceinline__ T pick_head(const T (&a)[kMaxHeads], int h) {
+  return h == 0 ? a[0] : (h == 1 ? a[1] : a[2]);
+}
+
+struct InitWeights {
+  const float* w_pw[kMaxHeads];  // [C][F]
+  const float* b_pw[kMaxHeads];  // [C]
+  const float* k_dw[kMaxHeads];  // [C][9]
+};
+
+struct ReadoutWeightsF32 {
+  const float* ro1_t[kMaxHeads];  // [C][C] transposed
+  const float* ro1_b[kMaxHeads];
+  const float* ro2[kMaxHeads];    // [m_max][C] (rows beyond the head's order are zero)
+  const float* ro2_b[kMaxHeads];
+};
+
 size_t state_init_smem_bytes(int C, int B);
 
 template <typename OutT>
-cudaError_t launch_state_init(const Geometry& g, const SlotTable& tab, const float2* y, const float* w_pw,
-                              const float* b_pw, const float* k_dw, OutT* s_out, cudaStream_t st);
+cudaError_t launch_state_init(const Geometry& g, const SlotTable& tab, const float2* y, const InitWeights& w,
+                              OutT* s_out, cudaStream_t st);
 
 cudaError_t launch_lmmse(const Geometry& g, const SlotTable& tab, const float2* y, float* llr, cudaStream_t st);
 
@@ -71,6 +96,5 @@ cudaError_t launch_mp_f32(const Geometry& g, const IterWeightsF32& w, const floa
                           cudaStream_t st);
 cudaError_t launch_block_f32(const Geometry& g, const IterWeightsF32& w, int r, const float* z_in, float* z_out,
                              float* state, bool last, cudaStream_t st);
-cudaError_t launch_readout_f32(const Geometry& g, const SlotTable& tab, const float* ro1_t, const float* ro1_b,
-                               const float* ro2, const float* ro2_b, const float* state, float* llr,
-                               cudaStream_t st);
+cudaError_t launch_readout_f32(const Geometry& g, const SlotTable& tab, const ReadoutWeightsF32& w,
+                               const float* state, float* llr, cudaStream_t st);

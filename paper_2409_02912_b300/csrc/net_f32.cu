@@ -273,16 +273,18 @@ struct RoCfg {
 };
 
 template <int C>
-__global__ void __launch_bounds__(kThreads) k_readout_f32(Geometry g, SlotTable tab, const float* __restrict__ ro1_t,
-                                                           const float* __restrict__ ro1_b,
-                                                           const float* __restrict__ ro2,  // [m_max][C]
-                                                           const float* __restrict__ ro2_b,
+__global__ void __launch_bounds__(kThreads) k_readout_f32(Geometry g, SlotTable tab, ReadoutWeightsF32 w,
                                                            const float* __restrict__ state, float* __restrict__ llr) {
   using Cf = RoCfg<C>;
   extern __shared__ __align__(16) float sm[];
   float* sa = sm;
   float* sb = sm + Cf::kRows * Cf::LD;
   const int u = blockIdx.y, sl = blockIdx.z;
+  const int head = tab.head[sl][u];  // Var-IO head of this user's modulation order
+  const float* __restrict__ ro1_t = pick_head(w.ro1_t, head);
+  const float* __restrict__ ro1_b = pick_head(w.ro1_b, head);
+  const float* __restrict__ ro2 = pick_head(w.ro2, head);  // [m_max][C]
+  const float* __restrict__ ro2_b = pick_head(w.ro2_b, head);
   const int r0 = blockIdx.x * Cf::kRows;
   const int S = g.S;
   const size_t base = ((size_t)sl * g.U + u) * NRX_SYMBOLS * S;
@@ -359,19 +361,18 @@ cudaError_t launch_block_f32(const Geometry& g, const IterWeightsF32& w, int r, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_readout_f32(const Geometry& g, const SlotTable& tab, const float* ro1_t, const float* ro1_b,
-                               const float* ro2, const float* ro2_b, const float* state, float* llr,
-                               cudaStream_t st) {
+cudaError_t launch_readout_f32(const Geometry& g, const SlotTable& tab, const ReadoutWeightsF32& w,
+                               const float* state, float* llr, cudaStream_t st) {
   if (g.C == 64) {
     using Cf = RoCfg<64>;
     const size_t smem = sizeof(float) * 2 * Cf::kRows * Cf::LD;
     k_readout_f32<64><<<dim3((g.n_data + Cf::kRows - 1) / Cf::kRows, g.U, g.n_slots), kThreads, smem, st>>>(
-        g, tab, ro1_t, ro1_b, ro2, ro2_b, state, llr);
+        g, tab, w, state, llr);
   } else if (g.C == 32) {
     using Cf = RoCfg<32>;
     const size_t smem = sizeof(float) * 2 * Cf::kRows * Cf::LD;
     k_readout_f32<32><<<dim3((g.n_data + Cf::kRows - 1) / Cf::kRows, g.U, g.n_slots), kThreads, smem, st>>>(
-        g, tab, ro1_t, ro1_b, ro2, ro2_b, state, llr);
+        g, tab, w, state, llr);
   } else {
     return cudaErrorInvalidValue;
   }

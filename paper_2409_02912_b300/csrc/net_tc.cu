@@ -859,16 +859,11 @@ __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, R
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = align1024(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  load_wtile<P>(sm + L::W1, w.ro1);
   float* w2 = reinterpret_cast<float*>(sm + L::W2F);
   float* sb1 = reinterpret_cast<float*>(sm + L::B1);
   float* sb2 = reinterpret_cast<float*>(sm + L::B2);
-  for (int i = tid; i < g.m_max * 64; i += blockDim.x) w2[i] = __ldg(w.ro2 + i);
-  for (int i = tid; i < 64; i += blockDim.x) sb1[i] = __ldg(w.ro1_b + i);
-  for (int i = tid; i < g.m_max; i += blockDim.x) sb2[i] = __ldg(w.ro2_b + i);
   float* ssc = reinterpret_cast<float*>(sm + L::SC);  // [64] weight scales, then [128] row scales
-  if constexpr (P::fp8)
-    for (int i = tid; i < 64; i += blockDim.x) ssc[i] = __ldg(w.ro1_sc + i);
+  int loaded = -1;  // Var-IO head whose weights are in shared memory
   TcCta c;
   tc_setup(c, reinterpret_cast<uint64_t*>(sm + L::BAR), reinterpret_cast<uint32_t*>(sm + L::BAR + 8), 64);
   const uint32_t sa = tc::smem_u32(sm + L::A), sw1 = tc::smem_u32(sm + L::W1);
@@ -880,6 +875,24 @@ __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, R
     const int su = tile / tiles_per_su, sl = su / U, u = su % U;
     const int r0 = (tile % tiles_per_su) * 128;
     const size_t base = (size_t)su * NRX_SYMBOLS * S;
+    const int head = tab.head[sl][u];
+    if (head != loaded) {
+      // The previous tile's MMA has completed and its epilogue ended with a
+      // barrier, so the weight region is free; the proxy fence and barrier
+      // after the A staging below publish it to the tensor cores.
+      load_wtile<P>(sm + L::W1, pick_head(w.ro1, head));
+      const float* ro2 = pick_head(w.ro2, head);
+      const float* ro1_b = pick_head(w.ro1_b, head);
+      const float* ro2_b = pick_head(w.ro2_b, head);
+      for (int i = tid; i < g.m_max * 64; i += blockDim.x) w2[i] = __ldg(ro2 + i);
+      for (int i = tid; i < 64; i += blockDim.x) sb1[i] = __ldg(ro1_b + i);
+      for (int i = tid; i < g.m_max; i += blockDim.x) sb2[i] = __ldg(ro2_b + i);
+      if constexpr (P::fp8) {
+        const float* sc = pick_head(w.ro1_sc, head);
+        for (int i = tid; i < 64; i += blockDim.x) ssc[i] = __ldg(sc + i);
+      }
+      loaded = head;
+    }
     {
       uint4 v[8];
 #pragma unroll
@@ -1043,13 +1056,14 @@ int grid_for(int smem, int max_per_sm, int tiles) {
 }  // namespace
 
 nrx_status upload_tc_weights(int mode, int C, int R, int N_it, const std::vector<const float*>& blob_it,
-                             const float* ro1w, const std::vector<IterWeightsF32>& it32, const float* ro1_b_dev,
-                             const float* ro2_dev, const float* ro2_b_dev, std::vector<IterWeightsTC>* out,
-                             void** dev_alloc, ReadoutWeightsTC* ro, int** err_word) {
+                             const std::vector<const float*>& ro1w_heads, const std::vector<IterWeightsF32>& it32,
+                             const ReadoutWeightsF32& ro32, std::vector<IterWeightsTC>* out, void** dev_alloc,
+                             ReadoutWeightsTC* ro, int** err_word) {
   if (C != 64) return NRX_EUNSUPPORTED;
   const size_t wb = mode == 1 ? 2 * 8192 : 8192;
   const int per_it = 3 + 2 * R;  // mp1, in_s, in_c, then pw1/pw2 per block
-  const size_t n_mats = (size_t)N_it * per_it + 1;
+  const int n_heads = (int)ro1w_heads.size();
+  const size_t n_mats = (size_t)N_it * per_it + n_heads;
   const size_t cb2_off = n_mats * wb;                         // N_it x C floats
   const size_t sc_off = cb2_off + (size_t)N_it * C * 4;        // n_mats x 64 E4M3 scales
   const size_t err_off = sc_off + n_mats * 64 * 4;             // one int
@@ -1086,7 +1100,7 @@ nrx_status upload_tc_weights(int mode, int C, int R, int N_it, const std::vector
       put(blk[4], C, 0);  // pw2
     }
   }
-  put(ro1w, C, 0);
+  for (const float* ro1w : ro1w_heads) put(ro1w, C, 0);
   void* d = nullptr;
   if (cudaMalloc(&d, host.size()) != cudaSuccess) {
     cudaGetLastError();
@@ -1131,11 +1145,14 @@ nrx_status upload_tc_weights(int mode, int C, int R, int N_it, const std::vector
     }
     w.err = err;
   }
-  ro->ro1_sc = scl(t);
-  ro->ro1 = mat(t++);
-  ro->ro1_b = ro1_b_dev;
-  ro->ro2 = ro2_dev;
-  ro->ro2_b = ro2_b_dev;
+  memset(ro, 0, sizeof(*ro));
+  for (int h = 0; h < n_heads; ++h) {
+    ro->ro1_sc[h] = scl(t);
+    ro->ro1[h] = mat(t++);
+    ro->ro1_b[h] = ro32.ro1_b[h];
+    ro->ro2[h] = ro32.ro2[h];
+    ro->ro2_b[h] = ro32.ro2_b[h];
+  }
   ro->err = err;
   return NRX_OK;
 }

@@ -61,12 +61,12 @@ struct IterWeightsTC {
   int* err;            // device word set when a bounded wait gives up
 };
 
-struct ReadoutWeightsTC {
-  const uint4* ro1;
-  const float* ro1_sc;  // E4M3 scales (FP8 policy only)
-  const float* ro1_b;
-  const float* ro2;    // [m_max][C] FP32
-  const float* ro2_b;
+struct ReadoutWeightsTC {  // per Var-IO head (entry 0 only for a single-head network)
+  const uint4* ro1[kMaxHeads];
+  const float* ro1_sc[kMaxHeads];  // E4M3 scales (FP8 policy only)
+  const float* ro1_b[kMaxHeads];
+  const float* ro2[kMaxHeads];     // [m_max][C] FP32
+  const float* ro2_b[kMaxHeads];
   int* err;
 };
 
@@ -76,9 +76,9 @@ struct ReadoutWeightsTC {
 // FP32 upload.  Only C = 64 is supported.  mode: 0 FP16, 1 BF16 (split
 // weights), 2 FP8 (E4M3 with per-output-channel scales).
 nrx_status upload_tc_weights(int mode, int C, int R, int N_it, const std::vector<const float*>& blob_it,
-                             const float* ro1w, const std::vector<IterWeightsF32>& it32, const float* ro1_b_dev,
-                             const float* ro2_dev, const float* ro2_b_dev, std::vector<IterWeightsTC>* out,
-                             void** dev_alloc, ReadoutWeightsTC* ro, int** err_word);
+                             const std::vector<const float*>& ro1w_heads, const std::vector<IterWeightsF32>& it32,
+                             const ReadoutWeightsF32& ro32, std::vector<IterWeightsTC>* out, void** dev_alloc,
+                             ReadoutWeightsTC* ro, int** err_word);
 
 template <typename P>
 cudaError_t launch_mp_tc(const Geometry& g, const IterWeightsTC& w, const typename P::T* state, typename P::T* z,

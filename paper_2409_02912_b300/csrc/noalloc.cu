@@ -187,7 +187,11 @@ extern "C" nrx_status nrx_detect_noalloc(const void* weights_header, const float
   k_layout_weights<<<dim3(16, plan.n_ops), 256, 0, s>>>(plan, weights_dev, W);
   if (cudaGetLastError() != cudaSuccess) return NRX_ECUDA;
   const float2* yy = static_cast<const float2*>(y);
-  if (launch_state_init<float>(g, tab, yy, W + o_init_w, W + o_init_b, W + o_init_dw, S, s) != cudaSuccess)
+  InitWeights iw{};
+  iw.w_pw[0] = W + o_init_w;
+  iw.b_pw[0] = W + o_init_b;
+  iw.k_dw[0] = W + o_init_dw;
+  if (launch_state_init<float>(g, tab, yy, iw, S, s) != cudaSuccess)
     return NRX_ECUDA;
   for (int k = 0; k < its; ++k) {
     IterWeightsF32 w;
@@ -216,7 +220,12 @@ extern "C" nrx_status nrx_detect_noalloc(const void* weights_header, const float
       zout = t;
     }
   }
-  if (launch_readout_f32(g, tab, W + o_ro1, W + o_ro1b, W + o_ro2, W + o_ro2b, S, llr, s) != cudaSuccess)
+  ReadoutWeightsF32 rw{};
+  rw.ro1_t[0] = W + o_ro1;
+  rw.ro1_b[0] = W + o_ro1b;
+  rw.ro2[0] = W + o_ro2;
+  rw.ro2_b[0] = W + o_ro2b;
+  if (launch_readout_f32(g, tab, rw, S, llr, s) != cudaSuccess)
     return NRX_ECUDA;
   return NRX_OK;
 }

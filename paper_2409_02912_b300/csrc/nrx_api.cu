@@ -17,6 +17,7 @@ namespace {
 
 constexpr int32_t kMagic = 0x5758524E;
 constexpr int32_t kVersion = 1;
+constexpr int32_t kVersionVarIO = 2;  // modulation-specific StateInit / ReadoutLLRs heads (Sec. III)
 
 }  // namespace
 
@@ -28,16 +29,13 @@ struct nrx_ctx {
   // device weights (one allocation per precision)
   float* w_f32 = nullptr;
   void* w_tc = nullptr;
-  const float* init_pw_w = nullptr;
-  const float* init_pw_b = nullptr;
-  const float* init_dw = nullptr;
+  InitWeights init{};        // StateInit per Var-IO head (entry 0 for a single-head net)
   std::vector<IterWeightsF32> it32;
   std::vector<IterWeightsTC> it16;
-  const float* ro1_t = nullptr;
-  const float* ro1_b = nullptr;
-  const float* ro2 = nullptr;
-  const float* ro2_b = nullptr;
+  ReadoutWeightsF32 ro32{};  // ReadoutLLRs per Var-IO head
   ReadoutWeightsTC ro_tc{};
+  int n_heads = 1;
+  int8_t head_of_bits[9] = {};  // modulation order -> head
   int* d_err = nullptr;  // device word set by a bounded wait that gave up (tensor-core path)
   // workspaces [max_slots][max_users][14][S_max][C]
   void* state = nullptr;
@@ -177,6 +175,7 @@ nrx_status prepare(nrx_ctx* ctx, int32_t n_slots, const nrx_slot_cfg* cfgs, cons
       if (!lmmse && m > ctx->m_max)
         return fail(ctx, NRX_EINVAL, "slot %d user %d: bits %d > m_max %d", i, u, m, ctx->m_max);
       tab->bits[i][u] = (int8_t)m;
+      tab->head[i][u] = ctx->head_of_bits[m];
       if (off > (size_t)INT32_MAX) return fail(ctx, NRX_EINVAL, "LLR output too large");
       tab->llr_off[i][u] = (int32_t)off;
       off += (size_t)g->n_data * m;
@@ -197,7 +196,7 @@ nrx_status run_tc(nrx_ctx* ctx, const Geometry& g, const SlotTable& tab, int its
   T* zb = static_cast<T*>(ctx->z_b);
   {
     KernelTimer kt(ctx, K_INIT, st);
-    e = launch_state_init<T>(g, tab, y, ctx->init_pw_w, ctx->init_pw_b, ctx->init_dw, S, st);
+    e = launch_state_init<T>(g, tab, y, ctx->init, S, st);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "state_init");
   ++*launches;
@@ -243,7 +242,7 @@ nrx_status run_nrx(nrx_ctx* ctx, const Geometry& g, const SlotTable& tab, int it
     float* zb = static_cast<float*>(ctx->z_b);
     {
       KernelTimer kt(ctx, K_INIT, st);
-      e = launch_state_init<float>(g, tab, y, ctx->init_pw_w, ctx->init_pw_b, ctx->init_dw, S, st);
+      e = launch_state_init<float>(g, tab, y, ctx->init, S, st);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "state_init");
     ++launches;
@@ -272,7 +271,7 @@ nrx_status run_nrx(nrx_ctx* ctx, const Geometry& g, const SlotTable& tab, int it
     }
     {
       KernelTimer kt(ctx, K_READOUT, st);
-      e = launch_readout_f32(g, tab, ctx->ro1_t, ctx->ro1_b, ctx->ro2, ctx->ro2_b, S, llr, st);
+      e = launch_readout_f32(g, tab, ctx->ro32, S, llr, st);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "readout_f32");
     ++launches;
@@ -416,14 +415,21 @@ nrx_status nrx_create(const void* weights, size_t weights_bytes, int32_t num_rx_
   memcpy(hdr, weights, sizeof(hdr));
   const int B = hdr[2], C = hdr[3], R = hdr[4], N_it = hdr[5], m_max = hdr[6];
   const int64_t n_floats = hdr[7];
-  if (hdr[0] != kMagic || hdr[1] != kVersion || B != num_rx_ant || (C != 32 && C != 64) || R < 1 || R > 4 ||
-      N_it < 1 || N_it > 16 || m_max < 2 || m_max > 8)
+  if (hdr[0] != kMagic || (hdr[1] != kVersion && hdr[1] != kVersionVarIO) || B != num_rx_ant ||
+      (C != 32 && C != 64) || R < 1 || R > 4 || N_it < 1 || N_it > 16 || m_max < 2 || m_max > 8)
     return NRX_EINVAL;
   const int F = 4 * B + 2;
-  const int64_t expect = (int64_t)C * F + C + 9 * C +
-                         (int64_t)N_it * (2 * ((int64_t)C * C + C) + (int64_t)C * (2 * C + 2) + C +
-                                          (int64_t)R * (2 * (9 * C + (int64_t)C * C + C))) +
-                         (int64_t)C * C + C + (int64_t)m_max * C + m_max;
+  // Heads: one shared head (version 1), or one per modulation order 2, 4, 6
+  // up to m_max (Var-IO, version 2), each with m_h outputs.
+  std::vector<int> head_m;
+  if (hdr[1] == kVersion) {
+    head_m.push_back(m_max);
+  } else {
+    for (int m = 2; m <= 6 && m <= m_max; m += 2) head_m.push_back(m);
+  }
+  int64_t expect = (int64_t)N_it * (2 * ((int64_t)C * C + C) + (int64_t)C * (2 * C + 2) + C +
+                                    (int64_t)R * (2 * (9 * C + (int64_t)C * C + C)));
+  for (int m : head_m) expect += (int64_t)C * F + C + 9 * C + (int64_t)C * C + C + (int64_t)m * C + m;
   if (n_floats != expect || weights_bytes != 32 + (size_t)n_floats * 4) return NRX_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return NRX_ECUDA;
@@ -436,6 +442,10 @@ nrx_status nrx_create(const void* weights, size_t weights_bytes, int32_t num_rx_
   ctx->N_it = N_it;
   ctx->m_max = m_max;
   ctx->max_users = max_users;
+  ctx->n_heads = (int)head_m.size();
+  for (int h = 0; h < (int)head_m.size(); ++h)
+    for (int m = 0; m <= 8; ++m)
+      if (hdr[1] == kVersion || m == head_m[h]) ctx->head_of_bits[m] = hdr[1] == kVersion ? 0 : (int8_t)h;
   ctx->max_prb = max_prb;
   ctx->max_slots = max_slots;
   ctx->prec = precision;
@@ -456,18 +466,22 @@ nrx_status nrx_create(const void* weights, size_t weights_bytes, int32_t num_rx_
     return put(t.data(), t.size());
   };
   struct Off {
-    size_t init_w, init_b, init_dw, ro1_t, ro1_b, ro2, ro2_b;
+    size_t init_w[kMaxHeads], init_b[kMaxHeads], init_dw[kMaxHeads];
+    size_t ro1_t[kMaxHeads], ro1_b[kMaxHeads], ro2[kMaxHeads], ro2_b[kMaxHeads];
     std::vector<size_t> f;
-  } o;
+  } o{};
   const float* p = src;
   auto take = [&](size_t n) {
     const float* q = p;
     p += n;
     return q;
   };
-  o.init_w = put(take((size_t)C * F), (size_t)C * F);
-  o.init_b = put(take(C), C);
-  o.init_dw = put(take(9 * C), 9 * C);
+  const int n_heads = (int)head_m.size();
+  for (int h = 0; h < n_heads; ++h) {
+    o.init_w[h] = put(take((size_t)C * F), (size_t)C * F);
+    o.init_b[h] = put(take(C), C);
+    o.init_dw[h] = put(take(9 * C), 9 * C);
+  }
   std::vector<const float*> blob_it;  // per iteration raw pointers, for the BF16 packer
   for (int k = 0; k < N_it; ++k) {
     const float* mp1w = take((size_t)C * C);
@@ -499,14 +513,20 @@ nrx_status nrx_create(const void* weights, size_t weights_bytes, int32_t num_rx_
       o.f.push_back(put(pw2b, C));
     }
   }
-  const float* ro1w = take((size_t)C * C);
-  const float* ro1b = take(C);
-  const float* ro2w = take((size_t)m_max * C);
-  const float* ro2b = take(m_max);
-  o.ro1_t = put_t(ro1w, C, C);
-  o.ro1_b = put(ro1b, C);
-  o.ro2 = put(ro2w, (size_t)m_max * C);
-  o.ro2_b = put(ro2b, m_max);
+  std::vector<const float*> ro1w_heads;
+  for (int h = 0; h < n_heads; ++h) {
+    const int m = head_m[h];
+    const float* ro1w = take((size_t)C * C);
+    const float* ro1b = take(C);
+    std::vector<float> ro2w((size_t)m_max * C, 0.f), ro2b(m_max, 0.f);  // rows beyond m stay zero
+    memcpy(ro2w.data(), take((size_t)m * C), sizeof(float) * (size_t)m * C);
+    memcpy(ro2b.data(), take(m), sizeof(float) * m);
+    ro1w_heads.push_back(ro1w);
+    o.ro1_t[h] = put_t(ro1w, C, C);
+    o.ro1_b[h] = put(ro1b, C);
+    o.ro2[h] = put(ro2w.data(), ro2w.size());
+    o.ro2_b[h] = put(ro2b.data(), ro2b.size());
+  }
 
   cudaError_t e = cudaMalloc(&ctx->w_f32, dev.size() * sizeof(float));
   if (e != cudaSuccess) {
@@ -519,13 +539,15 @@ nrx_status nrx_create(const void* weights, size_t weights_bytes, int32_t num_rx_
     return NRX_ECUDA;
   }
   const float* W = ctx->w_f32;
-  ctx->init_pw_w = W + o.init_w;
-  ctx->init_pw_b = W + o.init_b;
-  ctx->init_dw = W + o.init_dw;
-  ctx->ro1_t = W + o.ro1_t;
-  ctx->ro1_b = W + o.ro1_b;
-  ctx->ro2 = W + o.ro2;
-  ctx->ro2_b = W + o.ro2_b;
+  for (int h = 0; h < n_heads; ++h) {
+    ctx->init.w_pw[h] = W + o.init_w[h];
+    ctx->init.b_pw[h] = W + o.init_b[h];
+    ctx->init.k_dw[h] = W + o.init_dw[h];
+    ctx->ro32.ro1_t[h] = W + o.ro1_t[h];
+    ctx->ro32.ro1_b[h] = W + o.ro1_b[h];
+    ctx->ro32.ro2[h] = W + o.ro2[h];
+    ctx->ro32.ro2_b[h] = W + o.ro2_b[h];
+  }
   ctx->it32.resize(N_it);
   size_t fi = 0;
   for (int k = 0; k < N_it; ++k) {
@@ -548,8 +570,8 @@ nrx_status nrx_create(const void* weights, size_t weights_bytes, int32_t num_rx_
   }
   if (precision != NRX_FP32) {
     const int mode = precision == NRX_BF16 ? 1 : precision == NRX_FP8 ? 2 : 0;
-    nrx_status st = upload_tc_weights(mode, C, R, N_it, blob_it, ro1w, ctx->it32, ctx->ro1_b,
-                                      ctx->ro2, ctx->ro2_b, &ctx->it16, &ctx->w_tc, &ctx->ro_tc, &ctx->d_err);
+    nrx_status st = upload_tc_weights(mode, C, R, N_it, blob_it, ro1w_heads, ctx->it32, ctx->ro32, &ctx->it16,
+                                      &ctx->w_tc, &ctx->ro_tc, &ctx->d_err);
     if (st != NRX_OK) {
       nrx_destroy(ctx);
       return st;

@@ -44,11 +44,18 @@ class NetConfig:
     res_blocks: int
     iterations: int
     m_max: int = 6
+    var_io: bool = False  # modulation-specific StateInit / ReadoutLLRs heads (Sec. III)
 
     @property
     def in_features(self) -> int:
         # [Re/Im y per antenna, Re/Im LS estimate per antenna, 2 PE channels]
         return 4 * self.num_rx_ant + 2
+
+    @property
+    def heads(self) -> tuple:
+        """Modulation orders with their own input / output layers (Var-IO), or
+        (m_max,) for the single masked head."""
+        return tuple(m for m in (2, 4, 6) if m <= self.m_max) if self.var_io else (self.m_max,)
 
 
 @dataclasses.dataclass(frozen=True)
@@ -290,14 +297,22 @@ def workload_slots(w: Workload, n: int | None = None, start: int = 0) -> List[Sl
 
 WEIGHT_MAGIC = 0x5758524E  # "NRXW" little-endian
 WEIGHT_VERSION = 1
+WEIGHT_VERSION_VAR_IO = 2
 
 
 def weight_layout(net: NetConfig) -> List[tuple]:
     """(name, shape) of every tensor in blob order.  Dense weights are
     [out, in] row-major (y = W x + b); depthwise kernels are [C, 3, 3] indexed
-    [channel, symbol offset + 1, subcarrier offset + 1]."""
+    [channel, symbol offset + 1, subcarrier offset + 1].  A Var-IO network
+    (Sec. III) has one StateInit per modulation order m first ("init.m{m}.*")
+    and one ReadoutLLRs per order last ("ro.m{m}.*", m outputs)."""
     C, F, m = net.channels, net.in_features, net.m_max
-    lay = [("init.pw.w", (C, F)), ("init.pw.b", (C,)), ("init.dw", (C, 3, 3))]
+    if net.var_io:
+        lay = []
+        for mh in net.heads:
+            lay += [(f"init.m{mh}.pw.w", (C, F)), (f"init.m{mh}.pw.b", (C,)), (f"init.m{mh}.dw", (C, 3, 3))]
+    else:
+        lay = [("init.pw.w", (C, F)), ("init.pw.b", (C,)), ("init.dw", (C, 3, 3))]
     for k in range(net.iterations):
         p = f"it{k}."
         lay += [(p + "mp1.w", (C, C)), (p + "mp1.b", (C,)),
@@ -307,7 +322,12 @@ def weight_layout(net: NetConfig) -> List[tuple]:
             q = f"{p}blk{r}."
             lay += [(q + "dw1", (C, 3, 3)), (q + "pw1.w", (C, C)), (q + "pw1.b", (C,)),
                     (q + "dw2", (C, 3, 3)), (q + "pw2.w", (C, C)), (q + "pw2.b", (C,))]
-    lay += [("ro1.w", (C, C)), ("ro1.b", (C,)), ("ro2.w", (m, C)), ("ro2.b", (m,))]
+    if net.var_io:
+        for mh in net.heads:
+            lay += [(f"ro.m{mh}.1.w", (C, C)), (f"ro.m{mh}.1.b", (C,)), (f"ro.m{mh}.2.w", (mh, C)),
+                    (f"ro.m{mh}.2.b", (mh,))]
+    else:
+        lay += [("ro1.w", (C, C)), ("ro1.b", (C,)), ("ro2.w", (m, C)), ("ro2.b", (m,))]
     return lay
 
 
@@ -337,8 +357,8 @@ def pack_weights(net: NetConfig, weights: Dict[str, np.ndarray]) -> bytes:
     the float32 tensors in ``weight_layout`` order."""
     arrs = [np.ascontiguousarray(weights[n], dtype=np.float32).reshape(-1) for n, _ in weight_layout(net)]
     total = int(sum(a.size for a in arrs))
-    hdr = struct.pack("<8i", WEIGHT_MAGIC, WEIGHT_VERSION, net.num_rx_ant, net.channels,
-                      net.res_blocks, net.iterations, net.m_max, total)
+    hdr = struct.pack("<8i", WEIGHT_MAGIC, WEIGHT_VERSION_VAR_IO if net.var_io else WEIGHT_VERSION,
+                      net.num_rx_ant, net.channels, net.res_blocks, net.iterations, net.m_max, total)
     return hdr + b"".join(a.tobytes() for a in arrs)
 
 

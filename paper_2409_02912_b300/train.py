@@ -511,6 +511,7 @@ def main(argv=None):
     ap.add_argument("--prb", type=int, default=8, help="PRBs of the training slots (the net is size-agnostic)")
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--mcs", default="2,4", help="modulation orders drawn per user")
+    ap.add_argument("--snr", default=None, help="lo,hi: SNR range in dB before the offsets (default: workload's)")
     ap.add_argument("--seconds", type=float, default=600.0)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--lr-final", type=float, default=5e-5)
@@ -520,7 +521,8 @@ def main(argv=None):
     ap.add_argument("--out", required=True, help="write the inference weight blob here")
     a = ap.parse_args(argv)
     base = synth.WORKLOADS[a.workload]
-    wl = dataclasses_replace(base, num_prb=a.prb, batch=a.batch,
+    snr = tuple(float(v) for v in a.snr.split(",")) if a.snr else base.snr_db_range
+    wl = dataclasses_replace(base, num_prb=a.prb, batch=a.batch, snr_db_range=snr,
                              mcs_choices=tuple(int(v) for v in a.mcs.split(",")))
     tr = fit(wl, a.seconds, lr=a.lr, lr_final=a.lr_final, gamma=a.gamma, resume=a.resume)
     if a.checkpoint:

@@ -270,3 +270,24 @@ def test_cuda_graph_replay_matches_direct_call(prec):
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
     rx.nrx_check()
+
+
+# ----------------------------------------------------------------------------
+# Var-IO heads (Sec. III): per-user StateInit / ReadoutLLRs of its order
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision,tol", [("fp32", TOL_FP32), ("bf16", TOL_TC), ("fp16", TOL_TC), ("fp8", FP8_WORST)])
+def test_var_io_parity(precision, tol):
+    import dataclasses
+    w = synth.WORKLOADS["mu4_4rx_273prb"]
+    net = dataclasses.replace(w.net, var_io=True)
+    wl = dataclasses.replace(w, num_prb=24, batch=3, net=net)
+    slots = synth.workload_slots(wl, 3)
+    assert len({m for s in slots for m in s.cfg.bits_per_symbol}) >= 2
+    W = synth.make_weights(net, seed=5)
+    rx = nrx.Receiver(synth.pack_weights(net, W), 4, 4, 24, max_slots=3, precision=precision)
+    y, dmrs, bits, _ = H.device_inputs(slots)
+    llr = rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits).cpu().numpy()
+    W64 = {k: v.astype(np.float64) for k, v in W.items()}
+    errs = H.rel_errors(llr, H.oracle_nrx(slots, W64, net), slots)
+    assert max(errs) <= tol, errs

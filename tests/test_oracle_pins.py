@@ -405,3 +405,70 @@ def test_pack_llrs_order_and_count():
     assert out[2 * 2 * S] == grids[0][3, 0, 0]
     off = 13 * 12 * 2
     assert out[off] == grids[1][0, 0, 0] and out[off + 3] == grids[1][0, 0, 3]
+
+
+# ----------------------------------------------------------------------------
+# Var-IO heads (Sec. III)
+# ----------------------------------------------------------------------------
+
+def _var_io_copy_of(net1, W1):
+    """A Var-IO network whose every StateInit equals the single head and whose
+    order-m ReadoutLLRs is the first m rows of the single ReadoutLLRs."""
+    netv = synth.NetConfig(num_rx_ant=net1.num_rx_ant, channels=net1.channels, res_blocks=net1.res_blocks,
+                           iterations=net1.iterations, m_max=net1.m_max, var_io=True)
+    Wv = {}
+    for name, _ in synth.weight_layout(netv):
+        if name.startswith("init.m"):
+            Wv[name] = W1["init." + name.split(".", 2)[2]]
+        elif name.startswith("ro.m"):
+            m = int(name.split(".")[1][1:])
+            part = name.split(".", 2)[2]
+            src = {"1.w": "ro1.w", "1.b": "ro1.b", "2.w": "ro2.w", "2.b": "ro2.b"}[part]
+            Wv[name] = W1[src][:m] if part.startswith("2") else W1[src]
+        else:
+            Wv[name] = W1[name]
+    return netv, Wv
+
+
+def test_var_io_with_shared_heads_equals_masking():
+    """Masking the shared head (Sec. III) and Var-IO heads that copy it give
+    identical LLRs."""
+    net1 = synth.NetConfig(num_rx_ant=2, channels=8, res_blocks=1, iterations=2, m_max=6)
+    W1 = synth.make_weights(net1, seed=21)
+    netv, Wv = _var_io_copy_of(net1, W1)
+    assert netv.heads == (2, 4, 6)
+    cfg = synth.SlotConfig(num_prb=2, num_users=3, num_rx_ant=2, dmrs_symbols=(2, 11), bits_per_symbol=(6, 2, 4),
+                           snr_db=7.0, num_taps=4, delay_spread_s=1e-7, doppler_hz=50.0, ula=False)
+    sl = synth.make_slot(cfg, _rng(31))
+    a = O.nrx_forward(sl.y, sl.dmrs, 3, cfg.dmrs_symbols, cfg.bits_per_symbol, W1, 2, 1)
+    b = O.nrx_forward(sl.y, sl.dmrs, 3, cfg.dmrs_symbols, cfg.bits_per_symbol, Wv, 2, 1)
+    assert np.array_equal(a, b)
+
+
+def test_var_io_heads_act_only_on_their_users():
+    """Changing the 16-QAM heads changes the LLRs of the 16-QAM user (and,
+    through message passing, the others'), while changing the unused 64-QAM
+    head changes nothing."""
+    netv = synth.NetConfig(num_rx_ant=2, channels=8, res_blocks=1, iterations=1, m_max=6, var_io=True)
+    W = synth.make_weights(netv, seed=22)
+    cfg = synth.SlotConfig(num_prb=2, num_users=2, num_rx_ant=2, dmrs_symbols=(2,), bits_per_symbol=(2, 4),
+                           snr_db=7.0, num_taps=4, delay_spread_s=1e-7, doppler_hz=0.0, ula=False)
+    sl = synth.make_slot(cfg, _rng(32))
+    run = lambda Wx: O.nrx_forward(sl.y, sl.dmrs, 2, (2,), (2, 4), Wx, 1, 1)  # noqa: E731
+    base = run(W)
+    W6 = dict(W, **{"ro.m6.2.w": W["ro.m6.2.w"] + 1.0, "init.m6.pw.b": W["init.m6.pw.b"] + 1.0})
+    assert np.array_equal(run(W6), base)
+    n_data = 13 * 24
+    W4 = dict(W, **{"ro.m4.2.b": W["ro.m4.2.b"] + 1.0})
+    d = run(W4) - base
+    assert np.all(d[:n_data * 2] == 0.0) and np.allclose(d[n_data * 2:], 1.0)
+
+
+def test_var_io_blob_layout():
+    netv = synth.NetConfig(num_rx_ant=4, channels=64, res_blocks=2, iterations=2, m_max=6, var_io=True)
+    blob = synth.pack_weights(netv, synth.make_weights(netv))
+    hdr = np.frombuffer(blob[:32], dtype="<i4")
+    F, C = 18, 64
+    per_it = 2 * (C * C + C) + C * (2 * C + 2) + C + 2 * 2 * (9 * C + C * C + C)
+    heads = sum(C * F + C + 9 * C + C * C + C + m * C + m for m in (2, 4, 6))
+    assert hdr[1] == 2 and hdr[7] == 2 * per_it + heads and len(blob) == 32 + 4 * hdr[7]
