@@ -10,17 +10,20 @@
  * receiver of Fig. 3 (fallback).  The paper has no counterpart of this loop.
  *
  * Design:
- *   - one NRX context (nrx.h) and one CUDA stream per PRB bucket; batches of
- *     one bucket run in order on its stream, buckets run concurrently;
+ *   - one NRX context (nrx.h) per PRB bucket and two lanes, each a CUDA stream
+ *     with its own staging buffers: the NRX lane and the fallback lane
+ *     (LS+LMMSE), so that a fallback never waits behind an NRX batch; batches
+ *     of one lane run in order, lanes and buckets run concurrently;
  *   - admission by device-memory budget: at creation each bucket gets the
  *     largest batch capacity (<= max_batch, halving) whose context and
  *     staging fit in what remains of hbm_budget_bytes; at run time a request
  *     whose bucket queue is full is rejected (backpressure);
- *   - a worker thread dispatches, for each idle bucket, the pending slots of
- *     one user count, earliest deadline first, as many as the measured
- *     execution time allows before the earliest deadline; if not even one
- *     slot can finish in time with the NRX, the pending slots of that key go
- *     to LS+LMMSE;
+ *   - a worker thread per bucket moves every queued slot that the NRX lane cannot
+ *     finish before its deadline, even alone once the lane is free, to the
+ *     fallback lane; each idle NRX lane takes the pending slots of one user
+ *     count, earliest deadline first, as many as the measured execution time
+ *     allows before the earliest deadline; each idle fallback lane takes up
+ *     to a batch of its queue;
  *   - execution times per (bucket, users, batch size, receiver) are measured
  *     at creation (calibration launches) and tracked with an exponential
  *     moving average of the CUDA-event times of served batches;
@@ -105,6 +108,15 @@ int64_t nrx_server_now_ns(void);
  * produces a completion with receiver = -1 instead.  NRX_EINVAL for a
  * request that matches no bucket or is malformed (nothing queued). */
 nrx_status nrx_server_submit(nrx_server* srv, const nrx_request* req, uint64_t* ticket);
+
+/* Trace replay (load generation without host-language timing jitter): submit
+ * reqs[0..n) in order, each when the steady clock reaches its arrival_ns
+ * (spinning in the calling thread; requests whose time has passed are
+ * submitted at once).  Returns after the last submission; tickets[i] (if not
+ * NULL) receives request i's ticket and *max_late_ns the largest delay
+ * between a request's arrival_ns and its submission. */
+nrx_status nrx_server_replay(nrx_server* srv, int32_t n, const nrx_request* reqs, uint64_t* tickets,
+                             int64_t* max_late_ns);
 
 /* Move up to max_out completions into out (oldest first); *n receives the count. */
 nrx_status nrx_server_poll(nrx_server* srv, nrx_completion* out, int32_t max_out, int32_t* n);

@@ -35,24 +35,33 @@ struct Pending {
 
 struct Inflight {
   bool active = false;
-  int receiver = 0, users = 0, n = 0;
+  int users = 0, n = 0;
   std::vector<Pending> reqs;
   cudaEvent_t start = nullptr, done = nullptr;
+};
+
+// One execution lane of a bucket: a stream with its own staging buffers.
+// Lane 0 runs the NRX, lane 1 the LS+LMMSE fallback, so that a fallback
+// never waits behind an NRX batch.
+struct Lane {
+  cudaStream_t st = nullptr;
+  float2* y = nullptr;
+  float2* dmrs = nullptr;
+  float* llr = nullptr;
+  Inflight cur;
+  cudaEvent_t ref = nullptr;
+  int64_t ref_ns = 0;
+  int64_t busy_until_ns = 0;  // predicted end of the in-flight batch
 };
 
 struct Bucket {
   int prb = 0, S = 0, cap = 0;
   nrx_ctx* ctx = nullptr;
-  cudaStream_t st = nullptr;
-  float2* y = nullptr;
-  float2* dmrs = nullptr;
-  float* llr = nullptr;
-  std::deque<Pending> q[kMaxUsers + 1];
+  Lane lane[2];
+  std::deque<Pending> inbox;  // submitted, not yet seen by the bucket's worker (guarded by the server mutex)
+  std::deque<Pending> q[2][kMaxUsers + 1];  // [lane][users], arrival (= deadline) order
   int queued = 0;
-  Inflight cur;
-  cudaEvent_t ref = nullptr;
-  int64_t ref_ns = 0;
-  std::vector<double> est_us[2][kMaxUsers + 1];  // [receiver][users][n], n <= cap
+  std::vector<double> est_us[2][kMaxUsers + 1];  // [lane][users][n], n <= cap
 };
 
 }  // namespace
@@ -63,11 +72,10 @@ struct nrx_server {
   std::vector<Bucket> buckets;
   std::mutex mu;
   std::condition_variable cv;
-  std::deque<Pending> inbox;
   std::deque<nrx_completion> done;
   std::atomic<bool> stop{false};
   std::atomic<int64_t> outstanding{0};
-  std::thread worker;
+  std::vector<std::thread> workers;  // one per bucket
   nrx_server_stats stats{};
   uint64_t next_ticket = 1;
 };
@@ -97,21 +105,12 @@ size_t slot_llr_floats(int S, int n_dmrs, int users, int m_max) {
   return (size_t)(kSymbols - n_dmrs) * S * users * m_max;
 }
 
-// Launch one batch of `reqs` on bucket b with the chosen receiver (async).
-nrx_status launch(nrx_server* s, Bucket& b, const std::vector<Pending>& reqs, int receiver, int users) {
+std::vector<nrx_slot_cfg> slot_cfgs(const nrx_server* s, const Bucket& b, const Lane& L, int n, int users,
+                                    const std::vector<Pending>* reqs) {
   const nrx_server_cfg& c = s->cfg;
-  const int n = (int)reqs.size();
-  const size_t y_per = (size_t)s->B * kSymbols * b.S;
   const size_t d_per = (size_t)c.num_dmrs_symbols * (b.S / 2);
   std::vector<nrx_slot_cfg> cfgs(n);
-  std::vector<int32_t> bits((size_t)n * users);
   for (int i = 0; i < n; ++i) {
-    const nrx_request& r = reqs[i].req;
-    if (cudaMemcpyAsync(b.y + i * y_per, r.y_host, y_per * sizeof(float2), cudaMemcpyHostToDevice, b.st) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(b.dmrs + i * d_per, r.dmrs_host, d_per * sizeof(float2), cudaMemcpyHostToDevice, b.st) !=
-            cudaSuccess)
-      return NRX_ECUDA;
     nrx_slot_cfg& sc = cfgs[i];
     memset(&sc, 0, sizeof(sc));
     sc.num_prb = b.prb;
@@ -120,19 +119,37 @@ nrx_status launch(nrx_server* s, Bucket& b, const std::vector<Pending>& reqs, in
     sc.dmrs_symbols[0] = c.dmrs_symbols[0];
     sc.dmrs_symbols[1] = c.dmrs_symbols[c.num_dmrs_symbols - 1];
     sc.iterations = 0;
-    sc.noise_var = r.noise_var;
-    sc.dmrs_seq = b.dmrs + i * d_per;
+    sc.noise_var = reqs ? (*reqs)[i].req.noise_var : 0.1f;
+    sc.dmrs_seq = L.dmrs + i * d_per;
+  }
+  return cfgs;
+}
+
+// Enqueue one batch on lane `li` of bucket b: uploads, receiver, LLR downloads.
+nrx_status launch(nrx_server* s, Bucket& b, int li, const std::vector<Pending>& reqs, int users) {
+  Lane& L = b.lane[li];
+  const int n = (int)reqs.size();
+  const size_t y_per = (size_t)s->B * kSymbols * b.S;
+  const size_t d_per = (size_t)s->cfg.num_dmrs_symbols * (b.S / 2);
+  std::vector<nrx_slot_cfg> cfgs = slot_cfgs(s, b, L, n, users, &reqs);
+  std::vector<int32_t> bits((size_t)n * users);
+  for (int i = 0; i < n; ++i) {
+    const nrx_request& r = reqs[i].req;
+    if (cudaMemcpyAsync(L.y + i * y_per, r.y_host, y_per * sizeof(float2), cudaMemcpyHostToDevice, L.st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(L.dmrs + i * d_per, r.dmrs_host, d_per * sizeof(float2), cudaMemcpyHostToDevice, L.st) !=
+            cudaSuccess)
+      return NRX_ECUDA;
     for (int u = 0; u < users; ++u) bits[(size_t)i * users + u] = r.bits_per_symbol[u];
   }
-  nrx_status st = receiver == kRcvNrx
-                      ? nrx_detect_batch(b.ctx, n, b.y, cfgs.data(), bits.data(), b.llr, b.st)
-                      : lmmse_detect_batch(b.ctx, n, b.y, cfgs.data(), bits.data(), b.llr, b.st);
+  nrx_status st = li == kRcvNrx ? nrx_detect_batch(b.ctx, n, L.y, cfgs.data(), bits.data(), L.llr, L.st)
+                                : lmmse_detect_batch(b.ctx, n, L.y, cfgs.data(), bits.data(), L.llr, L.st);
   if (st != NRX_OK) return st;
   size_t off = 0;
   for (int i = 0; i < n; ++i) {
     const size_t cnt = nrx_llr_count(&cfgs[i], bits.data() + (size_t)i * users);
     if (reqs[i].req.llr_host &&
-        cudaMemcpyAsync(reqs[i].req.llr_host, b.llr + off, cnt * sizeof(float), cudaMemcpyDeviceToHost, b.st) !=
+        cudaMemcpyAsync(reqs[i].req.llr_host, L.llr + off, cnt * sizeof(float), cudaMemcpyDeviceToHost, L.st) !=
             cudaSuccess)
       return NRX_ECUDA;
     off += cnt;
@@ -140,131 +157,137 @@ nrx_status launch(nrx_server* s, Bucket& b, const std::vector<Pending>& reqs, in
   return NRX_OK;
 }
 
-double est(const Bucket& b, int rcv, int users, int n) {
-  const std::vector<double>& v = b.est_us[rcv][users];
+double est(const Bucket& b, int li, int users, int n) {
+  const std::vector<double>& v = b.est_us[li][users];
   if (v.empty()) return 0.0;
   return v[std::min<size_t>((size_t)n, v.size() - 1)];
 }
 
-void finish(nrx_server* s, int bi) {
+void finish(nrx_server* s, int bi, int li) {
   Bucket& b = s->buckets[bi];
-  Inflight& f = b.cur;
+  Lane& L = b.lane[li];
+  Inflight& f = L.cur;
   float ms_done = 0.f, ms_exec = 0.f;
-  cudaEventElapsedTime(&ms_done, b.ref, f.done);
+  cudaEventElapsedTime(&ms_done, L.ref, f.done);
   cudaEventElapsedTime(&ms_exec, f.start, f.done);
-  const int64_t done_ns = b.ref_ns + (int64_t)(ms_done * 1e6);
-  std::vector<double>& v = b.est_us[f.receiver][f.users];
+  const int64_t done_ns = L.ref_ns + (int64_t)(ms_done * 1e6);
+  std::vector<double>& v = b.est_us[li][f.users];
   if ((size_t)f.n < v.size()) v[f.n] = 0.8 * v[f.n] + 0.2 * (double)ms_exec * 1e3;
-  for (const Pending& p : f.reqs) complete(s, p, f.receiver, NRX_OK, f.n, bi, done_ns);
+  for (const Pending& p : f.reqs) complete(s, p, li, NRX_OK, f.n, bi, done_ns);
   f.reqs.clear();
   f.active = false;
 }
 
-void dispatch(nrx_server* s, int bi) {
-  Bucket& b = s->buckets[bi];
+// Users whose queue head on lane li has the earliest deadline (-1: empty).
+int earliest_users(const nrx_server* s, const Bucket& b, int li) {
   int users = -1;
   int64_t best = INT64_MAX;
   for (int u = 1; u <= s->cfg.max_users; ++u)
-    if (!b.q[u].empty() && b.q[u].front().deadline_ns < best) best = b.q[u].front().deadline_ns, users = u;
-  if (users < 0) return;
-  std::deque<Pending>& Q = b.q[users];
-  const int64_t now = steady_ns();
-  int n = std::min<int>(b.cap, (int)Q.size());
-  // largest NRX batch that still finishes before the earliest deadline
-  while (n > 1 && now + (int64_t)(est(b, kRcvNrx, users, n) * 1e3) > Q.front().deadline_ns) --n;
-  int rcv = kRcvNrx;
-  if (now + (int64_t)(est(b, kRcvNrx, users, n) * 1e3) > Q.front().deadline_ns) {
-    // the NRX misses even alone: LS+LMMSE for every queued slot that would miss
-    rcv = kRcvLmmse;
-    const int64_t nrx1 = now + (int64_t)(est(b, kRcvNrx, users, 1) * 1e3);
-    n = 0;
-    while (n < (int)Q.size() && n < b.cap && Q[n].deadline_ns < nrx1) ++n;
-    if (n == 0) n = 1;
+    if (!b.q[li][u].empty() && b.q[li][u].front().deadline_ns < best) best = b.q[li][u].front().deadline_ns, users = u;
+  return users;
+}
+
+// Move to the fallback lane every NRX-queued slot that the NRX lane cannot
+// finish in time even alone, once the lane is free.
+void triage(nrx_server* s, Bucket& b, int64_t now) {
+  const int64_t free_at = std::max(now, b.lane[kRcvNrx].cur.active ? b.lane[kRcvNrx].busy_until_ns : now);
+  for (int u = 1; u <= s->cfg.max_users; ++u) {
+    std::deque<Pending>& Q = b.q[kRcvNrx][u];
+    const int64_t nrx1 = free_at + (int64_t)(est(b, kRcvNrx, u, 1) * 1e3);
+    while (!Q.empty() && Q.front().deadline_ns < nrx1) {
+      b.q[kRcvLmmse][u].push_back(Q.front());
+      Q.pop_front();
+    }
   }
-  Inflight& f = b.cur;
+}
+
+void dispatch(nrx_server* s, int bi, int li, int64_t now) {
+  Bucket& b = s->buckets[bi];
+  const int users = earliest_users(s, b, li);
+  if (users < 0) return;
+  std::deque<Pending>& Q = b.q[li][users];
+  int n = std::min<int>(b.cap, (int)Q.size());
+  if (li == kRcvNrx)  // the largest batch that still meets the earliest deadline
+    while (n > 1 && now + (int64_t)(est(b, li, users, n) * 1e3) > Q.front().deadline_ns) --n;
+  Lane& L = b.lane[li];
+  Inflight& f = L.cur;
   f.reqs.assign(Q.begin(), Q.begin() + n);
   Q.erase(Q.begin(), Q.begin() + n);
   b.queued -= n;
-  f.receiver = rcv;
   f.users = users;
   f.n = n;
-  cudaEventRecord(f.start, b.st);
-  const nrx_status st = launch(s, b, f.reqs, rcv, users);
-  cudaEventRecord(f.done, b.st);
+  L.busy_until_ns = now + (int64_t)(est(b, li, users, n) * 1e3);
+  cudaEventRecord(f.start, L.st);
+  const nrx_status st = launch(s, b, li, f.reqs, users);
+  cudaEventRecord(f.done, L.st);
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stats.launches++;
   }
   if (st != NRX_OK) {
-    cudaStreamSynchronize(b.st);
+    cudaStreamSynchronize(L.st);
     const int64_t t = steady_ns();
-    for (const Pending& p : f.reqs) complete(s, p, rcv, st, n, bi, t);
+    for (const Pending& p : f.reqs) complete(s, p, li, st, n, bi, t);
     f.reqs.clear();
     return;
   }
   f.active = true;
 }
 
-void worker_main(nrx_server* s) {
+// Worker of one bucket: ingest its submissions, retire finished batches,
+// triage, dispatch.  One thread per bucket keeps the host-side launch work of
+// the buckets in parallel.
+void worker_main(nrx_server* s, int bi) {
   cudaSetDevice(s->device);
+  Bucket& b = s->buckets[bi];
   std::vector<Pending> incoming;
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      bool busy = false;
-      for (const Bucket& b : s->buckets) busy = busy || b.cur.active || b.queued > 0;
-      if (!busy && s->inbox.empty()) {
+      const bool busy = b.lane[0].cur.active || b.lane[1].cur.active || b.queued > 0;
+      if (!busy && b.inbox.empty()) {
         if (s->stop.load()) break;
         s->cv.wait_for(lk, std::chrono::microseconds(200));
       }
-      incoming.assign(s->inbox.begin(), s->inbox.end());
-      s->inbox.clear();
+      incoming.assign(b.inbox.begin(), b.inbox.end());
+      b.inbox.clear();
     }
     for (const Pending& p : incoming) {
-      int bi = 0;
-      while (s->buckets[bi].prb != p.req.num_prb) ++bi;
-      Bucket& b = s->buckets[bi];
       if (b.queued >= s->cfg.queue_capacity) {
         complete(s, p, -1, NRX_OK, 0, bi, steady_ns());
         continue;
       }
-      b.q[p.req.num_users].push_back(p);
+      b.q[kRcvNrx][p.req.num_users].push_back(p);
       b.queued++;
     }
-    for (size_t bi = 0; bi < s->buckets.size(); ++bi)
-      if (s->buckets[bi].cur.active && cudaEventQuery(s->buckets[bi].cur.done) == cudaSuccess) finish(s, (int)bi);
-    for (size_t bi = 0; bi < s->buckets.size(); ++bi)
-      if (!s->buckets[bi].cur.active && s->buckets[bi].queued > 0) dispatch(s, (int)bi);
+    for (int li = 0; li < 2; ++li) {
+      Lane& L = b.lane[li];
+      if (L.cur.active && cudaEventQuery(L.cur.done) == cudaSuccess) finish(s, bi, li);
+    }
+    if (b.queued > 0) {
+      const int64_t now = steady_ns();
+      triage(s, b, now);
+      for (int li = 0; li < 2; ++li)
+        if (!b.lane[li].cur.active) dispatch(s, bi, li, now);
+    }
     std::this_thread::yield();
   }
 }
 
-// Median CUDA-event time (us) of a receiver on zero inputs (unit pilots).
-double time_batch(nrx_server* s, Bucket& b, int rcv, int users, int n) {
-  const nrx_server_cfg& c = s->cfg;
-  std::vector<nrx_slot_cfg> cfgs(n);
+// Median CUDA-event time (us) of a lane's receiver on zero inputs (unit pilots).
+double time_batch(nrx_server* s, Bucket& b, int li, int users, int n) {
+  Lane& L = b.lane[li];
+  std::vector<nrx_slot_cfg> cfgs = slot_cfgs(s, b, L, n, users, nullptr);
   std::vector<int32_t> bits((size_t)n * users, std::min(6, s->m_max - (s->m_max & 1)));
-  const size_t d_per = (size_t)c.num_dmrs_symbols * (b.S / 2);
-  for (int i = 0; i < n; ++i) {
-    nrx_slot_cfg& sc = cfgs[i];
-    memset(&sc, 0, sizeof(sc));
-    sc.num_prb = b.prb;
-    sc.num_users = users;
-    sc.num_dmrs_symbols = c.num_dmrs_symbols;
-    sc.dmrs_symbols[0] = c.dmrs_symbols[0];
-    sc.dmrs_symbols[1] = c.dmrs_symbols[c.num_dmrs_symbols - 1];
-    sc.noise_var = 0.1f;
-    sc.dmrs_seq = b.dmrs + i * d_per;
-  }
   std::vector<float> t;
   for (int r = 0; r < 4; ++r) {
-    cudaEventRecord(b.cur.start, b.st);
-    nrx_status st = rcv == kRcvNrx ? nrx_detect_batch(b.ctx, n, b.y, cfgs.data(), bits.data(), b.llr, b.st)
-                                   : lmmse_detect_batch(b.ctx, n, b.y, cfgs.data(), bits.data(), b.llr, b.st);
-    cudaEventRecord(b.cur.done, b.st);
-    if (st != NRX_OK || cudaEventSynchronize(b.cur.done) != cudaSuccess) return -1.0;
+    cudaEventRecord(L.cur.start, L.st);
+    nrx_status st = li == kRcvNrx ? nrx_detect_batch(b.ctx, n, L.y, cfgs.data(), bits.data(), L.llr, L.st)
+                                  : lmmse_detect_batch(b.ctx, n, L.y, cfgs.data(), bits.data(), L.llr, L.st);
+    cudaEventRecord(L.cur.done, L.st);
+    if (st != NRX_OK || cudaEventSynchronize(L.cur.done) != cudaSuccess) return -1.0;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, b.cur.start, b.cur.done);
+    cudaEventElapsedTime(&ms, L.cur.start, L.cur.done);
     if (r > 0) t.push_back(ms);
   }
   std::sort(t.begin(), t.end());
@@ -278,19 +301,20 @@ __global__ void k_fill_unit(float2* p, size_t n) {
 
 nrx_status calibrate(nrx_server* s, Bucket& b) {
   const size_t d_n = (size_t)b.cap * s->cfg.num_dmrs_symbols * (b.S / 2);
-  if (cudaMemsetAsync(b.y, 0, (size_t)b.cap * s->B * kSymbols * b.S * sizeof(float2), b.st) != cudaSuccess)
-    return NRX_ECUDA;
-  k_fill_unit<<<64, 256, 0, b.st>>>(b.dmrs, d_n);
-  for (int rcv = 0; rcv < 2; ++rcv)
+  for (int li = 0; li < 2; ++li) {
+    Lane& L = b.lane[li];
+    if (cudaMemsetAsync(L.y, 0, (size_t)b.cap * s->B * kSymbols * b.S * sizeof(float2), L.st) != cudaSuccess)
+      return NRX_ECUDA;
+    k_fill_unit<<<64, 256, 0, L.st>>>(L.dmrs, d_n);
     for (int u = 1; u <= s->cfg.max_users; ++u) {
-      std::vector<double>& v = b.est_us[rcv][u];
+      std::vector<double>& v = b.est_us[li][u];
       v.assign((size_t)b.cap + 1, 0.0);
       std::vector<int> sizes;
       for (int n = 1; n < b.cap; n *= 2) sizes.push_back(n);
       sizes.push_back(b.cap);
       std::vector<double> ts;
       for (int n : sizes) {
-        const double us = time_batch(s, b, rcv, u, n);
+        const double us = time_batch(s, b, li, u, n);
         if (us < 0) return NRX_ECUDA;
         ts.push_back(us);
       }
@@ -306,22 +330,25 @@ nrx_status calibrate(nrx_server* s, Bucket& b) {
       }
       v[0] = v[1];
     }
+  }
   return NRX_OK;
 }
 
 void free_bucket(Bucket& b) {
   if (b.ctx) nrx_destroy(b.ctx);
-  if (b.y) cudaFree(b.y);
-  if (b.dmrs) cudaFree(b.dmrs);
-  if (b.llr) cudaFree(b.llr);
-  if (b.cur.start) cudaEventDestroy(b.cur.start);
-  if (b.cur.done) cudaEventDestroy(b.cur.done);
-  if (b.ref) cudaEventDestroy(b.ref);
-  if (b.st) cudaStreamDestroy(b.st);
+  for (Lane& L : b.lane) {
+    if (L.y) cudaFree(L.y);
+    if (L.dmrs) cudaFree(L.dmrs);
+    if (L.llr) cudaFree(L.llr);
+    if (L.cur.start) cudaEventDestroy(L.cur.start);
+    if (L.cur.done) cudaEventDestroy(L.cur.done);
+    if (L.ref) cudaEventDestroy(L.ref);
+    if (L.st) cudaStreamDestroy(L.st);
+  }
   b = Bucket();
 }
 
-// Context + staging of one bucket at batch capacity `cap`; bytes taken in *used.
+// Context + both lanes' staging at batch capacity `cap`; bytes taken in *used.
 nrx_status make_bucket(nrx_server* s, const void* w, size_t wb, Bucket& b, int prb, int cap, size_t* used) {
   size_t free0 = 0, total = 0, free1 = 0;
   cudaMemGetInfo(&free0, &total);
@@ -333,13 +360,17 @@ nrx_status make_bucket(nrx_server* s, const void* w, size_t wb, Bucket& b, int p
   const size_t y_n = (size_t)cap * s->B * kSymbols * b.S;
   const size_t d_n = (size_t)cap * s->cfg.num_dmrs_symbols * (b.S / 2);
   const size_t l_n = (size_t)cap * slot_llr_floats(b.S, s->cfg.num_dmrs_symbols, s->cfg.max_users, s->m_max);
-  if (cudaMalloc(&b.y, y_n * sizeof(float2)) != cudaSuccess || cudaMalloc(&b.dmrs, d_n * sizeof(float2)) != cudaSuccess ||
-      cudaMalloc(&b.llr, l_n * sizeof(float)) != cudaSuccess)
-    return NRX_ENOMEM;
-  if (cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreate(&b.cur.start) != cudaSuccess || cudaEventCreate(&b.cur.done) != cudaSuccess ||
-      cudaEventCreate(&b.ref) != cudaSuccess)
-    return NRX_ECUDA;
+  for (Lane& L : b.lane) {
+    if (cudaMalloc(&L.y, y_n * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&L.dmrs, d_n * sizeof(float2)) != cudaSuccess || cudaMalloc(&L.llr, l_n * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return NRX_ENOMEM;
+    }
+    if (cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&L.cur.start) != cudaSuccess || cudaEventCreate(&L.cur.done) != cudaSuccess ||
+        cudaEventCreate(&L.ref) != cudaSuccess)
+      return NRX_ECUDA;
+  }
   cudaMemGetInfo(&free1, &total);
   *used = free0 > free1 ? free0 - free1 : 0;
   return NRX_OK;
@@ -398,10 +429,11 @@ nrx_status nrx_server_create(const void* weights, size_t weights_bytes, int32_t 
   s->stats.device_bytes = used_total;
   for (Bucket& b : s->buckets) {
     nrx_status st = calibrate(s, b);
-    if (st == NRX_OK) {
-      cudaEventRecord(b.ref, b.st);
-      if (cudaEventSynchronize(b.ref) != cudaSuccess) st = NRX_ECUDA;
-      b.ref_ns = steady_ns();
+    for (Lane& L : b.lane) {
+      if (st != NRX_OK) break;
+      cudaEventRecord(L.ref, L.st);
+      if (cudaEventSynchronize(L.ref) != cudaSuccess) st = NRX_ECUDA;
+      L.ref_ns = steady_ns();
     }
     if (st != NRX_OK) {
       for (Bucket& o : s->buckets) free_bucket(o);
@@ -409,7 +441,7 @@ nrx_status nrx_server_create(const void* weights, size_t weights_bytes, int32_t 
       return st;
     }
   }
-  s->worker = std::thread(worker_main, s);
+  for (int bi = 0; bi < (int)s->buckets.size(); ++bi) s->workers.emplace_back(worker_main, s, bi);
   *out = s;
   return NRX_OK;
 }
@@ -419,9 +451,11 @@ void nrx_server_destroy(nrx_server* s) {
   nrx_server_drain(s, 10000);
   s->stop.store(true);
   s->cv.notify_all();
-  if (s->worker.joinable()) s->worker.join();
+  for (std::thread& t : s->workers)
+    if (t.joinable()) t.join();
   for (Bucket& b : s->buckets) {
-    if (b.st) cudaStreamSynchronize(b.st);
+    for (Lane& L : b.lane)
+      if (L.st) cudaStreamSynchronize(L.st);
     free_bucket(b);
   }
   delete s;
@@ -429,9 +463,10 @@ void nrx_server_destroy(nrx_server* s) {
 
 nrx_status nrx_server_submit(nrx_server* s, const nrx_request* r, uint64_t* ticket) {
   if (!s || !r || !r->y_host || !r->dmrs_host) return NRX_EINVAL;
-  bool found = false;
-  for (const Bucket& b : s->buckets) found = found || b.prb == r->num_prb;
-  if (!found || r->num_users < 1 || r->num_users > s->cfg.max_users) return NRX_EINVAL;
+  int bi = -1;
+  for (int i = 0; i < (int)s->buckets.size(); ++i)
+    if (s->buckets[i].prb == r->num_prb) bi = i;
+  if (bi < 0 || r->num_users < 1 || r->num_users > s->cfg.max_users) return NRX_EINVAL;
   for (int u = 0; u < r->num_users; ++u) {
     const int m = r->bits_per_symbol[u];
     if ((m != 2 && m != 4 && m != 6) || m > s->m_max) return NRX_EINVAL;
@@ -444,11 +479,26 @@ nrx_status nrx_server_submit(nrx_server* s, const nrx_request* r, uint64_t* tick
   {
     std::lock_guard<std::mutex> lk(s->mu);
     p.ticket = s->next_ticket++;
-    s->inbox.push_back(p);
+    s->buckets[bi].inbox.push_back(p);
     s->stats.submitted++;
   }
-  s->cv.notify_one();
+  s->cv.notify_all();
   if (ticket) *ticket = p.ticket;
+  return NRX_OK;
+}
+
+nrx_status nrx_server_replay(nrx_server* s, int32_t n, const nrx_request* reqs, uint64_t* tickets,
+                             int64_t* max_late_ns) {
+  if (!s || n < 0 || (n > 0 && !reqs)) return NRX_EINVAL;
+  int64_t late = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    while (steady_ns() < reqs[i].arrival_ns) {
+    }
+    late = std::max(late, steady_ns() - reqs[i].arrival_ns);
+    const nrx_status st = nrx_server_submit(s, &reqs[i], tickets ? tickets + i : nullptr);
+    if (st != NRX_OK) return st;
+  }
+  if (max_late_ns) *max_late_ns = late;
   return NRX_OK;
 }
 

@@ -17,7 +17,7 @@ import numpy as np
 from . import nrx, synth
 
 SERVER_EXPORTED = ("nrx_server_create", "nrx_server_destroy", "nrx_server_now_ns", "nrx_server_submit",
-                   "nrx_server_poll", "nrx_server_drain", "nrx_server_get_stats")
+                   "nrx_server_replay", "nrx_server_poll", "nrx_server_drain", "nrx_server_get_stats")
 MAX_BUCKETS = 8
 RECEIVER_NAMES = {0: "nrx", 1: "lmmse", -1: "rejected"}
 
@@ -65,6 +65,9 @@ def load():
         lib.nrx_server_now_ns.restype = ctypes.c_int64
         lib.nrx_server_submit.argtypes = [P, ctypes.POINTER(nrx_request), ctypes.POINTER(ctypes.c_uint64)]
         lib.nrx_server_submit.restype = ctypes.c_int
+        lib.nrx_server_replay.argtypes = [P, I32, ctypes.POINTER(nrx_request), ctypes.POINTER(ctypes.c_uint64),
+                                          ctypes.POINTER(ctypes.c_int64)]
+        lib.nrx_server_replay.restype = ctypes.c_int
         lib.nrx_server_poll.argtypes = [P, ctypes.POINTER(nrx_completion), I32, ctypes.POINTER(I32)]
         lib.nrx_server_poll.restype = ctypes.c_int
         lib.nrx_server_drain.argtypes = [P, I32]
@@ -123,6 +126,17 @@ class Server:
         if st != nrx.NRX_OK:
             raise nrx.NrxError(st, "nrx_server_submit")
         return t.value
+
+    def replay(self, reqs) -> tuple:
+        """Submit a ctypes array of requests at their arrival times (native
+        spin-wait); returns (tickets, max lateness in ns)."""
+        n = len(reqs)
+        tickets = (ctypes.c_uint64 * n)()
+        late = ctypes.c_int64()
+        st = self._lib.nrx_server_replay(self.h, n, reqs, tickets, ctypes.byref(late))
+        if st != nrx.NRX_OK:
+            raise nrx.NrxError(st, "nrx_server_replay")
+        return list(tickets), late.value
 
     def poll(self, max_out: int = 4096) -> List[nrx_completion]:
         buf = (nrx_completion * max_out)()
@@ -217,22 +231,17 @@ def run_load(srv: Server, spec: LoadSpec) -> Dict[str, object]:
             t += float(rng.exponential(1.0 / spec.slots_per_s_per_cell))
     events.sort()
     picks = [(cell_prb[c], int(rng.choice(spec.users)), int(rng.integers(0, spec.pool_per_key))) for _, c in events]
-    reqs = []
-    for (t, _), (prb, U, k) in zip(events, picks):
+    reqs = (nrx_request * len(events))()
+    for i, ((t, _), (prb, U, k)) in enumerate(zip(events, picks)):
         sl, y, d, l = pools[(prb, U)][k]
-        reqs.append(make_request(sl, y, d, l))
+        reqs[i] = make_request(sl, y, d, l)
     res_per_req = [14 * 12 * prb for (prb, _, _) in picks]
+    t0 = srv.now_ns() + 50_000_000
+    for i, (t, _) in enumerate(events):
+        reqs[i].arrival_ns = t0 + int(t * 1e9)
+    tickets, max_late = srv.replay(reqs)
+    res_of: Dict[int, int] = dict(zip(tickets, res_per_req))
     comps: List[nrx_completion] = []
-    res_of: Dict[int, int] = {}
-    t0 = srv.now_ns() + 20_000_000
-    for i, ((t, _), r) in enumerate(zip(events, reqs)):
-        at = t0 + int(t * 1e9)
-        while srv.now_ns() < at:
-            pass
-        r.arrival_ns = at
-        res_of[srv.submit(r)] = res_per_req[i]
-        if (i & 63) == 63:
-            comps.extend(srv.poll())
     srv.drain(60000)
     comps.extend(srv.poll(max(4096, len(reqs))))
     lat = {0: [], 1: []}
@@ -263,5 +272,6 @@ def run_load(srv: Server, spec: LoadSpec) -> Dict[str, object]:
                        "nrx_p50": pct(lat[0], 50), "nrx_p99": pct(lat[0], 99),
                        "lmmse_p50": pct(lat[1], 50), "lmmse_p99": pct(lat[1], 99)},
         "nrx_res_per_s": served_res[0] / spec.seconds, "mean_batch": float(np.mean(batches)) if batches else 0.0,
+        "max_submit_late_us": max_late / 1e3,
         "stats": srv.stats(),
     }
