@@ -183,15 +183,20 @@ __device__ __forceinline__ void tc_teardown(TcCta& c, uint32_t ncols, bool timed
 // ---------------------------------------------------------------------------
 template <typename P>
 struct MpLayout {
+  // With the split BF16 weights (2 x 8 KB per matrix) the CTA exchanges h one
+  // column half at a time (FP32 [128][32], 16 KB), which keeps two CTAs per
+  // SM; the other policies fit two CTAs with the whole rows (FP32 [128][64]),
+  // which FP8 needs for its per-row scales anyway.
+  static constexpr bool kHalfX = P::split;
   static constexpr int A_S = 0;
   static constexpr int A_G = 16384;
-  static constexpr int XCH = 32768;  // FP32 [128][64] exchange of h; later 16-bit z staging
-  static constexpr int W1 = 65536;
+  static constexpr int XCH = 32768;  // FP32 exchange of h; later 16-bit z staging [128][128 B]
+  static constexpr int W1 = XCH + (kHalfX ? 16384 : 32768);
   static constexpr int WS = W1 + wbytes<P>();
   static constexpr int WC = WS + wbytes<P>();
   static constexpr int VEC = WC + wbytes<P>();  // b1, bin, -, pe_t, pe_f, sW1, sWS, sWC: 8 x 64 floats
   static constexpr int RSC = VEC + 8 * 64 * 4;   // E4M3 row scales of A_S and A_G: 2 x 128 floats
-  static constexpr int BAR = RSC + 256 * 4;
+  static constexpr int BAR = RSC + (P::fp8 ? 256 * 4 : 0);
   static constexpr int TOTAL = BAR + 16;
   static constexpr int DYN = TOTAL + 1024;
 };
@@ -302,76 +307,137 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
       timed_out = true;
       break;
     }
-    // h = ReLU(acc + b1) -> FP32 exchange, row r, columns [32 hc, 32 hc + 32);
-    // float4 chunk k of a row is stored at k ^ (r & 7)
-    {
-      uint32_t a[16], b[16];
-      tc::tmem_ld16(c.tmem + tlane + 32 * hc, a);
-      tc::tmem_ld16(c.tmem + tlane + 32 * hc + 16, b);
-      tc::tmem_wait16(a);
-      tc::tmem_wait16(b);
-      const float* b1 = vec + 32 * hc;
-      float sc[32];  // dequantisation factor per column (1 unless FP8)
+    if constexpr (MpL::kHalfX) {
+      // h = ReLU(acc + b1) of row r, columns [32 hc, 32 hc + 32), in registers;
+      // then, per column half: its writer warps store it to the exchange
+      // (float4 chunk k of a row at k ^ (r & 7)), and all threads form
+      // g_u = sum over the other active users of that half -> A_G (SW128).
+      float hval[32];
+      {
+        uint32_t a[16], b[16];
+        tc::tmem_ld16(c.tmem + tlane + 32 * hc, a);
+        tc::tmem_ld16(c.tmem + tlane + 32 * hc + 16, b);
+        tc::tmem_wait16(a);
+        tc::tmem_wait16(b);
+        const float* b1 = vec + 32 * hc;
 #pragma unroll
-      for (int e = 0; e < 32; ++e) sc[e] = 1.f;
-      if constexpr (P::fp8) {
-        const float rs = rsc_s[r];
-#pragma unroll
-        for (int e = 0; e < 32; ++e) sc[e] = rs * vec[320 + 32 * hc + e];
+        for (int e = 0; e < 16; ++e) {
+          hval[e] = fmaxf(__uint_as_float(a[e]) + b1[e], 0.f);
+          hval[16 + e] = fmaxf(__uint_as_float(b[e]) + b1[16 + e], 0.f);
+        }
       }
+      tc::tc_fence_before();
+#pragma unroll 1
+      for (int half = 0; half < 2; ++half) {
+        if (hc == half) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const uint32_t* src = k < 4 ? a + 4 * k : b + 4 * (k - 4);
-        const int kk = 8 * hc + k;
-        *reinterpret_cast<float4*>(xch + r * 64 + ((kk ^ (r & 7)) << 2)) =
-            make_float4(fmaxf(fmaf(__uint_as_float(src[0]), sc[4 * k], b1[4 * k]), 0.f),
-                        fmaxf(fmaf(__uint_as_float(src[1]), sc[4 * k + 1], b1[4 * k + 1]), 0.f),
-                        fmaxf(fmaf(__uint_as_float(src[2]), sc[4 * k + 2], b1[4 * k + 2]), 0.f),
-                        fmaxf(fmaf(__uint_as_float(src[3]), sc[4 * k + 3], b1[4 * k + 3]), 0.f));
-      }
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    // g_u = sum over the other active users -> A_G (SW128).  Items (j, channel
-    // quad cq); the loop is warp-uniform so FP8 can reduce a row over 16 lanes.
-    for (int i0 = 0; i0 < nre * 16; i0 += kThreads) {
-      const int i = i0 + tid;
-      const bool valid = i < nre * 16;
-      const int j = valid ? i >> 4 : 0, cq = i & 15;
-      float4 hv[NRX_MAX_USERS];
+          for (int k = 0; k < 8; ++k)
+            *reinterpret_cast<float4*>(xch + r * 32 + ((k ^ (r & 7)) << 2)) =
+                make_float4(hval[4 * k], hval[4 * k + 1], hval[4 * k + 2], hval[4 * k + 3]);
+        }
+        __syncthreads();
+        for (int i0 = 0; i0 < nre * 8; i0 += kThreads) {
+          const int i = i0 + tid;
+          if (i >= nre * 8) break;
+          const int j = i >> 3, cql = i & 7, cq = 8 * half + cql;
+          float4 hv[NRX_MAX_USERS];
 #pragma unroll
-      for (int u = 0; u < NRX_MAX_USERS; ++u) {
-        const int rw = u * nre + j;
-        hv[u] = u < U ? *reinterpret_cast<const float4*>(xch + rw * 64 + ((cq ^ (rw & 7)) << 2))
-                      : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int u = 0; u < NRX_MAX_USERS; ++u) {
-        if (u >= U) break;
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int v = 0; v < NRX_MAX_USERS; ++v)
-          if (v != u && v < U) {
-            a.x += hv[v].x;
-            a.y += hv[v].y;
-            a.z += hv[v].z;
-            a.w += hv[v].w;
+          for (int u = 0; u < NRX_MAX_USERS; ++u) {
+            const int rw = u * nre + j;
+            hv[u] = u < U ? *reinterpret_cast<const float4*>(xch + rw * 32 + ((cql ^ (rw & 7)) << 2))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
           }
-        const int row = u * nre + j;
+#pragma unroll
+          for (int u = 0; u < NRX_MAX_USERS; ++u) {
+            if (u >= U) break;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int v = 0; v < NRX_MAX_USERS; ++v)
+              if (v != u && v < U) {
+                a.x += hv[v].x;
+                a.y += hv[v].y;
+                a.z += hv[v].z;
+                a.w += hv[v].w;
+              }
+            const int row = u * nre + j;
+            *reinterpret_cast<uint2*>(sm + MpL::A_G + tc::sw128_offset(row, 4 * cq)) =
+                make_uint2(Op<T>::pack(a.x, a.y), Op<T>::pack(a.z, a.w));
+          }
+        }
+        if (half == 0) __syncthreads();  // the second half overwrites the exchange
+      }
+    } else {
+      // h = ReLU(acc + b1) -> FP32 exchange, row r, columns [32 hc, 32 hc + 32);
+      // float4 chunk k of a row is stored at k ^ (r & 7)
+      {
+        uint32_t a[16], b[16];
+        tc::tmem_ld16(c.tmem + tlane + 32 * hc, a);
+        tc::tmem_ld16(c.tmem + tlane + 32 * hc + 16, b);
+        tc::tmem_wait16(a);
+        tc::tmem_wait16(b);
+        const float* b1 = vec + 32 * hc;
+        float sc[32];  // dequantisation factor per column (1 unless FP8)
+  #pragma unroll
+        for (int e = 0; e < 32; ++e) sc[e] = 1.f;
         if constexpr (P::fp8) {
-          float am = fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w)));
-#pragma unroll
-          for (int o = 1; o < 16; o <<= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
-          const float sc = e4m3_scale(am), inv = 1.f / sc;
-          if (valid) {
-            *reinterpret_cast<uint32_t*>(sm + MpL::A_G + (row >> 3) * 1024 + (row & 7) * 128 +
-                                         (((cq >> 2) ^ (row & 7)) << 4) + (cq & 3) * 4) =
-                e4m3x2(a.x * inv, a.y * inv) | (e4m3x2(a.z * inv, a.w * inv) << 16);
-            if (cq == 0) rsc_g[row] = sc;
+          const float rs = rsc_s[r];
+  #pragma unroll
+          for (int e = 0; e < 32; ++e) sc[e] = rs * vec[320 + 32 * hc + e];
+        }
+  #pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const uint32_t* src = k < 4 ? a + 4 * k : b + 4 * (k - 4);
+          const int kk = 8 * hc + k;
+          *reinterpret_cast<float4*>(xch + r * 64 + ((kk ^ (r & 7)) << 2)) =
+              make_float4(fmaxf(fmaf(__uint_as_float(src[0]), sc[4 * k], b1[4 * k]), 0.f),
+                          fmaxf(fmaf(__uint_as_float(src[1]), sc[4 * k + 1], b1[4 * k + 1]), 0.f),
+                          fmaxf(fmaf(__uint_as_float(src[2]), sc[4 * k + 2], b1[4 * k + 2]), 0.f),
+                          fmaxf(fmaf(__uint_as_float(src[3]), sc[4 * k + 3], b1[4 * k + 3]), 0.f));
+        }
+      }
+      tc::tc_fence_before();
+      __syncthreads();
+      // g_u = sum over the other active users -> A_G (SW128).  Items (j, channel
+      // quad cq); the loop is warp-uniform so FP8 can reduce a row over 16 lanes.
+      for (int i0 = 0; i0 < nre * 16; i0 += kThreads) {
+        const int i = i0 + tid;
+        const bool valid = i < nre * 16;
+        const int j = valid ? i >> 4 : 0, cq = i & 15;
+        float4 hv[NRX_MAX_USERS];
+  #pragma unroll
+        for (int u = 0; u < NRX_MAX_USERS; ++u) {
+          const int rw = u * nre + j;
+          hv[u] = u < U ? *reinterpret_cast<const float4*>(xch + rw * 64 + ((cq ^ (rw & 7)) << 2))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+  #pragma unroll
+        for (int u = 0; u < NRX_MAX_USERS; ++u) {
+          if (u >= U) break;
+          float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+  #pragma unroll
+          for (int v = 0; v < NRX_MAX_USERS; ++v)
+            if (v != u && v < U) {
+              a.x += hv[v].x;
+              a.y += hv[v].y;
+              a.z += hv[v].z;
+              a.w += hv[v].w;
+            }
+          const int row = u * nre + j;
+          if constexpr (P::fp8) {
+            float am = fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w)));
+  #pragma unroll
+            for (int o = 1; o < 16; o <<= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+            const float sc = e4m3_scale(am), inv = 1.f / sc;
+            if (valid) {
+              *reinterpret_cast<uint32_t*>(sm + MpL::A_G + (row >> 3) * 1024 + (row & 7) * 128 +
+                                           (((cq >> 2) ^ (row & 7)) << 4) + (cq & 3) * 4) =
+                  e4m3x2(a.x * inv, a.y * inv) | (e4m3x2(a.z * inv, a.w * inv) << 16);
+              if (cq == 0) rsc_g[row] = sc;
+            }
+          } else if (valid) {
+            *reinterpret_cast<uint2*>(sm + MpL::A_G + tc::sw128_offset(row, 4 * cq)) =
+                make_uint2(Op<T>::pack(a.x, a.y), Op<T>::pack(a.z, a.w));
           }
-        } else if (valid) {
-          *reinterpret_cast<uint2*>(sm + MpL::A_G + tc::sw128_offset(row, 4 * cq)) =
-              make_uint2(Op<T>::pack(a.x, a.y), Op<T>::pack(a.z, a.w));
         }
       }
     }
