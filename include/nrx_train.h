@@ -66,6 +66,24 @@ nrx_status nrx_train_gemm(int32_t M, int32_t N, int32_t K, const float* A, int64
                           int64_t sbk, int64_t sbn, const float* bias, const float* R, int64_t ldr, float* C,
                           int64_t ldc, int32_t relu, int32_t accumulate, int32_t split_k, void* stream);
 
+/*
+ * nrx_train_gemm with BF16 tensor-core compute (tcgen05, kind::f16): the same
+ * arguments, layouts, epilogues and errors; A and B are rounded to BF16
+ * (round to nearest even) as they are staged, products accumulate in FP32.
+ * One CTA per 128 x 64 output tile and K range (split_k ranges, each a whole
+ * number of 64-wide chunks).  A bounded wait for the tensor cores that gives
+ * up sets a device flag (nrx_train_check) and leaves the tile unwritten.
+ */
+nrx_status nrx_train_gemm_bf16(int32_t M, int32_t N, int32_t K, const float* A, int64_t sam, int64_t sak,
+                               const float* B, int64_t sbk, int64_t sbn, const float* bias, const float* R,
+                               int64_t ldr, float* C, int64_t ldc, int32_t relu, int32_t accumulate, int32_t split_k,
+                               void* stream);
+
+/* Synchronise `stream`; NRX_ETIMEDOUT (and clear the flag) if a tensor-core
+ * training GEMM gave up waiting since the last check, NRX_ECUDA on a CUDA
+ * error, else NRX_OK. */
+nrx_status nrx_train_check(void* stream);
+
 /* out[n] += sum_m X[m*ldx + n], n < N (bias gradients). */
 nrx_status nrx_train_colsum(int32_t M, int32_t N, const float* X, int64_t ldx, float* out, void* stream);
 
@@ -81,7 +99,7 @@ nrx_status nrx_train_dw3(int32_t planes, int32_t S, int32_t C, const float* X, c
                          int32_t relu, float* Y, void* stream);
 
 /* Tap gradient of nrx_train_dw3: gk[c][i][j] += sum G[t][s][c] X[t+i-1][s+j-1][c]
- * over all planes, t, s (zero padding).  Float atomics. */
+ * over all planes, t, s (zero padding).  Float atomics.  1 <= C <= 1024. */
 nrx_status nrx_train_dw3_wgrad(int32_t planes, int32_t S, int32_t C, const float* X, const float* G, float* gk,
                                void* stream);
 

@@ -115,12 +115,31 @@ __global__ void __launch_bounds__(kThreads) k_gemm(int M, int N, int K, const fl
   }
 }
 
-// out[n] += sum_m X[m][n] (bias gradients); FP32 partial sums per CTA.
-__global__ void k_colsum(int M, int N, const float* __restrict__ X, long long ldx, float* __restrict__ out) {
-  for (int n = threadIdx.x; n < N; n += blockDim.x) {
-    float acc = 0.f;
-    for (int m = blockIdx.x; m < M; m += gridDim.x) acc += X[(long long)m * ldx + n];
-    atomicAdd(out + n, acc);
+// out[n] += sum_m X[m][n] (bias gradients).  256 threads: 64 columns x 4 row
+// groups, four independent partial sums per thread, a shared-memory reduction
+// over the row groups, one atomic per column and CTA.
+__global__ void __launch_bounds__(256) k_colsum(int M, int N, const float* __restrict__ X, long long ldx,
+                                                float* __restrict__ out) {
+  __shared__ float red[4][64];
+  const int cn = threadIdx.x & 63, rg = threadIdx.x >> 6;
+  const long long step = (long long)gridDim.x * 4;
+  for (int n0 = 0; n0 < N; n0 += 64) {
+    const int n = n0 + cn;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    if (n < N) {
+      long long m = (long long)blockIdx.x * 4 + rg;
+      for (; m + 3 * step < M; m += 4 * step) {
+        a0 += X[m * ldx + n];
+        a1 += X[(m + step) * ldx + n];
+        a2 += X[(m + 2 * step) * ldx + n];
+        a3 += X[(m + 3 * step) * ldx + n];
+      }
+      for (; m < M; m += step) a0 += X[m * ldx + n];
+    }
+    red[rg][cn] = (a0 + a1) + (a2 + a3);
+    __syncthreads();
+    if (rg == 0 && n < N) atomicAdd(out + n, (red[0][cn] + red[1][cn]) + (red[2][cn] + red[3][cn]));
+    __syncthreads();
   }
 }
 
@@ -128,58 +147,96 @@ __global__ void k_colsum(int M, int N, const float* __restrict__ X, long long ld
 // Depthwise 3x3 over [planes][14][S][C], zero padding:
 //   Y[t,s,c] = act(sum_{i,j} k[c][i][j] X[t+i-1, s+j-1, c]); with flip the taps
 //   are read as k[c][2-i][2-j] (the adjoint, used for the input gradient).
+// One thread per (plane, s, c) slides down the 14 symbols with a window of
+// three input rows x three subcarriers (each input value is loaded once per
+// thread, consecutive threads read consecutive channels).
 // ---------------------------------------------------------------------------
-__global__ void k_dw3(int planes, int S, int C, const float* __restrict__ X, const float* __restrict__ k, int flip,
-                      int relu, float* __restrict__ Y) {
-  const size_t total = (size_t)planes * NRX_SYMBOLS * S * C;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    const int s = (int)((i / C) % S);
-    const int t = (int)((i / ((size_t)C * S)) % NRX_SYMBOLS);
-    const size_t plane = i / ((size_t)C * S * NRX_SYMBOLS);
-    const float* xp = X + plane * NRX_SYMBOLS * S * C;
-    float acc = 0.f;
-    for (int di = 0; di < 3; ++di) {
-      const int tt = t + di - 1;
-      if (tt < 0 || tt >= NRX_SYMBOLS) continue;
-      for (int dj = 0; dj < 3; ++dj) {
-        const int ss = s + dj - 1;
-        if (ss < 0 || ss >= S) continue;
-        const float kv = flip ? k[c * 9 + (2 - di) * 3 + (2 - dj)] : k[c * 9 + di * 3 + dj];
-        acc = fmaf(kv, xp[((size_t)tt * S + ss) * C + c], acc);
-      }
-    }
-    Y[i] = relu ? fmaxf(acc, 0.f) : acc;
+__device__ __forceinline__ void dw_load_row(const float* __restrict__ xp, int t, int s, int S, int C, int c,
+                                            float (&r)[3]) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int ss = s + j - 1;
+    r[j] = (t >= 0 && t < NRX_SYMBOLS && ss >= 0 && ss < S) ? xp[((size_t)t * S + ss) * C + c] : 0.f;
   }
 }
 
-// gk[c][i][j] += sum_{plane,t,s} G[t,s,c] X[t+i-1, s+j-1, c]
-__global__ void k_dw3_wgrad(int planes, int S, int C, const float* __restrict__ X, const float* __restrict__ G,
-                            float* __restrict__ gk) {
-  const size_t n_re = (size_t)planes * NRX_SYMBOLS * S;
-  for (int c = threadIdx.x; c < C; c += blockDim.x) {
-    float acc[9] = {};
-    for (size_t r = blockIdx.x; r < n_re; r += gridDim.x) {
-      const int s = (int)(r % S);
-      const int t = (int)((r / S) % NRX_SYMBOLS);
-      const size_t plane = r / ((size_t)S * NRX_SYMBOLS);
-      const float gv = G[r * C + c];
-      const float* xp = X + plane * NRX_SYMBOLS * S * C;
+__global__ void k_dw3(int planes, int S, int C, const float* __restrict__ X, const float* __restrict__ k, int flip,
+                      int relu, float* __restrict__ Y) {
+  const size_t total = (size_t)planes * S * C;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const int s = (int)((i / C) % S);
+    const size_t plane = i / ((size_t)C * S);
+    const float* xp = X + plane * NRX_SYMBOLS * S * C;
+    float* yp = Y + plane * NRX_SYMBOLS * S * C;
+    float kk[9];
 #pragma unroll
-      for (int di = 0; di < 3; ++di) {
-        const int tt = t + di - 1;
-        if (tt < 0 || tt >= NRX_SYMBOLS) continue;
+    for (int j = 0; j < 9; ++j) kk[j] = k[c * 9 + (flip ? 8 - j : j)];
+    float r0[3], r1[3], r2[3];
+    dw_load_row(xp, -1, s, S, C, c, r0);
+    dw_load_row(xp, 0, s, S, C, c, r1);
+    dw_load_row(xp, 1, s, S, C, c, r2);
+    for (int t = 0; t < NRX_SYMBOLS; ++t) {
+      float acc = 0.f;
 #pragma unroll
-        for (int dj = 0; dj < 3; ++dj) {
-          const int ss = s + dj - 1;
-          if (ss < 0 || ss >= S) continue;
-          acc[di * 3 + dj] = fmaf(gv, xp[((size_t)tt * S + ss) * C + c], acc[di * 3 + dj]);
-        }
+      for (int j = 0; j < 3; ++j) acc = fmaf(kk[j], r0[j], acc);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) acc = fmaf(kk[3 + j], r1[j], acc);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) acc = fmaf(kk[6 + j], r2[j], acc);
+      yp[((size_t)t * S + s) * C + c] = relu ? fmaxf(acc, 0.f) : acc;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        r0[j] = r1[j];
+        r1[j] = r2[j];
       }
+      dw_load_row(xp, t + 2, s, S, C, c, r2);
+    }
+  }
+}
+
+// gk[c][i][j] += sum_{plane,t,s} G[t,s,c] X[t+i-1, s+j-1, c]: one thread per
+// (plane, s, c) sliding down the symbols, partial sums reduced per channel in
+// shared memory, then one atomic per (channel, tap) and CTA.
+__global__ void __launch_bounds__(256) k_dw3_wgrad(int planes, int S, int C, const float* __restrict__ X,
+                                                   const float* __restrict__ G, float* __restrict__ gk) {
+  extern __shared__ float red[];  // [C][9]
+  for (int i = threadIdx.x; i < 9 * C; i += blockDim.x) red[i] = 0.f;
+  __syncthreads();
+  const size_t total = (size_t)planes * S * C;
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < total) {
+    const int c = (int)(i % C);
+    const int s = (int)((i / C) % S);
+    const size_t plane = i / ((size_t)C * S);
+    const float* xp = X + plane * NRX_SYMBOLS * S * C;
+    const float* gp = G + plane * NRX_SYMBOLS * S * C;
+    float acc[9] = {};
+    float r0[3], r1[3], r2[3];
+    dw_load_row(xp, -1, s, S, C, c, r0);
+    dw_load_row(xp, 0, s, S, C, c, r1);
+    dw_load_row(xp, 1, s, S, C, c, r2);
+    for (int t = 0; t < NRX_SYMBOLS; ++t) {
+      const float gv = gp[((size_t)t * S + s) * C + c];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        acc[j] = fmaf(gv, r0[j], acc[j]);
+        acc[3 + j] = fmaf(gv, r1[j], acc[3 + j]);
+        acc[6 + j] = fmaf(gv, r2[j], acc[6 + j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        r0[j] = r1[j];
+        r1[j] = r2[j];
+      }
+      dw_load_row(xp, t + 2, s, S, C, c, r2);
     }
 #pragma unroll
-    for (int j = 0; j < 9; ++j) atomicAdd(gk + c * 9 + j, acc[j]);
+    for (int j = 0; j < 9; ++j) atomicAdd(red + c * 9 + j, acc[j]);
   }
+  __syncthreads();
+  for (int j = threadIdx.x; j < 9 * C; j += blockDim.x)
+    if (red[j] != 0.f) atomicAdd(gk + j, red[j]);
 }
 
 // G <- G * (Y > 0)
@@ -332,24 +389,27 @@ nrx_status nrx_train_gemm(int32_t M, int32_t N, int32_t K, const float* A, int64
 
 nrx_status nrx_train_colsum(int32_t M, int32_t N, const float* X, int64_t ldx, float* out, void* stream) {
   if (M < 1 || N < 1 || !X || !out) return NRX_EINVAL;
-  k_colsum<<<M < 1024 ? M : 1024, 128, 0, static_cast<cudaStream_t>(stream)>>>(M, N, X, ldx, out);
+  const int blocks = (M + 63) / 64 < 592 ? (M + 63) / 64 : 592;
+  k_colsum<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(M, N, X, ldx, out);
   return to_status(cudaGetLastError());
 }
 
 nrx_status nrx_train_dw3(int32_t planes, int32_t S, int32_t C, const float* X, const float* k, int32_t flip,
                          int32_t relu, float* Y, void* stream) {
   if (planes < 1 || S < 1 || C < 1 || !X || !k || !Y) return NRX_EINVAL;
-  const size_t n = (size_t)planes * NRX_SYMBOLS * S * C;
+  const size_t n = (size_t)planes * S * C;  // one thread per (plane, subcarrier, channel)
   k_dw3<<<blocks_for(n), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(planes, S, C, X, k, flip, relu, Y);
   return to_status(cudaGetLastError());
 }
 
 nrx_status nrx_train_dw3_wgrad(int32_t planes, int32_t S, int32_t C, const float* X, const float* G, float* gk,
                                void* stream) {
-  if (planes < 1 || S < 1 || C < 1 || !X || !G || !gk) return NRX_EINVAL;
-  const size_t n_re = (size_t)planes * NRX_SYMBOLS * S;
-  const int blocks = (int)(n_re < 2048 ? n_re : 2048);
-  k_dw3_wgrad<<<blocks, C < 256 ? C : 256, 0, static_cast<cudaStream_t>(stream)>>>(planes, S, C, X, G, gk);
+  if (planes < 1 || S < 1 || C < 1 || C > 1024 || !X || !G || !gk) return NRX_EINVAL;
+  const size_t n = (size_t)planes * S * C;  // one thread per (plane, subcarrier, channel)
+  const size_t blocks = (n + 255) / 256;
+  if (blocks > 0x7fffffff) return NRX_EINVAL;
+  k_dw3_wgrad<<<(unsigned)blocks, 256, 9 * C * sizeof(float), static_cast<cudaStream_t>(stream)>>>(planes, S, C, X,
+                                                                                                   G, gk);
   return to_status(cudaGetLastError());
 }
 

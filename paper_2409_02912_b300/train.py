@@ -26,7 +26,7 @@ import numpy as np
 from . import nrx, synth
 
 TRAIN_EXPORTED = (
-    "nrx_train_features", "nrx_train_gemm", "nrx_train_colsum", "nrx_train_dw3", "nrx_train_dw3_wgrad",
+    "nrx_train_features", "nrx_train_gemm", "nrx_train_gemm_bf16", "nrx_train_check", "nrx_train_colsum", "nrx_train_dw3", "nrx_train_dw3_wgrad",
     "nrx_train_relu_mask", "nrx_train_aggregate", "nrx_train_axpy", "nrx_train_bce", "nrx_train_mse",
     "nrx_train_zero", "nrx_train_copy", "nrx_train_adam",
 )
@@ -45,6 +45,8 @@ def load():
     sig = {
         "nrx_train_features": [I32, I32, P, CFG, P, P],
         "nrx_train_gemm": [I32, I32, I32, P, I64, I64, P, I64, I64, P, P, I64, P, I64, I32, I32, I32, P],
+        "nrx_train_gemm_bf16": [I32, I32, I32, P, I64, I64, P, I64, I64, P, P, I64, P, I64, I32, I32, I32, P],
+        "nrx_train_check": [P],
         "nrx_train_colsum": [I32, I32, P, I64, P, P],
         "nrx_train_dw3": [I32, I32, I32, P, P, I32, I32, P, P],
         "nrx_train_dw3_wgrad": [I32, I32, I32, P, P, P, P],
@@ -72,9 +74,12 @@ def _ptr(t) -> Optional[int]:
 class _Ops:
     """Thin wrappers: one C call each, raising on a non-OK status."""
 
-    def __init__(self, stream_ptr):
+    def __init__(self, stream_ptr, precision: str = "fp32"):
         self.lib = load()
         self.st = stream_ptr
+        if precision not in ("fp32", "bf16"):
+            raise ValueError(f"training precision {precision!r}: fp32 or bf16")
+        self._gemm = self.lib.nrx_train_gemm_bf16 if precision == "bf16" else self.lib.nrx_train_gemm
 
     def _ok(self, st, what):
         if st != nrx.NRX_OK:
@@ -82,8 +87,8 @@ class _Ops:
 
     def gemm(self, M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias=None, R=None, ldr=0, relu=False,
              accumulate=False, split_k=1):
-        self._ok(self.lib.nrx_train_gemm(M, N, K, A, sam, sak, B, sbk, sbn, bias, R, ldr, C, ldc, int(relu),
-                                         int(accumulate), split_k, self.st), "nrx_train_gemm")
+        self._ok(self._gemm(M, N, K, A, sam, sak, B, sbk, sbn, bias, R, ldr, C, ldc, int(relu), int(accumulate),
+                            split_k, self.st), "nrx_train_gemm")
 
     def colsum(self, M, N, X, ldx, out):
         self._ok(self.lib.nrx_train_colsum(M, N, X, ldx, out, self.st), "nrx_train_colsum")
@@ -111,8 +116,10 @@ class _Ops:
 
 
 class Trainer:
-    """FP32 training state of one network (master weights, gradients, Adam
-    moments) on the current CUDA device.
+    """Training state of one network (FP32 master weights, gradients, Adam
+    moments) on the current CUDA device.  ``precision`` selects the GEMMs of
+    the forward and reverse passes: "fp32" (CUDA cores) or "bf16" (tensor
+    cores, BF16 operands, FP32 accumulation); everything else is FP32.
 
     ``loss_and_grad(batch)`` runs the forward and reverse passes and leaves the
     gradient in ``self.g``; ``step(batch)`` adds the Adam update.
@@ -120,9 +127,13 @@ class Trainer:
 
     def __init__(self, net: synth.NetConfig, weights: Dict[str, np.ndarray],
                  chest: Optional[Dict[str, np.ndarray]] = None, lr: float = 1e-3, gamma: float = 1.0,
-                 beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+                 beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, precision: str = "fp32"):
         import torch
         self.torch = torch
+        if net.var_io:
+            raise NotImplementedError("training of Var-IO heads is not supported")
+        self.precision = precision
+        _Ops(None, precision)  # validates the precision
         self.net = net
         self.lr, self.gamma, self.beta1, self.beta2, self.eps = lr, gamma, beta1, beta2, eps
         chest = synth.make_chest_weights(net) if chest is None else chest
@@ -225,7 +236,7 @@ class Trainer:
         words, forward pass with saved activations, losses, reverse pass, and
         with `adam` the update (step size read from ``self.lr_t_dev``)."""
         net = self.net
-        ops = _Ops(st)
+        ops = _Ops(st, self.precision)
         lib = ops.lib
         n, U, S = batch.n, batch.U, batch.S
         C, F, R, K, B = net.channels, net.in_features, net.res_blocks, net.iterations, net.num_rx_ant
@@ -351,6 +362,7 @@ class Trainer:
     def _read_loss(self) -> Dict[str, List[float]]:
         K = self.net.iterations
         ld = self.loss_dev.cpu().numpy()
+        self._ok(load().nrx_train_check(nrx._stream_ptr(None)), "nrx_train_check")
         bce = [float(v) for v in ld[:K]]
         mse = [float(v) / self.gamma for v in ld[K:]] if self.gamma > 0 else [0.0] * K
         return {"bce": bce, "mse": mse, "loss": float(sum(bce) + self.gamma * sum(mse))}
@@ -460,7 +472,7 @@ def _make_batch(args):
 
 def fit(workload: synth.Workload, seconds: float, lr: float = 2e-3, lr_final: float = 5e-5, gamma: float = 1.0,
         seed: int = 1, resume: Optional[str] = None, workers: Optional[int] = None, log_every: int = 2000,
-        trainer: Optional[Trainer] = None) -> Trainer:
+        trainer: Optional[Trainer] = None, precision: str = "fp32") -> Trainer:
     """Train for a wall-clock budget on fresh random batches of ``workload``
     (random MCS association and SNR offsets, Sec. IV-A), with an exponential
     learning-rate decay from lr to lr_final over the budget.  Batches are
@@ -477,7 +489,7 @@ def fit(workload: synth.Workload, seconds: float, lr: float = 2e-3, lr_final: fl
         for k in ("ro2.w", "ro2.b"):
             W[k][...] = 0.0
         Wc["chest.2.w"][...] = 0.0
-        trainer = Trainer(net, W, Wc, lr=lr, gamma=gamma)
+        trainer = Trainer(net, W, Wc, lr=lr, gamma=gamma, precision=precision)
     if resume:
         trainer.restore(resume)
     nw = workers or max(2, min(14, (os.cpu_count() or 4) - 2))
@@ -517,6 +529,7 @@ def main(argv=None):
     ap.add_argument("--lr-final", type=float, default=5e-5)
     ap.add_argument("--gamma", type=float, default=1.0)
     ap.add_argument("--resume", default=None)
+    ap.add_argument("--precision", default="fp32", choices=("fp32", "bf16"), help="GEMM compute of the passes")
     ap.add_argument("--checkpoint", default=None, help="write an .npz checkpoint here")
     ap.add_argument("--out", required=True, help="write the inference weight blob here")
     a = ap.parse_args(argv)
@@ -524,7 +537,7 @@ def main(argv=None):
     snr = tuple(float(v) for v in a.snr.split(",")) if a.snr else base.snr_db_range
     wl = dataclasses_replace(base, num_prb=a.prb, batch=a.batch, snr_db_range=snr,
                              mcs_choices=tuple(int(v) for v in a.mcs.split(",")))
-    tr = fit(wl, a.seconds, lr=a.lr, lr_final=a.lr_final, gamma=a.gamma, resume=a.resume)
+    tr = fit(wl, a.seconds, lr=a.lr, lr_final=a.lr_final, gamma=a.gamma, resume=a.resume, precision=a.precision)
     if a.checkpoint:
         tr.save(a.checkpoint)
     with open(a.out, "wb") as f:
