@@ -146,6 +146,49 @@ nrx_status nrx_train_bce(int32_t n_slots, const nrx_slot_cfg* cfg, int32_t m_max
 nrx_status nrx_train_mse(int64_t n, const float* h_hat, const float* h, float scale, float* grad, double* loss,
                          void* stream);
 
+/*
+ * GPU link simulator for training data (system model, Eq. 1): per slot the
+ * users' bits -> Gray QAM (TS 38.211 Sec. 5.1), QPSK DMRS on the type-1 comb
+ * with the frequency OCC (DMRS symbols carry no data), a tapped delay line per
+ * user (L taps at l 4 DS/(L-1), exponential power-delay profile normalised to
+ * one; a Clarke sum of 16 sinusoids per tap for Doppler > 0, CN(0, 1) static
+ * gains otherwise; a half-wavelength ULA with one arrival angle in
+ * [-60, 60] degrees per tap, or independent gains per antenna), AWGN of
+ * variance noise_var.  Subcarrier s sits at (s - S/2) 30 kHz, symbol t at
+ * t 0.5 ms / 14.
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = (seed low,
+ * seed high), counter = (index low, index high, batch, stream); stream 1 bits
+ * (index (slot U + u) n_data + re, bit j of word 0), 2 DMRS (index
+ * (slot n_dmrs + d) S/2 + m, bits 0 and 1 of word 0 are the QPSK signs of Re
+ * and Im), 3 noise (index ((slot B + b) 14 + t) S + s, Box-Muller of words 0
+ * and 1), 4-8 tap gains (index ((slot U + u) L + l) Bd + bd, Bd = 1 for a ULA
+ * else B; stream 4 word 0 the arrival rotation, or words 0 and 1 a Box-Muller
+ * static gain; streams 5-8 words 0-3 the 16 sinusoid phases), 9 arrival
+ * angles (index (slot U + u) L + l).  Uniform u(x) = (x >> 8) 2^-24;
+ * Box-Muller u1 = ((x0 >> 8) + 1) 2^-24, u2 = u(x1).
+ * Outputs, in the layouts of nrx_train_features / nrx_train_bce /
+ * nrx_train_mse: y complex64 [n][B][14][S], dmrs complex64 [n][n_dmrs][S/2],
+ * bits uint8 [n][U][n_data][m_max] (zero beyond m_u), bits_per_symbol_dev
+ * int32 [n][U], h float32 [n][U][14][S][2B] (the true channel).
+ * scratch: device memory of nrx_train_sim_scratch_bytes(n, U, B, max taps).
+ * 1 <= n <= 64, 1 <= U <= 4, 1 <= B <= 8, 1 <= num_prb <= 275, taps 1..32.
+ */
+typedef struct {
+  float noise_var;           /* N0 (unit average symbol energy and channel power) */
+  float delay_spread_s;      /* DS > 0 */
+  float doppler_hz;          /* maximum Doppler, >= 0 (0: static channel) */
+  int32_t num_taps;          /* L, 1..32 */
+  int32_t ula;               /* 1: half-wavelength ULA, 0: independent antennas */
+  int32_t bits_per_symbol[4];
+} nrx_sim_slot;
+
+size_t nrx_train_sim_scratch_bytes(int32_t n_slots, int32_t num_users, int32_t num_rx_ant, int32_t max_taps);
+
+nrx_status nrx_train_simulate(int32_t n_slots, const nrx_sim_slot* slots, int32_t num_users, int32_t num_rx_ant,
+                              int32_t num_prb, int32_t num_dmrs_symbols, const int32_t* dmrs_symbols, int32_t m_max,
+                              uint64_t seed, uint32_t batch, void* scratch, void* y, void* dmrs, uint8_t* bits,
+                              int32_t* bits_per_symbol_dev, float* h, void* stream);
+
 /* Asynchronous zero fill of `bytes` bytes at ptr (gradient and loss reset). */
 nrx_status nrx_train_zero(int64_t bytes, void* ptr, void* stream);
 

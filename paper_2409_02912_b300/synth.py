@@ -580,3 +580,168 @@ def dmrs_gold(num_prb: int, dmrs_symbols: Sequence[int], slot_number: int, n_id:
         c = gold_sequence(dmrs_c_init(slot_number, l, n_id, n_scid), 2 * M).astype(np.float64)
         out[d] = ((1.0 - 2.0 * c[0::2]) + 1j * (1.0 - 2.0 * c[1::2])) / np.sqrt(2.0)
     return out
+
+
+# ----------------------------------------------------------------------------
+# Counter-based link simulator (the reference of the GPU simulator)
+# ----------------------------------------------------------------------------
+# The GPU training simulator draws every random number from the Philox4x32-10
+# counter-based generator (Salmon et al., SC'11), so that this numpy
+# restatement of the same link, from the same counters, reproduces its batches:
+# key = (seed low word, seed high word), counter = (index low word, index high
+# word, batch, stream).  Streams and indices:
+#   1 bits     index ((slot U + u) n_data + re): bit j of word 0 is bit j of the RE
+#   2 DMRS     index ((slot n_dmrs + d) S/2 + m): bits 0 / 1 of word 0 are the
+#              QPSK signs of Re / Im
+#   3 noise    index ((slot B + b) 14 + t) S + s: Box-Muller of words 0 and 1
+#   4..8       channel gains, index ((slot U + u) L + l) Bd + bd (Bd = 1 for a
+#              ULA, else B): stream 4 word 0 = arrival rotation theta (or, for
+#              a static channel, words 0/1 = a Box-Muller CN(0,1) gain),
+#              streams 5..8 words 0..3 = the 16 sinusoid phases
+#   9 AoA      index ((slot U + u) L + l): word 0
+# Uniform u(x) = (x >> 8) 2^-24; Box-Muller uses u1 = ((x0 >> 8) + 1) 2^-24 and
+# u2 = u(x1): (re, im) = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
+
+PHILOX_M = (0xD2511F53, 0xCD9E8D57)
+PHILOX_W = (0x9E3779B9, 0xBB67AE85)
+SIM_STREAM_BITS, SIM_STREAM_DMRS, SIM_STREAM_NOISE, SIM_STREAM_GAIN, SIM_STREAM_AOA = 1, 2, 3, 4, 9
+SIM_SINUSOIDS = 16
+SIM_MAX_TAPS = 32
+
+
+def philox4x32(ctr, key, rounds: int = 10) -> np.ndarray:
+    """Philox4x32-R: ctr uint [..., 4], key uint [..., 2] -> uint32 [..., 4]."""
+    c = [np.asarray(ctr[..., i], dtype=np.uint64) & 0xFFFFFFFF for i in range(4)]
+    k0 = np.asarray(key[..., 0], dtype=np.uint64) & 0xFFFFFFFF
+    k1 = np.asarray(key[..., 1], dtype=np.uint64) & 0xFFFFFFFF
+    for r in range(rounds):
+        if r > 0:
+            k0 = (k0 + PHILOX_W[0]) & 0xFFFFFFFF
+            k1 = (k1 + PHILOX_W[1]) & 0xFFFFFFFF
+        p0 = np.uint64(PHILOX_M[0]) * c[0]
+        p1 = np.uint64(PHILOX_M[1]) * c[2]
+        c = [(p1 >> np.uint64(32)) ^ c[1] ^ k0, p1 & 0xFFFFFFFF, (p0 >> np.uint64(32)) ^ c[3] ^ k1,
+             p0 & 0xFFFFFFFF]
+    return np.stack(c, axis=-1).astype(np.uint32)
+
+
+def _philox_draw(index, seed: int, batch: int, stream: int) -> np.ndarray:
+    index = np.asarray(index, dtype=np.uint64)
+    ctr = np.stack([index & 0xFFFFFFFF, index >> np.uint64(32), np.full_like(index, batch),
+                    np.full_like(index, stream)], axis=-1)
+    key = np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], dtype=np.uint64)
+    return philox4x32(ctr, np.broadcast_to(key, ctr.shape[:-1] + (2,)))
+
+
+def _uniform(x) -> np.ndarray:
+    return (np.asarray(x, dtype=np.uint64) >> np.uint64(8)).astype(np.float64) * 2.0 ** -24
+
+
+def _box_muller(x0, x1):
+    u1 = ((np.asarray(x0, dtype=np.uint64) >> np.uint64(8)).astype(np.float64) + 1.0) * 2.0 ** -24
+    r = np.sqrt(-2.0 * np.log(u1))
+    a = 2.0 * np.pi * _uniform(x1)
+    return r * np.cos(a), r * np.sin(a)
+
+
+@dataclasses.dataclass(frozen=True)
+class SimSlot:
+    """Per-slot parameters of the counter-based simulator."""
+
+    noise_var: float
+    delay_spread_s: float
+    doppler_hz: float
+    num_taps: int
+    ula: bool
+    bits_per_symbol: tuple
+
+
+def sim_slot_params(w: Workload, rng: np.random.Generator) -> SimSlot:
+    """Training-sample parameters as ``training_slot`` draws them (random MCS
+    association, SNR with the offsets of Sec. IV-A, delay spread, Doppler)."""
+    c = draw_slot_config(w, rng)
+    snr = c.snr_db + snr_offset_db(c.bits_per_symbol)
+    return SimSlot(noise_var=float(np.float32(10.0 ** (-snr / 10.0))), delay_spread_s=float(np.float32(c.delay_spread_s)),
+                   doppler_hz=float(np.float32(c.doppler_hz)), num_taps=w.num_taps, ula=w.ula,
+                   bits_per_symbol=c.bits_per_symbol)
+
+
+def simulate_philox(slots: Sequence[SimSlot], num_users: int, num_rx_ant: int, num_prb: int,
+                    dmrs_symbols: Sequence[int], m_max: int, seed: int, batch: int) -> TrainingBatch:
+    """The link of ``make_slot`` (Eq. 1) with every draw from Philox (see
+    above): bits -> Gray QAM, QPSK DMRS on the type-1 comb with OCC, TDL
+    channel with the Clarke sum of sinusoids (or CN(0,1) static gains), ULA
+    steering, AWGN.  float64 arithmetic; returns a ``TrainingBatch``."""
+    n, U, B, S = len(slots), num_users, num_rx_ant, 12 * num_prb
+    ds = tuple(dmrs_symbols)
+    nd = len(ds)
+    data = [t for t in range(NUM_SYMBOLS) if t not in ds]
+    n_data = len(data) * S
+    # DMRS
+    idx = np.arange(n * nd * (S // 2))
+    w = _philox_draw(idx, seed, batch, SIM_STREAM_DMRS)[:, 0].astype(np.int64)
+    dm = (((1 - 2 * (w & 1)) + 1j * (1 - 2 * ((w >> 1) & 1))) / np.sqrt(2.0)).reshape(n, nd, S // 2)
+    # bits
+    bits = np.zeros((n, U, n_data, m_max), dtype=np.uint8)
+    m_u = np.array([[s.bits_per_symbol[u] for u in range(U)] for s in slots], dtype=np.int32)
+    wb = _philox_draw(np.arange(n * U * n_data), seed, batch, SIM_STREAM_BITS)[:, 0].reshape(n, U, n_data)
+    for j in range(m_max):
+        bits[..., j] = (wb >> j) & 1
+    for i in range(n):
+        for u in range(U):
+            bits[i, u, :, m_u[i, u]:] = 0
+    # transmitted grids
+    x = np.zeros((n, U, NUM_SYMBOLS, S), dtype=np.complex128)
+    for i in range(n):
+        for u in range(U):
+            m = int(m_u[i, u])
+            sym = qam_modulate(bits[i, u, :, :m], m).reshape(len(data), S)
+            for k, t in enumerate(data):
+                x[i, u, t] = sym[k]
+            for d, t in enumerate(ds):
+                x[i, u, t, (u // 2)::2] = dmrs_port_values(dm[i, d], u)
+    # channel
+    t_n = np.arange(NUM_SYMBOLS) * (SLOT_DURATION_S / NUM_SYMBOLS)
+    f_s = (np.arange(S) - S / 2) * SUBCARRIER_SPACING_HZ
+    h = np.zeros((n, U, B, NUM_SYMBOLS, S), dtype=np.complex128)
+    for i, sp in enumerate(slots):
+        L = sp.num_taps
+        DS = sp.delay_spread_s
+        tau = np.arange(L) * (4.0 * DS / max(L - 1, 1))
+        pdp = np.exp(-tau / DS)
+        pdp /= pdp.sum()
+        Bd = 1 if sp.ula else B
+        for u in range(U):
+            gidx = ((i * U + u) * L + np.arange(L))[:, None] * Bd + np.arange(Bd)[None, :]  # [L, Bd]
+            w4 = _philox_draw(gidx, seed, batch, SIM_STREAM_GAIN)
+            if sp.doppler_hz == 0.0:
+                gr, gi = _box_muller(w4[..., 0], w4[..., 1])
+                a = np.repeat(((gr + 1j * gi) / np.sqrt(2.0))[:, :, None], NUM_SYMBOLS, axis=2)
+            else:
+                theta = (2.0 * _uniform(w4[..., 0]) - 1.0) * np.pi  # [L, Bd]
+                phi = np.concatenate([2.0 * np.pi * _uniform(_philox_draw(gidx, seed, batch, SIM_STREAM_GAIN + 1 + k))
+                                      for k in range(4)], axis=-1)  # [L, Bd, 16]
+                mm = np.arange(1, SIM_SINUSOIDS + 1)
+                alpha = (2.0 * np.pi * mm - np.pi + theta[..., None]) / SIM_SINUSOIDS
+                ph = 2.0 * np.pi * sp.doppler_hz * np.cos(alpha)[..., None] * t_n + phi[..., None]
+                a = np.exp(1j * ph).sum(axis=2) / np.sqrt(SIM_SINUSOIDS)  # [L, Bd, T]
+            a = a * np.sqrt(pdp)[:, None, None]
+            if sp.ula:
+                wa = _philox_draw((i * U + u) * L + np.arange(L), seed, batch, SIM_STREAM_AOA)[:, 0]
+                aoa = (2.0 * _uniform(wa) - 1.0) * (np.pi / 3.0)
+                steer = np.exp(1j * np.pi * np.arange(B)[None, :] * np.sin(aoa)[:, None])  # [L, B]
+                a = a[:, 0:1, :] * steer[:, :, None]
+            phase = np.exp(-2j * np.pi * f_s[None, :] * tau[:, None])  # [L, S]
+            h[i, u] = np.einsum("lbt,ls->bts", a, phase)
+    # received grid
+    nidx = np.arange(n * B * NUM_SYMBOLS * S)
+    wn = _philox_draw(nidx, seed, batch, SIM_STREAM_NOISE)
+    nr, ni = _box_muller(wn[:, 0], wn[:, 1])
+    noise = (nr + 1j * ni).reshape(n, B, NUM_SYMBOLS, S)
+    n0 = np.array([s.noise_var for s in slots])
+    y = np.einsum("nubts,nuts->nbts", h, x) + np.sqrt(n0 / 2.0)[:, None, None, None] * noise
+    hr = np.zeros((n, U, NUM_SYMBOLS, S, 2 * B), dtype=np.float32)
+    hr[..., 0::2] = np.transpose(h, (0, 1, 3, 4, 2)).real
+    hr[..., 1::2] = np.transpose(h, (0, 1, 3, 4, 2)).imag
+    return TrainingBatch(y=y.astype(np.complex64), dmrs=dm.astype(np.complex64), bits=bits, m_u=m_u, h=hr,
+                         dmrs_symbols=ds, noise_var=n0)

@@ -28,8 +28,13 @@ from . import nrx, synth
 TRAIN_EXPORTED = (
     "nrx_train_features", "nrx_train_gemm", "nrx_train_gemm_bf16", "nrx_train_check", "nrx_train_colsum", "nrx_train_dw3", "nrx_train_dw3_wgrad",
     "nrx_train_relu_mask", "nrx_train_aggregate", "nrx_train_axpy", "nrx_train_bce", "nrx_train_mse",
-    "nrx_train_zero", "nrx_train_copy", "nrx_train_adam",
+    "nrx_train_zero", "nrx_train_copy", "nrx_train_adam", "nrx_train_sim_scratch_bytes", "nrx_train_simulate",
 )
+
+
+class nrx_sim_slot(ctypes.Structure):
+    _fields_ = [("noise_var", ctypes.c_float), ("delay_spread_s", ctypes.c_float), ("doppler_hz", ctypes.c_float),
+                ("num_taps", ctypes.c_int32), ("ula", ctypes.c_int32), ("bits_per_symbol", ctypes.c_int32 * 4)]
 
 _configured = False
 
@@ -58,11 +63,15 @@ def load():
         "nrx_train_zero": [I64, P, P],
         "nrx_train_copy": [I64, P, P, P],
         "nrx_train_adam": [I64, P, P, P, P, P, F32, F32, F32, P],
+        "nrx_train_simulate": [I32, ctypes.POINTER(nrx_sim_slot), I32, I32, I32, I32, P, I32, ctypes.c_uint64,
+                               ctypes.c_uint32, P, P, P, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    lib.nrx_train_sim_scratch_bytes.argtypes = [I32, I32, I32, I32]
+    lib.nrx_train_sim_scratch_bytes.restype = ctypes.c_size_t
     _configured = True
     return lib
 
@@ -385,31 +394,48 @@ class Trainer:
         self._enqueue(batch, nrx._stream_ptr(stream), adam=True)
         return self._read_loss()
 
-    def graph_step(self, tb: synth.TrainingBatch) -> Dict[str, List[float]]:
-        """``step`` through a CUDA graph of the whole launch sequence: the
-        batch is uploaded into fixed device buffers and the graph captured on
-        the first call (per batch shape) is replayed, so the host issues one
-        launch per step instead of a few hundred."""
+    def graph_step(self, tb) -> Dict[str, List[float]]:
+        """``step`` through a CUDA graph of the whole launch sequence, captured
+        on the first call (per batch shape) and replayed after, so the host
+        issues one launch per step instead of a few hundred.  ``tb`` is a host
+        ``synth.TrainingBatch`` (uploaded into fixed device buffers) or a
+        ``DeviceBatch`` filled in place (e.g. by ``GpuSimulator``), which must
+        then be the same object at every call."""
         torch = self.torch
+        if isinstance(tb, DeviceBatch):
+            if self._graph is None or self._static is not tb:
+                self._graph = None
+                self._static = tb
+                self._graph_shape = None
+                self.step(tb)
+                self._capture()
+                return self._read_loss()
+            self._advance()
+            self._graph.replay()
+            return self._read_loss()
         shape = (tb.y.shape, tb.m_u.shape, tb.bits.shape, tb.dmrs_symbols)
         if self._graph is None or self._graph_shape != shape:
             self._graph = None
             self._static = DeviceBatch(tb)
             self._graph_shape = shape
             self.step(self._static)  # eager step: the buffers exist before capture
-            g = torch.cuda.CUDAGraph()
-            side = torch.cuda.Stream()
-            side.wait_stream(torch.cuda.current_stream())
-            with torch.cuda.stream(side):
-                with torch.cuda.graph(g, stream=side):
-                    self._enqueue(self._static, side.cuda_stream, adam=True)
-            torch.cuda.current_stream().wait_stream(side)
-            self._graph = g
+            self._capture()
             return self._read_loss()
         self._static.load(tb)
         self._advance()
         self._graph.replay()
         return self._read_loss()
+
+    def _capture(self):
+        torch = self.torch
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                self._enqueue(self._static, side.cuda_stream, adam=True)
+        torch.cuda.current_stream().wait_stream(side)
+        self._graph = g
 
     @staticmethod
     def _ok(st, what):
@@ -438,6 +464,20 @@ class DeviceBatch:
                                   [self.dmrs[i].data_ptr() for i in range(self.n)], tb.noise_var)
         self._pinned = None
 
+    @classmethod
+    def empty(cls, n: int, num_users: int, num_rx_ant: int, num_prb: int, m_max: int, dmrs_symbols) -> "DeviceBatch":
+        """Device buffers of a batch shape, to be filled on the GPU."""
+        S = 12 * num_prb
+        nd = len(dmrs_symbols)
+        n_data = (14 - nd) * S
+        tb = synth.TrainingBatch(y=np.zeros((n, num_rx_ant, 14, S), np.complex64),
+                                 dmrs=np.ones((n, nd, S // 2), np.complex64),
+                                 bits=np.zeros((n, num_users, n_data, m_max), np.uint8),
+                                 m_u=np.full((n, num_users), 2, np.int32),
+                                 h=np.zeros((n, num_users, 14, S, 2 * num_rx_ant), np.float32),
+                                 dmrs_symbols=tuple(dmrs_symbols), noise_var=np.ones(n))
+        return cls(tb)
+
     def load(self, tb: synth.TrainingBatch, stream=None):
         """Upload a batch of the same shape into these buffers (through pinned
         staging, asynchronous on the stream; the staging is reused, so the
@@ -458,6 +498,49 @@ class DeviceBatch:
         self.dmrs_symbols = tb.dmrs_symbols
 
 
+class GpuSimulator:
+    """Training batches drawn on the GPU (``nrx_train_simulate``) into one
+    ``DeviceBatch``: per-slot parameters (random MCS association, SNR with
+    offsets, delay spread, Doppler) from ``synth.sim_slot_params`` on the host,
+    every per-RE draw from Philox on the device."""
+
+    def __init__(self, workload: synth.Workload, seed: int = 7, param_seed: int = 11):
+        import torch
+        w = workload
+        self.w = w
+        self.seed = seed
+        self.batch_index = 0
+        self.rng = np.random.Generator(np.random.PCG64(param_seed))
+        self.batch = DeviceBatch.empty(w.batch, w.num_users, w.num_rx_ant, w.num_prb, w.net.m_max, w.dmrs_symbols)
+        nbytes = load().nrx_train_sim_scratch_bytes(w.batch, w.num_users, w.num_rx_ant, synth.SIM_MAX_TAPS)
+        self.scratch = torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device="cuda")
+        self._ds = np.ascontiguousarray(np.asarray(w.dmrs_symbols, dtype=np.int32))
+
+    def draw(self, stream=None) -> DeviceBatch:
+        """Simulate the next batch into ``self.batch`` (asynchronous)."""
+        w = self.w
+        params = [synth.sim_slot_params(w, self.rng) for _ in range(w.batch)]
+        arr = (nrx_sim_slot * w.batch)()
+        for i, sp in enumerate(params):
+            arr[i].noise_var = sp.noise_var
+            arr[i].delay_spread_s = sp.delay_spread_s
+            arr[i].doppler_hz = sp.doppler_hz
+            arr[i].num_taps = sp.num_taps
+            arr[i].ula = int(sp.ula)
+            for u, m in enumerate(sp.bits_per_symbol):
+                arr[i].bits_per_symbol[u] = m
+        b = self.batch
+        st = load().nrx_train_simulate(w.batch, arr, w.num_users, w.num_rx_ant, w.num_prb, len(w.dmrs_symbols),
+                                       self._ds.ctypes.data, w.net.m_max, self.seed, self.batch_index,
+                                       self.scratch.data_ptr(), b.y.data_ptr(), b.dmrs.data_ptr(), b.bits.data_ptr(),
+                                       b.m_u.data_ptr(), b.h.data_ptr(), nrx._stream_ptr(stream))
+        if st != nrx.NRX_OK:
+            raise nrx.NrxError(st, "nrx_train_simulate")
+        self.batch_index += 1
+        self.last_params = params
+        return b
+
+
 # ----------------------------------------------------------------------------
 # Training driver
 # ----------------------------------------------------------------------------
@@ -472,7 +555,7 @@ def _make_batch(args):
 
 def fit(workload: synth.Workload, seconds: float, lr: float = 2e-3, lr_final: float = 5e-5, gamma: float = 1.0,
         seed: int = 1, resume: Optional[str] = None, workers: Optional[int] = None, log_every: int = 2000,
-        trainer: Optional[Trainer] = None, precision: str = "fp32") -> Trainer:
+        trainer: Optional[Trainer] = None, precision: str = "fp32", simulator: str = "cpu") -> Trainer:
     """Train for a wall-clock budget on fresh random batches of ``workload``
     (random MCS association and SNR offsets, Sec. IV-A), with an exponential
     learning-rate decay from lr to lr_final over the budget.  Batches are
@@ -492,6 +575,17 @@ def fit(workload: synth.Workload, seconds: float, lr: float = 2e-3, lr_final: fl
         trainer = Trainer(net, W, Wc, lr=lr, gamma=gamma, precision=precision)
     if resume:
         trainer.restore(resume)
+    if simulator == "gpu":  # every batch drawn on the device, no host workers
+        sim = GpuSimulator(workload, seed=seed * 1_000_003 + trainer.t)
+        t0 = time.time()
+        hist = []
+        while time.time() - t0 < seconds:
+            trainer.lr = lr * (lr_final / lr) ** min(1.0, (time.time() - t0) / seconds)
+            hist.append(trainer.graph_step(sim.draw())["loss"])
+            if log_every and len(hist) % log_every == 0:
+                print(f"step {trainer.t} {time.time() - t0:.0f}s lr {trainer.lr:.2e} "
+                      f"loss {np.mean(hist[-log_every:]):.4f}", flush=True)
+        return trainer
     nw = workers or max(2, min(14, (os.cpu_count() or 4) - 2))
     pool = mp.get_context("spawn").Pool(nw)
     try:
@@ -530,6 +624,8 @@ def main(argv=None):
     ap.add_argument("--gamma", type=float, default=1.0)
     ap.add_argument("--resume", default=None)
     ap.add_argument("--precision", default="fp32", choices=("fp32", "bf16"), help="GEMM compute of the passes")
+    ap.add_argument("--simulator", default="cpu", choices=("cpu", "gpu"),
+                    help="draw batches with CPU workers (synth) or on the GPU (nrx_train_simulate)")
     ap.add_argument("--checkpoint", default=None, help="write an .npz checkpoint here")
     ap.add_argument("--out", required=True, help="write the inference weight blob here")
     a = ap.parse_args(argv)
@@ -537,7 +633,8 @@ def main(argv=None):
     snr = tuple(float(v) for v in a.snr.split(",")) if a.snr else base.snr_db_range
     wl = dataclasses_replace(base, num_prb=a.prb, batch=a.batch, snr_db_range=snr,
                              mcs_choices=tuple(int(v) for v in a.mcs.split(",")))
-    tr = fit(wl, a.seconds, lr=a.lr, lr_final=a.lr_final, gamma=a.gamma, resume=a.resume, precision=a.precision)
+    tr = fit(wl, a.seconds, lr=a.lr, lr_final=a.lr_final, gamma=a.gamma, resume=a.resume, precision=a.precision,
+             simulator=a.simulator)
     if a.checkpoint:
         tr.save(a.checkpoint)
     with open(a.out, "wb") as f:

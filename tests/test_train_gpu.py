@@ -302,3 +302,61 @@ def test_bf16_training_reduces_the_loss():
         tr.graph_step(synth.training_batch([synth.training_slot(w, rng) for _ in range(8)], 4))
     after = tr.loss_and_grad(val)["bce"][-1]
     assert np.isfinite(after) and after < 0.75 * before, (before, after)
+
+
+# ----------------------------------------------------------------------------
+# GPU link simulator
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("ula,dmrs,U", [(True, (2, 11), 3), (False, (3,), 2), (True, (2,), 4)])
+def test_gpu_simulator_matches_counter_based_reference(ula, dmrs, U):
+    """The device simulator reproduces the numpy restatement from the same
+    Philox counters: bits, pilots and modulation orders exactly, the channel
+    and the received grid to FP32 accuracy."""
+    w = synth.Workload(name="simcheck", seed_base=0, batch=4, num_prb=5, num_users=U, num_rx_ant=4,
+                       dmrs_symbols=dmrs, mcs_choices=(2, 4, 6), snr_db_range=(0.0, 20.0), num_taps=9,
+                       delay_spread_range_s=(30e-9, 300e-9), doppler_range_hz=(0.0, 400.0), ula=ula,
+                       net=synth.NetConfig(num_rx_ant=4, channels=8, res_blocks=1, iterations=1, m_max=6))
+    sim = train.GpuSimulator(w, seed=1234567890123, param_seed=4)
+    sim.draw()
+    b = sim.draw()  # second batch: batch index 1
+    params = list(sim.last_params)
+    params[0] = synth.dataclasses.replace(params[0], doppler_hz=0.0)  # keep a static slot in the check
+    sim.batch_index = 1
+    import ctypes
+    arr = (train.nrx_sim_slot * len(params))()
+    for i, sp in enumerate(params):
+        arr[i].noise_var, arr[i].delay_spread_s, arr[i].doppler_hz = sp.noise_var, sp.delay_spread_s, sp.doppler_hz
+        arr[i].num_taps, arr[i].ula = sp.num_taps, int(sp.ula)
+        for u, m in enumerate(sp.bits_per_symbol):
+            arr[i].bits_per_symbol[u] = m
+    ds = np.asarray(dmrs, dtype=np.int32)
+    st = train.load().nrx_train_simulate(len(params), arr, U, 4, 5, len(dmrs), ds.ctypes.data, 6, sim.seed, 1,
+                                         sim.scratch.data_ptr(), b.y.data_ptr(), b.dmrs.data_ptr(), b.bits.data_ptr(),
+                                         b.m_u.data_ptr(), b.h.data_ptr(), None)
+    assert st == nrx.NRX_OK
+    torch.cuda.synchronize()
+    ref = synth.simulate_philox(params, U, 4, 5, dmrs, 6, seed=sim.seed, batch=1)
+    assert np.array_equal(b.bits.cpu().numpy(), ref.bits)
+    assert np.array_equal(b.m_u.cpu().numpy(), ref.m_u)
+    assert np.array_equal(b.dmrs.cpu().numpy(), ref.dmrs)
+    h = b.h.cpu().numpy()
+    assert np.max(np.abs(h - ref.h)) < 1e-4 * max(1.0, np.max(np.abs(ref.h)))
+    y = b.y.cpu().numpy()
+    assert np.max(np.abs(y - ref.y)) < 1e-4 * max(1.0, np.max(np.abs(ref.y)))
+
+
+def test_training_on_the_gpu_simulator_reduces_the_loss():
+    w = synth.Workload(name="train_gpu_sim", seed_base=54, batch=8, num_prb=4, num_users=2, num_rx_ant=4,
+                       dmrs_symbols=(2, 11), mcs_choices=(2, 4), snr_db_range=(5.0, 15.0), num_taps=8,
+                       delay_spread_range_s=(30e-9, 200e-9), doppler_range_hz=(0.0, 200.0), ula=True,
+                       net=synth.NetConfig(num_rx_ant=4, channels=32, res_blocks=1, iterations=2, m_max=4))
+    tr = train.Trainer(w.net, synth.make_weights(w.net, seed=1), lr=2e-3, gamma=0.5)
+    val_sim = train.GpuSimulator(w, seed=99, param_seed=98)
+    val = val_sim.draw()
+    before = tr.loss_and_grad(val)["bce"][-1]
+    sim = train.GpuSimulator(w, seed=5, param_seed=6)
+    for _ in range(300):
+        tr.graph_step(sim.draw())
+    after = tr.loss_and_grad(val)["bce"][-1]
+    assert np.isfinite(after) and after < 0.75 * before, (before, after)
