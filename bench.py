@@ -330,8 +330,11 @@ def run_ours(args, rank, world, local):
             for _ in range(3):
                 f()
             ts = timed(f, max(5, args.steps // 2))
+            l1 = timed(lambda: rx2.nrx_detect_batch(y1, d1, w.dmrs_symbols, b1, out=llr, stream=stream), 30)
             cmp[f"nrx_{other}"] = {"value": res_step / (1e-3 * statistics.mean(ts)), "unit": UNIT,
-                                   "ms_per_step": statistics.mean(ts)}
+                                   "ms_per_step": statistics.mean(ts),
+                                   "slot_batch1_p50_us": 1e3 * float(np.percentile(l1, 50)),
+                                   "slot_batch1_p99_us": 1e3 * float(np.percentile(l1, 99))}
             rx2.close()
         # Var-IO heads (Sec. III) on the same slots: same active weights, same work
         import dataclasses
@@ -349,8 +352,11 @@ def run_ours(args, rank, world, local):
         for _ in range(3):
             f()
         ts = timed(f, max(5, args.steps // 2))
+        l1 = timed(lambda: rx.lmmse_detect_batch(y1, d1, w.dmrs_symbols, b1, nv[:1], out=llr, stream=stream), 30)
         cmp["lmmse_fp32"] = {"value": res_step / (1e-3 * statistics.mean(ts)), "unit": UNIT,
-                             "ms_per_step": statistics.mean(ts)}
+                             "ms_per_step": statistics.mean(ts),
+                             "slot_batch1_p50_us": 1e3 * float(np.percentile(l1, 50)),
+                             "slot_batch1_p99_us": 1e3 * float(np.percentile(l1, 99))}
         extras["compare"] = cmp
         # end to end through the host-buffer entry point
         y_h = torch.from_numpy(synth.stack_batch(slots)).pin_memory()
