@@ -74,6 +74,7 @@ struct nrx_server {
   std::condition_variable cv;
   std::deque<nrx_completion> done;
   std::atomic<bool> stop{false};
+  std::atomic<bool> abandon{false};  // stop without waiting for in-flight batches (drain timed out)
   std::atomic<int64_t> outstanding{0};
   std::vector<std::thread> workers;  // one per bucket
   nrx_server_stats stats{};
@@ -245,6 +246,7 @@ void worker_main(nrx_server* s, int bi) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
       const bool busy = b.lane[0].cur.active || b.lane[1].cur.active || b.queued > 0;
+      if (s->abandon.load()) break;
       if (!busy && b.inbox.empty()) {
         if (s->stop.load()) break;
         s->cv.wait_for(lk, std::chrono::microseconds(200));
@@ -448,7 +450,7 @@ nrx_status nrx_server_create(const void* weights, size_t weights_bytes, int32_t 
 
 void nrx_server_destroy(nrx_server* s) {
   if (!s) return;
-  nrx_server_drain(s, 10000);
+  if (nrx_server_drain(s, 10000) != NRX_OK) s->abandon.store(true);
   s->stop.store(true);
   s->cv.notify_all();
   for (std::thread& t : s->workers)
