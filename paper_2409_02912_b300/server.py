@@ -9,8 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
-import time
-from typing import Dict, List, Optional, Sequence
+from typing import Dict, List, Sequence
 
 import numpy as np
 

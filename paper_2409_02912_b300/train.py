@@ -19,7 +19,7 @@ from __future__ import annotations
 import ctypes
 import math
 import struct
-from typing import Dict, List, Optional, Sequence
+from typing import Dict, List, Optional
 
 import numpy as np
 

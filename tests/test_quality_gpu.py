@@ -3,7 +3,6 @@ comparison at 10% BLER) on coded synthetic slots: the trained NRX against the
 untrained one and LS+LMMSE on the same slots, and the reduced-precision modes
 against FP32.  The paper's own curves are not reproducible (its data and
 weights are absent), so the comparison is against this build's LMMSE."""
-import numpy as np
 import pytest
 
 from paper_2409_02912_b300 import evaluate, synth
