@@ -55,9 +55,11 @@ def sweep_batches(sw: Sweep):
 
 
 def compare(blob: bytes, precisions: Sequence[str] = ("fp32", "bf16", "fp16", "fp8"), sw: Sweep = Sweep(),
-            batches=None, untrained_blob: Optional[bytes] = None) -> Dict[str, dict]:
+            batches=None, untrained_blob: Optional[bytes] = None, early_exit: bool = True) -> Dict[str, dict]:
     """BLER curves and SNR at 10% BLER of the NRX (each precision) and of
-    LS+LMMSE on the same coded slots."""
+    LS+LMMSE on the same coded slots; with ``early_exit`` also the FP32 NRX
+    stopped after each number of CGNN iterations below N_it (the multi-loss
+    read-outs, Sec. II-B and Sec. IV-B)."""
     import torch
     batches = sweep_batches(sw) if batches is None else batches
     n = sw.slots_per_point
@@ -84,6 +86,10 @@ def compare(blob: bytes, precisions: Sequence[str] = ("fp32", "bf16", "fp16", "f
         run(f"nrx_{p}", rx, nrx_fn)
         if p == precisions[0]:
             run("lmmse", rx, lmmse_fn)
+        if early_exit and p == "fp32":
+            for its in range(1, rx.iterations):
+                run(f"nrx_fp32_it{its}", rx,
+                    lambda r, b, y, dm, its=its: r.nrx_detect_batch(y, dm, sw.dmrs_symbols, b.bits, iterations=its))
         rx.close()
     if untrained_blob is not None:
         rx = nrx.Receiver(untrained_blob, sw.num_rx_ant, sw.num_users, sw.num_prb, max_slots=n, precision="fp32")

@@ -43,3 +43,46 @@ def test_bf16_and_fp16_within_0p2_db_of_fp32(quality):
     for p in ("bf16", "fp16"):
         assert abs(quality[f"nrx_{p}"]["snr_at_10pct"] - ref) <= 0.2, p
     assert quality["nrx_fp8"]["snr_at_10pct"] is not None  # reported, not gated
+
+
+def test_fp32_blocks_decode_like_the_fp64_oracle():
+    """The FP32 GPU receiver stands in for the FP64 oracle NRX at matched BLER:
+    on the 8 dB point of the sweep (first 8 slots) the LLRs of both decode to
+    the same block-error pattern (at most one block differs)."""
+    import numpy as np
+    from oracle import nrx_oracle as O
+    from paper_2409_02912_b300 import bler, nrx
+    sw = evaluate.Sweep(snrs=(8.0,), slots_per_point=8)
+    batch = evaluate.sweep_batches(sw)[0]
+    with open(evaluate.TRAINED_MU2, "rb") as f:
+        blob = f.read()
+    net = synth.WORKLOADS["mu2_4rx_24prb"].net
+    W = {}
+    o = 0
+    payload = np.frombuffer(blob[32:], dtype=np.float32)
+    for name, shape in synth.weight_layout(net):
+        k = int(np.prod(shape))
+        W[name] = payload[o:o + k].reshape(shape).astype(np.float64)
+        o += k
+    ref = np.concatenate([O.nrx_forward(s.y, s.dmrs, 2, s.cfg.dmrs_symbols, s.cfg.bits_per_symbol, W,
+                                        net.iterations, net.res_blocks) for s in batch.slots]).astype(np.float32)
+    rx = nrx.Receiver(blob, 4, 2, 24, max_slots=8, precision="fp32")
+    y = torch.from_numpy(synth.stack_batch(batch.slots)).cuda()
+    dm = torch.from_numpy(np.stack([s.dmrs for s in batch.slots])).cuda()
+    gpu = rx.nrx_detect_batch(y, dm, (2, 11), batch.bits)
+    offs = torch.from_numpy(batch.offsets).cuda()
+    perm = torch.from_numpy(batch.perm).cuda()
+    dec_gpu = bler.conv_decode(gpu, offs, batch.n_info, perm).cpu().numpy()
+    dec_ref = bler.conv_decode(torch.from_numpy(ref).cuda(), offs, batch.n_info, perm).cpu().numpy()
+    err_gpu = (dec_gpu != batch.info).any(axis=1)
+    err_ref = (dec_ref != batch.info).any(axis=1)
+    assert err_ref.size > 50 and 0 < err_ref.sum() < err_ref.size
+    assert np.sum(err_gpu != err_ref) <= 1, (err_gpu.sum(), err_ref.sum())
+
+
+def test_early_exit_after_one_iteration_still_decodes(quality):
+    """Multi-loss training (Sec. II-B) makes the read-out after one CGNN
+    iteration usable (early exit, Sec. IV-B): it reaches 10% BLER, at most
+    2 dB after the full network."""
+    one, full = quality["nrx_fp32_it1"]["snr_at_10pct"], quality["nrx_fp32"]["snr_at_10pct"]
+    assert one is not None and full <= one + 0.05 and one <= full + 2.0, (one, full)
