@@ -189,6 +189,19 @@ nrx_status nrx_train_simulate(int32_t n_slots, const nrx_sim_slot* slots, int32_
                               uint64_t seed, uint32_t batch, void* scratch, void* y, void* dmrs, uint8_t* bits,
                               int32_t* bits_per_symbol_dev, float* h, void* stream);
 
+/*
+ * Var-IO head selection (Sec. III): activations [planes][rows_per_plane][*]
+ * (a plane is one (slot, user)); for the planes whose modulation order
+ * bits_per_symbol_dev[plane] equals m_head, dst[row][c] = src[row][c] (or +=
+ * with accumulate), c < width; other planes get dst = 0 (unchanged with
+ * accumulate).  Row strides ld_src, ld_dst >= width.  Used to assemble the
+ * per-user StateInit and read-out of the matching head in the forward pass
+ * and to route the gradient to that head in the reverse pass.
+ */
+nrx_status nrx_train_plane_mask(int64_t planes, int64_t rows_per_plane, int32_t width, int64_t ld_src, int64_t ld_dst,
+                                const int32_t* bits_per_symbol_dev, int32_t m_head, const float* src, float* dst,
+                                int32_t accumulate, void* stream);
+
 /* Asynchronous zero fill of `bytes` bytes at ptr (gradient and loss reset). */
 nrx_status nrx_train_zero(int64_t bytes, void* ptr, void* stream);
 

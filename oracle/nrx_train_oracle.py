@@ -20,6 +20,8 @@ What is computed, with the passage each part follows:
   added to the loss.
 * Multi-loss (Sec. II-B): both read-outs are applied after every CGNN
   iteration and the per-iteration losses are summed.
+* Var-IO (Sec. III): in a network with modulation-specific input and output
+  layers, each user runs the StateInit and ReadoutLLRs of its own order.
 * Normalisation (this build's reading): each BCE term is the mean over the
   counted bits of the whole batch, each MSE term the mean over (slot, user,
   antenna, RE) of |h_hat - h|^2 (the sum of the real and imaginary squared
@@ -85,13 +87,13 @@ def training_loss(slots, W: Dict[str, np.ndarray], Wc: Dict[str, np.ndarray], it
     for sl in slots:
         U = sl.cfg.num_users
         ds = sl.cfg.dmrs_symbols
-        states = O.nrx_states(sl.y, sl.dmrs, U, ds, W, n_it, res_blocks)
+        states = O.nrx_states(sl.y, sl.dmrs, U, ds, W, n_it, res_blocks, sl.cfg.bits_per_symbol)
         for u in range(U):
             m = sl.cfg.bits_per_symbol[u]
             target = channel_target(sl.h[u])
             for k in range(n_it):
                 S_u = states[k + 1][u]
-                v, cnt = bce_terms(O.readout(S_u, W), sl.bits[u], m, ds)
+                v, cnt = bce_terms(O.readout(S_u, O.head_weights(W, m)), sl.bits[u], m, ds)
                 bce_sum[k] += v
                 mse_sum[k] += float(np.sum((readout_chest(S_u, Wc) - target) ** 2))
             n_bits += cnt
@@ -106,9 +108,16 @@ def training_loss(slots, W: Dict[str, np.ndarray], Wc: Dict[str, np.ndarray], it
 # ----------------------------------------------------------------------------
 
 
+_HEAD_NAMES = {"init.pw.w": "init.m{m}.pw.w", "init.pw.b": "init.m{m}.pw.b", "init.dw": "init.m{m}.dw",
+               "ro1.w": "ro.m{m}.1.w", "ro1.b": "ro.m{m}.1.b", "ro2.w": "ro.m{m}.2.w", "ro2.b": "ro.m{m}.2.b"}
+
+
 def _torch_loss(slots, Wt, Wct, iterations: int, res_blocks: int, gamma: float):
     import torch
     F = torch.nn.functional
+
+    def hw(name, m):  # Var-IO (Sec. III): the modulation-specific input / output layers of order m
+        return Wt[_HEAD_NAMES[name].format(m=m)] if "init.pw.w" not in Wt else Wt[name]
 
     def dw(x, k):  # x [U, 14, S, C]; cross-correlation with zero padding
         C = x.shape[-1]
@@ -126,7 +135,9 @@ def _torch_loss(slots, Wt, Wct, iterations: int, res_blocks: int, gamma: float):
         pes = [O.positional_encoding(u, S, ds) for u in range(U)]
         x = torch.stack([torch.from_numpy(O.input_features(sl.y, H[u], pes[u])) for u in range(U)])
         pe = torch.stack([torch.from_numpy(p) for p in pes])
-        st = F.relu(dw(F.linear(x, Wt["init.pw.w"], Wt["init.pw.b"]), Wt["init.dw"]))
+        bits_u = sl.cfg.bits_per_symbol
+        st = torch.cat([F.relu(dw(F.linear(x[u:u + 1], hw("init.pw.w", bits_u[u]), hw("init.pw.b", bits_u[u])),
+                                  hw("init.dw", bits_u[u]))) for u in range(U)])
         data = [t for t in range(14) if t not in ds]
         for k in range(iterations):
             p = f"it{k}."
@@ -138,12 +149,13 @@ def _torch_loss(slots, Wt, Wct, iterations: int, res_blocks: int, gamma: float):
                 hh = F.relu(F.linear(dw(z, Wt[q + "dw1"]), Wt[q + "pw1.w"], Wt[q + "pw1.b"]))
                 z = z + F.linear(F.relu(dw(hh, Wt[q + "dw2"])), Wt[q + "pw2.w"], Wt[q + "pw2.b"])
             st = st + z
-            l = F.linear(F.relu(F.linear(st, Wt["ro1.w"], Wt["ro1.b"])), Wt["ro2.w"], Wt["ro2.b"])
+            ls = [F.linear(F.relu(F.linear(st[u], hw("ro1.w", bits_u[u]), hw("ro1.b", bits_u[u]))),
+                           hw("ro2.w", bits_u[u]), hw("ro2.b", bits_u[u])) for u in range(U)]
             hh = F.linear(F.relu(F.linear(st, Wct["chest.1.w"], Wct["chest.1.b"])), Wct["chest.2.w"],
                           Wct["chest.2.b"])
             for u in range(U):
                 m = sl.cfg.bits_per_symbol[u]
-                lu = l[u][data][:, :, :m].reshape(-1, m)
+                lu = ls[u][data][:, :, :m].reshape(-1, m)
                 bu = torch.from_numpy(np.asarray(sl.bits[u], dtype=np.float64)[:, :m])
                 total_bce[k] = total_bce[k] + (F.softplus(lu) - bu * lu).sum()
                 tgt = torch.from_numpy(channel_target(sl.h[u]))

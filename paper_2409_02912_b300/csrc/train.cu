@@ -320,6 +320,28 @@ __global__ void k_mse(size_t n, const float* __restrict__ h_hat, const float* __
   if ((threadIdx.x & 31) == 0) atomicAdd(loss, part);
 }
 
+// Var-IO plane selection: rows of the planes (slot, user) whose modulation
+// order is m_head take src (first `width` columns), other planes 0 (or stay
+// unchanged with accumulate).
+__global__ void k_plane_mask(long long planes, long long rows_per_plane, int width, long long ld_src,
+                             long long ld_dst, const int32_t* __restrict__ m_u, int m_head,
+                             const float* __restrict__ src, float* __restrict__ dst, int accumulate) {
+  const long long total = planes * rows_per_plane * width;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % width);
+    const long long row = i / width;
+    const bool sel = m_u[row / rows_per_plane] == m_head;
+    const float v = sel ? src[row * ld_src + c] : 0.f;
+    float* d = dst + row * ld_dst + c;
+    if (accumulate) {
+      if (sel) *d += v;
+    } else {
+      *d = v;
+    }
+  }
+}
+
 // Adam on FP32 master weights (bias-corrected step sizes passed in).
 __global__ void k_adam(size_t n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m1,
                        float* __restrict__ m2, const float* __restrict__ lr_t_dev, float b1, float b2, float eps) {
@@ -463,6 +485,18 @@ nrx_status nrx_train_mse(int64_t n, const float* h_hat, const float* h, float sc
   if (n < 1 || !h_hat || !h || !grad || !loss) return NRX_EINVAL;
   k_mse<<<blocks_for((size_t)n), kThreads, 0, static_cast<cudaStream_t>(stream)>>>((size_t)n, h_hat, h, scale, grad,
                                                                                   loss);
+  return to_status(cudaGetLastError());
+}
+
+nrx_status nrx_train_plane_mask(int64_t planes, int64_t rows_per_plane, int32_t width, int64_t ld_src, int64_t ld_dst,
+                                const int32_t* bits_per_symbol_dev, int32_t m_head, const float* src, float* dst,
+                                int32_t accumulate, void* stream) {
+  if (planes < 1 || rows_per_plane < 1 || width < 1 || ld_src < width || ld_dst < width || !bits_per_symbol_dev ||
+      !src || !dst)
+    return NRX_EINVAL;
+  const size_t n = (size_t)planes * rows_per_plane * width;
+  k_plane_mask<<<blocks_for(n), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      planes, rows_per_plane, width, ld_src, ld_dst, bits_per_symbol_dev, m_head, src, dst, accumulate ? 1 : 0);
   return to_status(cudaGetLastError());
 }
 

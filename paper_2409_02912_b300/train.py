@@ -29,6 +29,7 @@ TRAIN_EXPORTED = (
     "nrx_train_features", "nrx_train_gemm", "nrx_train_gemm_bf16", "nrx_train_check", "nrx_train_colsum", "nrx_train_dw3", "nrx_train_dw3_wgrad",
     "nrx_train_relu_mask", "nrx_train_aggregate", "nrx_train_axpy", "nrx_train_bce", "nrx_train_mse",
     "nrx_train_zero", "nrx_train_copy", "nrx_train_adam", "nrx_train_sim_scratch_bytes", "nrx_train_simulate",
+    "nrx_train_plane_mask",
 )
 
 
@@ -65,6 +66,7 @@ def load():
         "nrx_train_adam": [I64, P, P, P, P, P, F32, F32, F32, P],
         "nrx_train_simulate": [I32, ctypes.POINTER(nrx_sim_slot), I32, I32, I32, I32, P, I32, ctypes.c_uint64,
                                ctypes.c_uint32, P, P, P, P, P, P, P],
+        "nrx_train_plane_mask": [I64, I64, I32, I64, I64, P, I32, P, P, I32, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -123,6 +125,10 @@ class _Ops:
     def copy(self, nbytes, dst, src):
         self._ok(self.lib.nrx_train_copy(nbytes, dst, src, self.st), "nrx_train_copy")
 
+    def plane_mask(self, planes, rows, width, ld_src, ld_dst, m_u, m_head, src, dst, accumulate=False):
+        self._ok(self.lib.nrx_train_plane_mask(planes, rows, width, ld_src, ld_dst, m_u, m_head, src, dst,
+                                               int(accumulate), self.st), "nrx_train_plane_mask")
+
 
 class Trainer:
     """Training state of one network (FP32 master weights, gradients, Adam
@@ -139,8 +145,6 @@ class Trainer:
                  beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, precision: str = "fp32"):
         import torch
         self.torch = torch
-        if net.var_io:
-            raise NotImplementedError("training of Var-IO heads is not supported")
         self.precision = precision
         _Ops(None, precision)  # validates the precision
         self.net = net
@@ -211,8 +215,9 @@ class Trainer:
     def blob(self) -> bytes:
         """Inference weight blob (nrx.h layout) of the current weights."""
         net = self.net
-        hdr = struct.pack("<8i", synth.WEIGHT_MAGIC, synth.WEIGHT_VERSION, net.num_rx_ant, net.channels,
-                          net.res_blocks, net.iterations, net.m_max, self.n_blob)
+        hdr = struct.pack("<8i", synth.WEIGHT_MAGIC,
+                          synth.WEIGHT_VERSION_VAR_IO if net.var_io else synth.WEIGHT_VERSION, net.num_rx_ant,
+                          net.channels, net.res_blocks, net.iterations, net.m_max, self.n_blob)
         return hdr + self.w[:self.n_blob].cpu().numpy().tobytes()
 
     # -- buffers ------------------------------------------------------------
@@ -235,6 +240,11 @@ class Trainer:
              "c1": [e(C) for _ in range(K)], "hh": [e(2 * net.num_rx_ant) for _ in range(K)],
              "gS": e(C), "gz": e(C), "t1": e(C), "t2": e(C), "gl": e(net.m_max),
              "ghh": e(2 * net.num_rx_ant)}
+        if net.var_io:  # per-head StateInit and read-out activations (Sec. III)
+            H = net.heads
+            b.update({"P0h": [e(C) for _ in H], "S0h": [e(C) for _ in H],
+                      "r1h": [[e(C) for _ in H] for _ in range(K)], "lh": [[e(m) for m in H] for _ in range(K)],
+                      "glh": [e(m) for m in H], "gSh": e(C)})
         self._bufs = {key: b}  # keep one shape resident
         return b
 
@@ -276,8 +286,16 @@ class Trainer:
 
         # ---- forward ----
         self._ok(lib.nrx_train_features(n, B, batch.y.data_ptr(), batch.cfgs, p(bf["x"]), st), "features")
-        dense(p(bf["x"]), F, "init.pw", F, C, p(bf["P0"]))
-        ops.dw3(planes, S, C, p(bf["P0"]), wp("init.dw"), p(bf["S"][0]), relu=True)
+        m_u = batch.m_u.data_ptr()
+        rows = 14 * S
+        if net.var_io:  # every head over all REs, then each user's plane from its own head
+            for h, m in enumerate(net.heads):
+                dense(p(bf["x"]), F, f"init.m{m}.pw", F, C, p(bf["P0h"][h]))
+                ops.dw3(planes, S, C, p(bf["P0h"][h]), wp(f"init.m{m}.dw"), p(bf["S0h"][h]), relu=True)
+                ops.plane_mask(planes, rows, C, C, C, m_u, m, p(bf["S0h"][h]), p(bf["S"][0]), accumulate=h > 0)
+        else:
+            dense(p(bf["x"]), F, "init.pw", F, C, p(bf["P0"]))
+            ops.dw3(planes, S, C, p(bf["P0"]), wp("init.dw"), p(bf["S"][0]), relu=True)
         for k in range(K):
             q = f"it{k}."
             Sk = p(bf["S"][k])
@@ -301,8 +319,16 @@ class Trainer:
             ops.axpy(M * C, 1.0, p(bf["z"][k][R]), p(bf["S"][k + 1]))
             # read-outs after iteration k (multi-loss)
             Sn = p(bf["S"][k + 1])
-            dense(Sn, C, "ro1", C, C, p(bf["r1"][k]), relu=True)
-            dense(p(bf["r1"][k]), C, "ro2", C, mm, p(bf["l"][k]))
+            if net.var_io:  # LLRs of each plane from its own head, m outputs (the rest stay zero)
+                ops.zero(4 * M * mm, p(bf["l"][k]))
+                for h, m in enumerate(net.heads):
+                    dense(Sn, C, f"ro.m{m}.1", C, C, p(bf["r1h"][k][h]), relu=True)
+                    dense(p(bf["r1h"][k][h]), C, f"ro.m{m}.2", C, m, p(bf["lh"][k][h]))
+                    ops.plane_mask(planes, rows, m, m, mm, m_u, m, p(bf["lh"][k][h]), p(bf["l"][k]),
+                                   accumulate=True)
+            else:
+                dense(Sn, C, "ro1", C, C, p(bf["r1"][k]), relu=True)
+                dense(p(bf["r1"][k]), C, "ro2", C, mm, p(bf["l"][k]))
             if self.gamma > 0:
                 dense(Sn, C, "chest.1", C, C, p(bf["c1"][k]), relu=True)
                 dense(p(bf["c1"][k]), C, "chest.2", C, 2 * B, p(bf["hh"][k]))
@@ -318,9 +344,17 @@ class Trainer:
             gl = p(bf["gl"])
             self._ok(lib.nrx_train_bce(n, batch.cfgs, mm, p(bf["l"][k]), batch.bits.data_ptr(),
                                        batch.m_u.data_ptr(), 1.0, gl, self.loss_dev.data_ptr() + 8 * k, st), "bce")
-            dense_bwd(gl, p(bf["r1"][k]), C, "ro2", C, mm, gX=t1)
-            ops.relu_mask(M * C, t1, p(bf["r1"][k]))
-            dense_bwd(t1, Sn, C, "ro1", C, C, gX=gS, accumulate_into_gX=True)
+            if net.var_io:  # route each plane's LLR gradient to its head
+                for h, m in enumerate(net.heads):
+                    glh = p(bf["glh"][h])
+                    ops.plane_mask(planes, rows, m, mm, m, m_u, m, gl, glh)
+                    dense_bwd(glh, p(bf["r1h"][k][h]), C, f"ro.m{m}.2", C, m, gX=t1)
+                    ops.relu_mask(M * C, t1, p(bf["r1h"][k][h]))
+                    dense_bwd(t1, Sn, C, f"ro.m{m}.1", C, C, gX=gS, accumulate_into_gX=True)
+            else:
+                dense_bwd(gl, p(bf["r1"][k]), C, "ro2", C, mm, gX=t1)
+                ops.relu_mask(M * C, t1, p(bf["r1"][k]))
+                dense_bwd(t1, Sn, C, "ro1", C, C, gX=gS, accumulate_into_gX=True)
             if self.gamma > 0:
                 ghh = p(bf["ghh"])
                 self._ok(lib.nrx_train_mse(M * 2 * B, p(bf["hh"][k]), batch.h.data_ptr(), self.gamma / n_mse, ghh,
@@ -358,10 +392,19 @@ class Trainer:
             ops.relu_mask(M * C, t1, p(bf["h1"][k]))
             dense_bwd(t1, Sk, C, q + "mp1", C, C, gX=gS, accumulate_into_gX=True)
         # StateInit: S0 = ReLU(DW(P0)), P0 = PW(x)
-        ops.relu_mask(M * C, gS, p(bf["S"][0]))
-        ops.dw3(planes, S, C, gS, wp("init.dw"), t1, flip=True)
-        ops.dw3_wgrad(planes, S, C, p(bf["P0"]), gS, gp("init.dw"))
-        dense_bwd(t1, p(bf["x"]), F, "init.pw", F, C)
+        if net.var_io:  # each head receives the gradient of its planes only
+            gSh = p(bf["gSh"])
+            for h, m in enumerate(net.heads):
+                ops.plane_mask(planes, rows, C, C, C, m_u, m, gS, gSh)
+                ops.relu_mask(M * C, gSh, p(bf["S0h"][h]))
+                ops.dw3(planes, S, C, gSh, wp(f"init.m{m}.dw"), t1, flip=True)
+                ops.dw3_wgrad(planes, S, C, p(bf["P0h"][h]), gSh, gp(f"init.m{m}.dw"))
+                dense_bwd(t1, p(bf["x"]), F, f"init.m{m}.pw", F, C)
+        else:
+            ops.relu_mask(M * C, gS, p(bf["S"][0]))
+            ops.dw3(planes, S, C, gS, wp("init.dw"), t1, flip=True)
+            ops.dw3_wgrad(planes, S, C, p(bf["P0"]), gS, gp("init.dw"))
+            dense_bwd(t1, p(bf["x"]), F, "init.pw", F, C)
         if adam:
             ops.copy(4, self.lr_t_dev.data_ptr(), self._lr_host.data_ptr())
             self._ok(lib.nrx_train_adam(self.n_total, self.w.data_ptr(), self.g.data_ptr(), self.m1.data_ptr(),

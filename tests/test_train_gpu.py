@@ -360,3 +360,38 @@ def test_training_on_the_gpu_simulator_reduces_the_loss():
         tr.graph_step(sim.draw())
     after = tr.loss_and_grad(val)["bce"][-1]
     assert np.isfinite(after) and after < 0.75 * before, (before, after)
+
+
+# ----------------------------------------------------------------------------
+# Var-IO heads (Sec. III)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("U,bits,mm", [(2, (2, 4), 4), (4, (2, 4, 6, 4), 6)])
+def test_var_io_trainer_gradient_matches_oracle(U, bits, mm):
+    net = synth.NetConfig(num_rx_ant=2, channels=8, res_blocks=1, iterations=2, m_max=mm, var_io=True)
+    W = synth.make_weights(net, seed=15)
+    Wc = synth.make_chest_weights(net, seed=16)
+    sl = _slots(net, U, bits, 2, 2, (2, 11), seed=40 + U)
+    ref_loss, ref_g = TO.training_grads(sl, W, Wc, 2, 1, 0.5)
+    tr = train.Trainer(net, W, Wc, gamma=0.5)
+    out = tr.loss_and_grad(train.DeviceBatch(synth.training_batch(sl, mm)))
+    assert abs(out["loss"] - ref_loss) < TOL_LOSS * max(1.0, abs(ref_loss))
+    g = tr.grads()
+    for name, ref in ref_g.items():
+        nrm = np.linalg.norm(ref)
+        err = np.linalg.norm(g[name] - ref)
+        assert (err == 0.0) if nrm == 0.0 else (err <= TOL_GRAD * nrm), (name, err, nrm)
+
+
+def test_var_io_blob_from_the_trainer_runs_in_the_inference_path():
+    net = synth.NetConfig(num_rx_ant=4, channels=64, res_blocks=2, iterations=2, m_max=6, var_io=True)
+    sl = _slots(net, 3, (6, 2, 4), 2, 4, (2, 11), seed=8)
+    tr = train.Trainer(net, synth.make_weights(net, seed=9), gamma=0.0)
+    out = tr.loss_and_grad(train.DeviceBatch(synth.training_batch(sl, 6)))
+    rx = nrx.Receiver(tr.blob(), 4, 3, 4, max_slots=2, precision="fp32")
+    y = _t(synth.stack_batch(sl))
+    dm = _t(np.stack([s.dmrs for s in sl]))
+    llr = rx.nrx_detect_batch(y, dm, (2, 11), [[6, 2, 4]] * 2).cpu().numpy().astype(np.float64)
+    bits = np.concatenate([np.concatenate([s.bits[u].reshape(-1) for u in range(3)]) for s in sl])
+    bce = float(np.mean(TO.softplus(llr) - bits * llr))
+    assert abs(bce - out["bce"][-1]) < 1e-5 * bce

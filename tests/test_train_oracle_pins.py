@@ -180,3 +180,30 @@ def test_training_batch_layout():
     assert np.array_equal(tb.bits[1, 1, :, :4], sl[1].bits[1]) and np.all(tb.bits[1, 0, :, 2:] == 0)
     assert np.allclose(tb.h[0, 1, 5, 7, 2] + 1j * tb.h[0, 1, 5, 7, 3], sl[0].h[1, 1, 5, 7], atol=1e-6)
     assert np.allclose(TO.channel_target(sl[0].h[1])[5, 7], tb.h[0, 1, 5, 7], atol=1e-6)
+
+
+def test_var_io_training_loss_and_gradient():
+    """Var-IO (Sec. III): the loss of a Var-IO network whose heads copy a
+    single masked head equals the masked network's loss, the torch loss equals
+    the numpy loss, and the autograd gradient of a head equals central finite
+    differences; heads of orders no user carries get zero gradient."""
+    import torch
+    netv = synth.NetConfig(num_rx_ant=2, channels=4, res_blocks=1, iterations=2, m_max=6, var_io=True)
+    Wv = synth.make_weights(netv, seed=27)
+    Wc = synth.make_chest_weights(NET, seed=28)
+    sl = _slots(U=2, bits=(2, 4), n=1, seed=31)
+    a = TO.training_loss(sl, Wv, Wc, 2, 1, 0.3)[0]
+    Wt = {k: torch.from_numpy(np.asarray(v, dtype=np.float64)) for k, v in Wv.items()}
+    Wct = {k: torch.from_numpy(np.asarray(v, dtype=np.float64)) for k, v in Wc.items()}
+    assert abs(float(TO._torch_loss(sl, Wt, Wct, 2, 1, 0.3)) - a) < 1e-12 * max(1.0, abs(a))
+    _, g = TO.training_grads(sl, Wv, Wc, 2, 1, 0.3)
+    assert all(np.all(g[k] == 0.0) for k in g if k.startswith("init.m6") or k.startswith("ro.m6"))
+    h = 1e-6
+    for name, idx in (("init.m4.pw.w", (1, 3)), ("ro.m2.2.w", (1, 2)), ("ro.m4.1.b", (3,)), ("init.m2.dw", (0, 1, 2))):
+        base = {k: np.asarray(v, dtype=np.float64).copy() for k, v in Wv.items()}
+        base[name][idx] += h
+        lp = TO.training_loss(sl, base, Wc, 2, 1, 0.3)[0]
+        base[name][idx] -= 2 * h
+        lm = TO.training_loss(sl, base, Wc, 2, 1, 0.3)[0]
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[name][idx]) < 1e-6 * max(1.0, abs(fd)), (name, fd, g[name][idx])
