@@ -63,3 +63,27 @@ def test_dmrs_gold_matches_transmitter(n_id, n_scid, prb, syms):
     out = nrx.nrx_dmrs_gold(slots, n_id, prb, syms, n_scid).cpu().numpy()
     ref = np.stack([synth.dmrs_gold(prb, syms, s, n_id, n_scid) for s in slots])
     assert out.shape == ref.shape and np.array_equal(out, ref)
+
+
+def test_receivers_with_device_generated_gold_pilots():
+    """A slot transmitted with TS 38.211 Gold-sequence DMRS, received with the
+    pilots generated on the device by nrx_dmrs_gold: LS+LMMSE and the FP32 NRX
+    match the FP64 oracle fed the transmitter's pilots."""
+    from oracle import nrx_oracle as O
+    from paper_2409_02912_b300 import nrx
+    w = synth.WORKLOADS["mu2_4rx_24prb"]
+    cfg = synth.dataclasses.replace(synth.draw_slot_config(w, np.random.Generator(np.random.PCG64(5))),
+                                    n_id=321, slot_number=7)
+    sl = synth.make_slot(cfg, np.random.Generator(np.random.PCG64(6)))
+    W = synth.make_weights(w.net)
+    rx = nrx.Receiver(synth.pack_weights(w.net, W), 4, 2, 24, max_slots=1, precision="fp32")
+    dm = nrx.nrx_dmrs_gold([7], 321, 24, cfg.dmrs_symbols)
+    y = torch.from_numpy(sl.y[None]).cuda()
+    bits = [list(cfg.bits_per_symbol)]
+    l = rx.lmmse_detect_batch(y, dm, cfg.dmrs_symbols, bits, [cfg.noise_var]).cpu().numpy()
+    ref = O.lmmse_receiver(sl.y, sl.dmrs, 2, cfg.dmrs_symbols, cfg.bits_per_symbol, cfg.noise_var)
+    assert np.max(np.abs(l - ref)) <= 1e-4 * np.max(np.abs(ref))
+    l = rx.nrx_detect_batch(y, dm, cfg.dmrs_symbols, bits).cpu().numpy()
+    W64 = {k: v.astype(np.float64) for k, v in W.items()}
+    ref = O.nrx_forward(sl.y, sl.dmrs, 2, cfg.dmrs_symbols, cfg.bits_per_symbol, W64, 2, 2)
+    assert np.max(np.abs(l - ref)) <= 1e-4 * np.max(np.abs(ref))
