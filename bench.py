@@ -384,6 +384,12 @@ def run_ours(args, rank, world, local):
             "delta_vs_fp32_db": {k: (None if v is None or ref10 is None else v - ref10) for k, v in snr10.items()},
             "bler": {k: v["bler"] for k, v in q.items() if not k.startswith("_")},
             "snrs_db": q["_sweep"]["snrs"], "blocks_per_point": q["_sweep"]["blocks_per_point"]}
+        with open(evaluate.TRAINED_MU2_VAR_IO, "rb") as f:
+            qv = evaluate.compare(f.read(), precisions=("fp32", "bf16"), early_exit=False)
+        extras["quality"]["var_io"] = {
+            "weights": os.path.basename(evaluate.TRAINED_MU2_VAR_IO),
+            "snr_db_at_10pct_bler": {k: v["snr_at_10pct"] for k, v in qv.items() if not k.startswith("_")},
+            "bler": {k: v["bler"] for k, v in qv.items() if not k.startswith("_")}}
         # serving loop under the multi-cell load (16 cells, PRB 24/51/106/273, 1-4 users, Poisson
         # arrivals of one slot per 0.5 ms per cell, 0.5 ms deadline) and at a quarter of it
         from paper_2409_02912_b300 import server as nrx_server

@@ -19,6 +19,10 @@ WEIGHTS_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights"
 # Trained by ``python -m paper_2409_02912_b300.train`` on 2-user, 4-Rx slots
 # with QPSK / 16-QAM (the mu2_4rx_24prb network: C=64, R=2, N_it=2, m_max=4).
 TRAINED_MU2 = os.path.join(WEIGHTS_DIR, "nrx_mu2_4rx_c64_r2_it2.bin")
+# The same network with modulation-specific StateInit / ReadoutLLRs heads
+# (Var-IO, Sec. III; blob version 2), initialised from the masked network's
+# checkpoint and trained 135 k further steps on the GPU simulator.
+TRAINED_MU2_VAR_IO = os.path.join(WEIGHTS_DIR, "nrx_mu2_4rx_c64_r2_it2_varIO.bin")
 
 
 @dataclasses.dataclass(frozen=True)
