@@ -486,6 +486,45 @@ class Trainer:
             raise nrx.NrxError(st, what)
 
 
+def _autograd_function():
+    import torch
+
+    class NrxTrainingLoss(torch.autograd.Function):
+        """torch.autograd interface to the training kernels.  forward(w,
+        trainer, batch) returns the multi-loss of Sec. II-B for the trainer's
+        flat FP32 weight vector ``w`` (a tensor sharing ``trainer.w``'s
+        storage, e.g. a ``torch.nn.Parameter`` made from it); backward returns
+        the gradient of the hand-written reverse pass, which runs in the same
+        launch sequence as the forward (one fused, graph-capturable sequence),
+        so a torch optimiser can drive the kernels."""
+
+        @staticmethod
+        def forward(ctx, w, trainer, batch):
+            if w.data_ptr() != trainer.w.data_ptr():
+                raise ValueError("w must share storage with trainer.w")
+            out = trainer.loss_and_grad(batch)
+            ctx.trainer = trainer
+            return torch.tensor(out["loss"], dtype=torch.float32, device=w.device)
+
+        @staticmethod
+        def backward(ctx, grad):
+            return ctx.trainer.g * grad, None, None
+
+    return NrxTrainingLoss
+
+
+def nrx_training_loss(w, trainer: "Trainer", batch: "DeviceBatch"):
+    """``NrxTrainingLoss.apply(w, trainer, batch)``: the differentiable
+    training loss (see ``_autograd_function``)."""
+    global _NRX_FN
+    if _NRX_FN is None:
+        _NRX_FN = _autograd_function()
+    return _NRX_FN.apply(w, trainer, batch)
+
+
+_NRX_FN = None
+
+
 class DeviceBatch:
     """A ``synth.TrainingBatch`` resident on the GPU, with its slot configs."""
 

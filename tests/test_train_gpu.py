@@ -395,3 +395,24 @@ def test_var_io_blob_from_the_trainer_runs_in_the_inference_path():
     bits = np.concatenate([np.concatenate([s.bits[u].reshape(-1) for u in range(3)]) for s in sl])
     bce = float(np.mean(TO.softplus(llr) - bits * llr))
     assert abs(bce - out["bce"][-1]) < 1e-5 * bce
+
+
+def test_autograd_function_drives_a_torch_optimiser():
+    """The kernels behind torch.autograd: the loss is differentiable in the
+    flat weight vector, its gradient is the reverse pass's, and a torch
+    optimiser updating the shared parameter updates the trainer's weights."""
+    net = synth.NetConfig(num_rx_ant=2, channels=8, res_blocks=1, iterations=2, m_max=4)
+    W = synth.make_weights(net, seed=5)
+    sl = _slots(net, 2, (2, 4), 2, 2, (2, 11), seed=60)
+    tr = train.Trainer(net, W, gamma=0.5)
+    batch = train.DeviceBatch(synth.training_batch(sl, 4))
+    param = torch.nn.Parameter(tr.w)
+    loss = train.nrx_training_loss(param, tr, batch)
+    loss.backward()
+    ref = tr.loss_and_grad(batch)
+    assert abs(float(loss) - ref["loss"]) < 1e-5 * ref["loss"]
+    assert torch.allclose(param.grad, tr.g, rtol=1e-4, atol=1e-6 * float(tr.g.abs().max()))
+    w0 = tr.w.clone()
+    opt = torch.optim.SGD([param], lr=1e-3)
+    opt.step()
+    assert torch.allclose(tr.w, w0 - 1e-3 * param.grad)
