@@ -13,7 +13,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <type_traits>
 #include <vector>
+
+#include <cudaTypedefs.h>
 
 #include "net_tc.h"
 #include "tc.cuh"
@@ -546,9 +550,11 @@ struct BlkLayout {
   static constexpr int B2 = B1 + 256;
   static constexpr int SW = B2 + 256;       // E4M3 weight scales: W1, W2 (2 x 64 floats)
   static constexpr int RS = SW + 512;       // E4M3 row scales of the A tiles (256 floats)
-  static constexpr int BAR = RS + 1024;
-  static constexpr int TOTAL = BAR + 16;
+  static constexpr int BAR = RS + 1024;     // MMA mbarrier + TMEM slot
+  static constexpr int INBAR = BAR + 16;    // mbarrier of the input tile's bulk tensor copy
+  static constexpr int TOTAL = INBAR + 16;
   static constexpr int DYN = TOTAL + 1024;
+  static constexpr uint32_t kInBytes = NRX_SYMBOLS * IW * 128;  // the TMA box [14][IW][64] of 16-bit
 };
 
 // Sliding 3x3 depthwise for two adjacent output columns (o = 0, 1) of one
@@ -614,7 +620,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
                                                            const float* __restrict__ w2s,
                                                            const typename P::T* __restrict__ z_in,
                                                            typename P::T* __restrict__ z_out,
-                                                           typename P::T* __restrict__ state, int last, int* err) {
+                                                           typename P::T* __restrict__ state, int last, int* err,
+                                                           const __grid_constant__ CUtensorMap zmap) {
   using T = typename P::T;
   using L = BlkLayout<P>;
   extern __shared__ unsigned char smem_raw[];
@@ -644,6 +651,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
     for (int i = tid; i < 256; i += kThreads) srs[i] = 1.f;
   // zero the A tiles once: padding rows (t = 14, 15) are never written
   for (int i = tid; i < 2 * kTileBytes / 16; i += kThreads) reinterpret_cast<uint4*>(sm + L::A)[i] = make_uint4(0, 0, 0, 0);
+  uint64_t* in_bar = reinterpret_cast<uint64_t*>(sm + L::INBAR);
+  if (tid == 0) tc::mbar_init(in_bar, 1);  // made visible by the fence and barrier in tc_setup
+  uint32_t in_phase = 0;
+  bool tma_pending = false;
   TcCta c;
   tc_setup(c, reinterpret_cast<uint64_t*>(sm + L::BAR), reinterpret_cast<uint32_t*>(sm + L::BAR + 8), 256);
   // this thread's channel pair (2 cp, 2 cp + 1) for the depthwise phases; its taps
@@ -679,27 +690,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
     const int su = tile / tps;  // slot * U + user
     const int s0 = (tile % tps) * L::TW;
     const size_t base = (size_t)su * NRX_SYMBOLS * S;
-    // input tile with a two-subcarrier halo, zero outside the grid (all loads
-    // of a thread issued before its stores)
-    {
-      constexpr int kN = NRX_SYMBOLS * L::IW * 8;
-      constexpr int kIt = (kN + kThreads - 1) / kThreads;
-      uint4 v[kIt];
-#pragma unroll
-      for (int it = 0; it < kIt; ++it) {
-        const int i = tid + it * kThreads;
-        const int ch = i & 7, re = i >> 3;
-        const int t = re / L::IW, e = re % L::IW, s = s0 - 2 + e;
-        v[it] = make_uint4(0, 0, 0, 0);
-        if (i < kN && s >= 0 && s < S)
-          v[it] = __ldg(reinterpret_cast<const uint4*>(z_in + (base + (size_t)t * S + s) * C64) + ch);
-      }
-#pragma unroll
-      for (int it = 0; it < kIt; ++it) {
-        const int i = tid + it * kThreads;
-        if (i < kN) reinterpret_cast<uint4*>(sm + L::ZB)[i] = v[it];
-      }
+    // input tile [14 symbols][IW subcarriers][64 channels] with a two-subcarrier
+    // halo, staged by one bulk tensor copy (TMA); subcarriers outside the grid
+    // read as zero.  The previous tile's readers of ZB are past the barrier
+    // that ended it, and their generic writes were fenced for the async proxy.
+    if (tid == 0) {
+      tc::mbar_arrive_expect_tx(in_bar, L::kInBytes);
+      tc::tma_load_3d(sm + L::ZB, &zmap, 0, s0 - 2, su * NRX_SYMBOLS, in_bar);
     }
+    tma_pending = true;
     // L2 prefetch: the next tile's input rows, and this tile's state rows (last block)
     {
       const int nt = tile + gridDim.x;
@@ -714,7 +713,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
         if (s < S) tc::prefetch_l2(state + (base + (size_t)t * S + s) * C64);
       }
     }
-    __syncthreads();
+    {  // wait (bounded) for the input tile
+      bool ok = true;
+      if (tid == 0) ok = tc::mbar_wait(in_bar, in_phase);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(err, 1);
+        timed_out = true;
+        break;  // tma_pending stays set: the teardown waits for this phase
+      }
+      in_phase ^= 1u;
+      tma_pending = false;
+    }
     // DW1: output column e (s = s0-1+e) reads input columns e, e+1, e+2; warp
     // cg computes output columns 2 cg and 2 cg + 1.
     {
@@ -893,9 +902,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
         *reinterpret_cast<uint4*>(out + tbase + out_off[it]) = pack8<T>(o);
       }
     }
+    tc::fence_async_smem();  // the next tile's bulk copy overwrites ZB after these generic writes
     tc::tc_fence_before();
     __syncthreads();
   }
+  if (tma_pending && tid == 0) tc::mbar_wait(in_bar, in_phase, 100000000ull);  // let a copy in flight land
   tc_teardown(c, 256, timed_out);
 }
 
@@ -1237,17 +1248,56 @@ cudaError_t launch_mp_tc(const Geometry& g, const IterWeightsTC& w, const typena
   return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no direct
+// libcuda link).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 3-D map of a 16-bit activation tensor [planes x 14][S][64]: box
+// [14 symbols][IW subcarriers][64 channels], no swizzle, zero fill.
+template <typename T>
+cudaError_t activation_map(CUtensorMap* map, const T* base, int planes, int S, int box_s) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {64, (cuuint64_t)S, (cuuint64_t)planes * NRX_SYMBOLS};
+  const cuuint64_t strides[2] = {64 * sizeof(T), (cuuint64_t)S * 64 * sizeof(T)};
+  const cuuint32_t box[3] = {64, (cuuint32_t)box_s, NRX_SYMBOLS};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUtensorMapDataType dt =
+      sizeof(T) == 2 && std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const CUresult r = enc(map, dt, 3, const_cast<T*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <typename P>
 cudaError_t launch_block_tc(const Geometry& g, const IterWeightsTC& w, int r, const typename P::T* z_in,
                             typename P::T* z_out, typename P::T* state, bool last, cudaStream_t st) {
   if (g.C != 64) return cudaErrorInvalidValue;
+  if (reinterpret_cast<uintptr_t>(z_in) & 15) return cudaErrorInvalidValue;  // TMA global address alignment
   const int tps = (g.S + BlkLayout<P>::TW - 1) / BlkLayout<P>::TW;
   const int tiles = g.n_slots * g.U * tps;
   const int smem = BlkLayout<P>::DYN;
   ensure_smem<k_block_tc<P>>(smem);
+  CUtensorMap zmap;
+  const cudaError_t e = activation_map(&zmap, z_in, g.n_slots * g.U, g.S, BlkLayout<P>::IW);
+  if (e != cudaSuccess) return e;
   const int grid = grid_for(smem, 2, tiles);
   k_block_tc<P><<<grid, kThreads, smem, st>>>(g, w.pw1[r], w.pw2[r], w.pw1_b[r], w.pw2_b[r], w.dw1[r], w.dw2[r],
-                                               w.pw1_sc[r], w.pw2_sc[r], z_in, z_out, state, last ? 1 : 0, w.err);
+                                               w.pw1_sc[r], w.pw2_sc[r], z_in, z_out, state, last ? 1 : 0, w.err,
+                                               zmap);
   return cudaGetLastError();
 }
 
@@ -1259,7 +1309,7 @@ cudaError_t launch_readout_tc(const Geometry& g, const SlotTable& tab, const Rea
   const int tiles = g.n_slots * g.U * tpsu;
   const int smem = RoLayout<P>::DYN;
   ensure_smem<k_readout_tc<P>>(smem);
-  const int grid = grid_for(smem, 4, tiles);
+  const int grid = grid_for(smem, 8, tiles);  // 8 x 64 TMEM columns per SM
   k_readout_tc<P><<<grid, 128, smem, st>>>(g, tab, w, state, llr, tpsu);
   return cudaGetLastError();
 }

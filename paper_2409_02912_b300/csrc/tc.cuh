@@ -4,6 +4,7 @@
 // bounded waits.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -62,6 +63,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
     if ((i & 255) == 0 && globaltimer() - t0 > limit_ns) return false;
   }
   return false;
+}
+
+// Arrive on `bar` and add `bytes` to the transaction count it waits for (the
+// bytes of the bulk tensor copies that complete on it).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// TMA: copy the box at coordinates (x, y, z) of the 3-D tensor `map` into
+// shared memory at dst; completion is signalled on `bar` (complete_tx).  x
+// must be a multiple of 16 bytes / element size; y and z may lie outside the
+// tensor (the fill value, zero, is read there).
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
 }
 
 // ---------------------------------------------------------------------------
