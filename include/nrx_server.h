@@ -24,6 +24,11 @@
  *     count, earliest deadline first, as many as the measured execution time
  *     allows before the earliest deadline; each idle fallback lane takes up
  *     to a batch of its queue;
+ *   - an NRX batch runs as a CUDA graph: the receiver's launch sequence is
+ *     captured once per (bucket, user count, batch size, modulation orders)
+ *     on the lane's fixed staging buffers and replayed after (up to 256
+ *     graphs per bucket; the uploads and downloads, whose host addresses
+ *     change, are issued around it);
  *   - execution times per (bucket, users, batch size, receiver) are measured
  *     at creation (calibration launches) and tracked with an exponential
  *     moving average of the CUDA-event times of served batches;
@@ -70,9 +75,13 @@ typedef struct {
   int32_t bits_per_symbol[4];   /* m_u of users 0..num_users-1 (2, 4 or 6, <= m_max) */
   float noise_var;              /* N0 (used by the LMMSE fallback) */
   const void* y_host;           /* pinned host complex64 [B][14][12 num_prb] */
-  const void* dmrs_host;        /* pinned host complex64 [n_dmrs][6 num_prb] */
+  const void* dmrs_host;        /* pinned host complex64 [n_dmrs][6 num_prb], or NULL: the server
+                                   generates the cell's TS 38.211 pilots on the device from
+                                   n_id and slot_number (nrx_dmrs_gold, n_SCID = 0) */
   float* llr_host;              /* pinned host float32, nrx_llr_count floats (written on completion) */
   int64_t arrival_ns;           /* arrival time on the steady clock (nrx_server_now_ns); 0 = now */
+  int32_t n_id;                 /* DMRS scrambling identity of the cell (0..65535; with dmrs_host NULL) */
+  int32_t slot_number;          /* slot index within the frame (0..159; with dmrs_host NULL) */
 } nrx_request;
 
 typedef struct {
@@ -89,6 +98,11 @@ typedef struct {
   int64_t submitted, served_nrx, served_lmmse, rejected, launches;
   int32_t bucket_batch_capacity[NRX_SERVER_MAX_BUCKETS];  /* after admission */
   size_t device_bytes;          /* device memory taken by the server */
+  int64_t graph_launches;       /* NRX batches run by replaying a captured CUDA graph */
+  int64_t graphs_captured;
+  int64_t direct_launches;      /* NRX batches launched kernel by kernel (composition not captured yet) */
+  int64_t enqueue_ns_graph;     /* host time spent enqueueing the NRX on each path (sums) */
+  int64_t enqueue_ns_direct;
 } nrx_server_stats;
 
 /* Create the server: contexts per bucket (weights blob as nrx_create),

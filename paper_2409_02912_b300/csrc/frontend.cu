@@ -105,16 +105,16 @@ __global__ void __launch_bounds__(256) k_state_init(Geometry g, SlotTable tab, c
         x[4 * B + 1] = pe_freq(u, s);
 #pragma unroll 4
         for (int q = 0; q < NQ; ++q) {
-          float4 acc = *reinterpret_cast<const float4*>(bias + 4 * q);
+          const float4 b4 = *reinterpret_cast<const float4*>(bias + 4 * q);
+          float2 a01 = make_float2(b4.x, b4.y), a23 = make_float2(b4.z, b4.w);
 #pragma unroll
-          for (int k = 0; k < F; ++k) {
+          for (int k = 0; k < F; ++k) {  // packed FP32 FMAs, two channels each
             const float4 w = *reinterpret_cast<const float4*>(wt + k * C + 4 * q);  // same for all lanes
-            acc.x = fmaf(w.x, x[k], acc.x);
-            acc.y = fmaf(w.y, x[k], acc.y);
-            acc.z = fmaf(w.z, x[k], acc.z);
-            acc.w = fmaf(w.w, x[k], acc.w);
+            const float2 xk = make_float2(x[k], x[k]);
+            a01 = tc::ffma2(make_float2(w.x, w.y), xk, a01);
+            a23 = tc::ffma2(make_float2(w.z, w.w), xk, a23);
           }
-          hrow[q ^ (tid & (NQ - 1))] = acc;
+          hrow[q ^ (tid & (NQ - 1))] = make_float4(a01.x, a01.y, a23.x, a23.y);
         }
       }
     }

@@ -9,7 +9,9 @@
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
+#include <cstddef>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -21,6 +23,9 @@ namespace {
 constexpr int kSymbols = 14;
 constexpr int kMaxUsers = 4;
 constexpr int kRcvNrx = 0, kRcvLmmse = 1;
+constexpr size_t kMaxGraphs = 256;  // captured NRX launch sequences per bucket
+static_assert(sizeof(nrx_request) == 72 && offsetof(nrx_request, slot_number) == 68, "nrx_request layout");
+static_assert(sizeof(nrx_completion) == 40 && sizeof(nrx_server_stats) == 120, "serving ABI layout");
 
 int64_t steady_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
@@ -62,6 +67,11 @@ struct Bucket {
   std::deque<Pending> q[2][kMaxUsers + 1];  // [lane][users], arrival (= deadline) order
   int queued = 0;
   std::vector<double> est_us[2][kMaxUsers + 1];  // [lane][users][n], n <= cap
+  // (users, n, m_u...) -> captured NRX launch sequence; nullptr while the
+  // composition waits in `to_capture` for an idle moment of the worker
+  std::map<std::vector<int32_t>, cudaGraphExec_t> graphs;
+  std::deque<std::vector<int32_t>> to_capture;
+  cudaStream_t capture_st = nullptr;
 };
 
 }  // namespace
@@ -126,7 +136,67 @@ std::vector<nrx_slot_cfg> slot_cfgs(const nrx_server* s, const Bucket& b, const 
   return cfgs;
 }
 
-// Enqueue one batch on lane `li` of bucket b: uploads, receiver, LLR downloads.
+// The NRX launch sequence of a batch composition: replayed from its captured
+// CUDA graph when there is one, else launched directly and the composition
+// queued for capture (capture and instantiation cost host time, so they run
+// only when the bucket's worker is idle, never in front of a waiting batch).
+nrx_status run_nrx_batch(nrx_server* s, Bucket& b, Lane& L, int n, const nrx_slot_cfg* cfgs, const int32_t* bits,
+                         int users) {
+  const int64_t t0 = steady_ns();
+  std::vector<int32_t> key = {users, n};
+  key.insert(key.end(), bits, bits + (size_t)n * users);
+  auto it = b.graphs.find(key);
+  if (it != b.graphs.end() && it->second) {
+    if (cudaGraphLaunch(it->second, L.st) != cudaSuccess) return NRX_ECUDA;
+    const int64_t dt = steady_ns() - t0;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stats.graph_launches++;
+    s->stats.enqueue_ns_graph += dt;
+    return NRX_OK;
+  }
+  if (it == b.graphs.end() && b.graphs.size() < kMaxGraphs) {
+    b.to_capture.push_back(key);
+    b.graphs.emplace(std::move(key), nullptr);
+  }
+  const nrx_status st = nrx_detect_batch(b.ctx, n, L.y, cfgs, bits, L.llr, L.st);
+  const int64_t dt = steady_ns() - t0;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->stats.direct_launches++;
+  s->stats.enqueue_ns_direct += dt;
+  return st;
+}
+
+// Capture one queued composition on the bucket's capture stream (nothing
+// executes) and instantiate it.  A failed capture leaves the composition on
+// direct launches.
+void capture_one(nrx_server* s, Bucket& b) {
+  const std::vector<int32_t> key = b.to_capture.front();
+  b.to_capture.pop_front();
+  const int users = key[0], n = key[1];
+  Lane& L = b.lane[kRcvNrx];
+  std::vector<nrx_slot_cfg> cfgs = slot_cfgs(s, b, L, n, users, nullptr);
+  if (cudaStreamBeginCapture(b.capture_st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const nrx_status st = nrx_detect_batch(b.ctx, n, L.y, cfgs.data(), key.data() + 2, L.llr, b.capture_st);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b.capture_st, &g);
+  cudaGraphExec_t exec = nullptr;
+  const bool ok = st == NRX_OK && e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  if (!ok) {
+    if (exec) cudaGraphExecDestroy(exec);
+    return;
+  }
+  b.graphs[key] = exec;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->stats.graphs_captured++;
+}
+
+// Enqueue one batch on lane `li` of bucket b: uploads (or device-generated
+// pilots), receiver, LLR downloads.
 nrx_status launch(nrx_server* s, Bucket& b, int li, const std::vector<Pending>& reqs, int users) {
   Lane& L = b.lane[li];
   const int n = (int)reqs.size();
@@ -137,13 +207,20 @@ nrx_status launch(nrx_server* s, Bucket& b, int li, const std::vector<Pending>& 
   for (int i = 0; i < n; ++i) {
     const nrx_request& r = reqs[i].req;
     if (cudaMemcpyAsync(L.y + i * y_per, r.y_host, y_per * sizeof(float2), cudaMemcpyHostToDevice, L.st) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(L.dmrs + i * d_per, r.dmrs_host, d_per * sizeof(float2), cudaMemcpyHostToDevice, L.st) !=
-            cudaSuccess)
+        cudaSuccess)
       return NRX_ECUDA;
+    if (r.dmrs_host) {
+      if (cudaMemcpyAsync(L.dmrs + i * d_per, r.dmrs_host, d_per * sizeof(float2), cudaMemcpyHostToDevice, L.st) !=
+          cudaSuccess)
+        return NRX_ECUDA;
+    } else {
+      const nrx_status st = nrx_dmrs_gold(1, &r.slot_number, r.n_id, 0, b.prb, s->cfg.num_dmrs_symbols,
+                                          s->cfg.dmrs_symbols, L.dmrs + i * d_per, L.st);
+      if (st != NRX_OK) return st;
+    }
     for (int u = 0; u < users; ++u) bits[(size_t)i * users + u] = r.bits_per_symbol[u];
   }
-  nrx_status st = li == kRcvNrx ? nrx_detect_batch(b.ctx, n, L.y, cfgs.data(), bits.data(), L.llr, L.st)
+  nrx_status st = li == kRcvNrx ? run_nrx_batch(s, b, L, n, cfgs.data(), bits.data(), users)
                                 : lmmse_detect_batch(b.ctx, n, L.y, cfgs.data(), bits.data(), L.llr, L.st);
   if (st != NRX_OK) return st;
   size_t off = 0;
@@ -243,16 +320,20 @@ void worker_main(nrx_server* s, int bi) {
   Bucket& b = s->buckets[bi];
   std::vector<Pending> incoming;
   for (;;) {
+    bool idle = false;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       const bool busy = b.lane[0].cur.active || b.lane[1].cur.active || b.queued > 0;
       if (s->abandon.load()) break;
-      if (!busy && b.inbox.empty()) {
-        if (s->stop.load()) break;
-        s->cv.wait_for(lk, std::chrono::microseconds(200));
-      }
+      idle = !busy && b.inbox.empty();
+      if (idle && s->stop.load()) break;
+      if (idle && b.to_capture.empty()) s->cv.wait_for(lk, std::chrono::microseconds(200));
       incoming.assign(b.inbox.begin(), b.inbox.end());
       b.inbox.clear();
+    }
+    if (idle && incoming.empty() && !b.to_capture.empty()) {
+      capture_one(s, b);
+      continue;
     }
     for (const Pending& p : incoming) {
       if (b.queued >= s->cfg.queue_capacity) {
@@ -337,6 +418,10 @@ nrx_status calibrate(nrx_server* s, Bucket& b) {
 }
 
 void free_bucket(Bucket& b) {
+  for (auto& kv : b.graphs)
+    if (kv.second) cudaGraphExecDestroy(kv.second);
+  b.graphs.clear();
+  if (b.capture_st) cudaStreamDestroy(b.capture_st);
   if (b.ctx) nrx_destroy(b.ctx);
   for (Lane& L : b.lane) {
     if (L.y) cudaFree(L.y);
@@ -373,6 +458,7 @@ nrx_status make_bucket(nrx_server* s, const void* w, size_t wb, Bucket& b, int p
         cudaEventCreate(&L.ref) != cudaSuccess)
       return NRX_ECUDA;
   }
+  if (cudaStreamCreateWithFlags(&b.capture_st, cudaStreamNonBlocking) != cudaSuccess) return NRX_ECUDA;
   cudaMemGetInfo(&free1, &total);
   *used = free0 > free1 ? free0 - free1 : 0;
   return NRX_OK;
@@ -464,7 +550,9 @@ void nrx_server_destroy(nrx_server* s) {
 }
 
 nrx_status nrx_server_submit(nrx_server* s, const nrx_request* r, uint64_t* ticket) {
-  if (!s || !r || !r->y_host || !r->dmrs_host) return NRX_EINVAL;
+  if (!s || !r || !r->y_host) return NRX_EINVAL;
+  if (!r->dmrs_host && (r->n_id < 0 || r->n_id > 65535 || r->slot_number < 0 || r->slot_number > 159))
+    return NRX_EINVAL;
   int bi = -1;
   for (int i = 0; i < (int)s->buckets.size(); ++i)
     if (s->buckets[i].prb == r->num_prb) bi = i;

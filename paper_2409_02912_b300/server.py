@@ -33,7 +33,7 @@ class nrx_request(ctypes.Structure):
     _fields_ = [("num_prb", ctypes.c_int32), ("num_users", ctypes.c_int32),
                 ("bits_per_symbol", ctypes.c_int32 * 4), ("noise_var", ctypes.c_float),
                 ("y_host", ctypes.c_void_p), ("dmrs_host", ctypes.c_void_p), ("llr_host", ctypes.c_void_p),
-                ("arrival_ns", ctypes.c_int64)]
+                ("arrival_ns", ctypes.c_int64), ("n_id", ctypes.c_int32), ("slot_number", ctypes.c_int32)]
 
 
 class nrx_completion(ctypes.Structure):
@@ -45,7 +45,10 @@ class nrx_completion(ctypes.Structure):
 class nrx_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("served_nrx", ctypes.c_int64), ("served_lmmse", ctypes.c_int64),
                 ("rejected", ctypes.c_int64), ("launches", ctypes.c_int64),
-                ("bucket_batch_capacity", ctypes.c_int32 * MAX_BUCKETS), ("device_bytes", ctypes.c_size_t)]
+                ("bucket_batch_capacity", ctypes.c_int32 * MAX_BUCKETS), ("device_bytes", ctypes.c_size_t),
+                ("graph_launches", ctypes.c_int64), ("graphs_captured", ctypes.c_int64),
+                ("direct_launches", ctypes.c_int64), ("enqueue_ns_graph", ctypes.c_int64),
+                ("enqueue_ns_direct", ctypes.c_int64)]
 
 
 _configured = False
@@ -156,12 +159,17 @@ class Server:
         return {"submitted": s.submitted, "served_nrx": s.served_nrx, "served_lmmse": s.served_lmmse,
                 "rejected": s.rejected, "launches": s.launches,
                 "bucket_batch_capacity": list(s.bucket_batch_capacity)[:len(self.bucket_prb)],
-                "device_bytes": int(s.device_bytes)}
+                "device_bytes": int(s.device_bytes), "graph_launches": s.graph_launches,
+                "graphs_captured": s.graphs_captured, "direct_launches": s.direct_launches,
+                "enqueue_us_graph_mean": s.enqueue_ns_graph / max(s.graph_launches, 1) / 1e3,
+                "enqueue_us_direct_mean": s.enqueue_ns_direct / max(s.direct_launches, 1) / 1e3}
 
 
 def make_request(sl: synth.Slot, y_pin, dmrs_pin, llr_pin, arrival_ns: int = 0) -> nrx_request:
     """Request for one slot whose grid / pilots are in the pinned host tensors
-    ``y_pin`` / ``dmrs_pin`` and whose LLRs go to ``llr_pin``."""
+    ``y_pin`` / ``dmrs_pin`` and whose LLRs go to ``llr_pin``.  With
+    ``dmrs_pin`` None the server generates the cell's TS 38.211 pilots on the
+    device from the slot's ``n_id`` and ``slot_number``."""
     r = nrx_request()
     r.num_prb = sl.cfg.num_prb
     r.num_users = sl.cfg.num_users
@@ -169,7 +177,9 @@ def make_request(sl: synth.Slot, y_pin, dmrs_pin, llr_pin, arrival_ns: int = 0) 
         r.bits_per_symbol[u] = m
     r.noise_var = sl.cfg.noise_var
     r.y_host = y_pin.data_ptr()
-    r.dmrs_host = dmrs_pin.data_ptr()
+    r.dmrs_host = dmrs_pin.data_ptr() if dmrs_pin is not None else None
+    r.n_id = sl.cfg.n_id
+    r.slot_number = sl.cfg.slot_number
     r.llr_host = llr_pin.data_ptr() if llr_pin is not None else None
     r.arrival_ns = arrival_ns
     return r

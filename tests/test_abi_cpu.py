@@ -118,8 +118,10 @@ def test_create_without_gpu_fails_loudly(lib):
 def test_server_structs_and_validation(lib):
     """ctypes layouts of the serving ABI and its host-side config checks."""
     import ctypes
-    assert ctypes.sizeof(server.nrx_request) == 64
+    assert ctypes.sizeof(server.nrx_request) == 72
     assert server.nrx_request.arrival_ns.offset == 56
+    assert server.nrx_request.slot_number.offset == 68
+    assert ctypes.sizeof(server.nrx_server_stats) == 120
     assert ctypes.sizeof(server.nrx_completion) == 40
     sl = server.load()
     net = synth.WORKLOADS["su_2rx_4prb"].net

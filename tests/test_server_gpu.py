@@ -43,6 +43,20 @@ def _serve(srv, slots):
     return [b[2].numpy().copy() for b in bufs], comps
 
 
+def _settle_captures(srv, quiet_s=0.2, limit_s=10.0):
+    """Wait until the server has captured no new graph for ``quiet_s``."""
+    import time
+    t_end = time.monotonic() + limit_s
+    last, t_last = srv.stats()["graphs_captured"], time.monotonic()
+    while time.monotonic() < t_end:
+        time.sleep(0.02)
+        n = srv.stats()["graphs_captured"]
+        if n != last:
+            last, t_last = n, time.monotonic()
+        elif time.monotonic() - t_last >= quiet_s:
+            return
+
+
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_llrs_do_not_depend_on_batch_company(precision):
     blob = synth.pack_weights(NET, synth.make_weights(NET))
@@ -59,11 +73,50 @@ def test_llrs_do_not_depend_on_batch_company(precision):
         assert max(c.batch_size for c in c2) > 1
         for a, m in zip(alone, mixed):
             assert np.array_equal(a, m)
+        # compositions are captured while the worker is idle; the same
+        # composition served again replays its graph, with the same LLRs
+        _settle_captures(srv)
+        before = srv.stats()["graph_launches"]
+        again, _ = _serve(srv, slots[:1])
+        assert np.array_equal(again[0], alone[0])
+        st = srv.stats()
+        assert st["graphs_captured"] >= 1 and st["graph_launches"] == before + 1
         rx = nrx.Receiver(blob, 4, 2, 8, max_slots=1, precision=precision)
         y = torch.from_numpy(synth.stack_batch(slots[:1])).cuda()
         d = torch.from_numpy(np.stack([slots[0].dmrs])).cuda()
         direct = rx.nrx_detect_batch(y, d, (2, 11), [slots[0].cfg.bits_per_symbol]).cpu().numpy()
         assert np.array_equal(direct, alone[0])
+    finally:
+        srv.close()
+
+
+def test_device_generated_gold_pilots_match_host_pilots():
+    """Requests without host pilots get the cell's TS 38.211 DMRS generated on
+    the device from (n_id, slot_number); the LLRs equal those served with the
+    same pilots uploaded from the host."""
+    blob = synth.pack_weights(NET, synth.make_weights(NET))
+    srv = server.Server(blob, 4, [8], max_users=2, max_batch=4, precision="fp16", deadline_us=1e7)
+    try:
+        slots = []
+        for i in range(4):
+            rng = np.random.Generator(np.random.PCG64(700 + i))
+            cfg = synth.SlotConfig(num_prb=8, num_users=2, num_rx_ant=4, dmrs_symbols=(2, 11), bits_per_symbol=(4, 2),
+                                   snr_db=12.0, num_taps=8, delay_spread_s=1e-7, doppler_hz=100.0, ula=True,
+                                   n_id=[0, 17, 1000, 65535][i], slot_number=[0, 5, 19, 159][i])
+            slots.append(synth.make_slot(cfg, rng))
+        host, _ = _serve(srv, slots)
+        bufs = [_pinned(s) for s in slots]
+        for s, (y, _, l) in zip(slots, bufs):
+            srv.submit(server.make_request(s, y, None, l))
+        srv.drain(20000)
+        comps = srv.poll()
+        assert len(comps) == 4 and all(c.status == 0 and c.receiver == 0 for c in comps)
+        for h, (_, _, l) in zip(host, bufs):
+            assert np.array_equal(h, l.numpy())
+        bad = server.make_request(slots[0], bufs[0][0], None, bufs[0][2])
+        bad.slot_number = 160
+        with pytest.raises(nrx.NrxError):
+            srv.submit(bad)
     finally:
         srv.close()
 
