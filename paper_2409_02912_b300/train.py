@@ -138,14 +138,26 @@ class Trainer:
 
     ``loss_and_grad(batch)`` runs the forward and reverse passes and leaves the
     gradient in ``self.g``; ``step(batch)`` adds the Adam update.
+
+    ``recompute``: keep only each residual block's input and rebuild its three
+    conv activations (DW1, ReLU(PW1), ReLU(DW2)) from it in the reverse pass,
+    one block at a time, instead of storing them for every block of every
+    iteration.  ``None`` decides per batch shape: recompute when the stored
+    activations would take more than ``memory_fraction`` of the free device
+    memory.  The recomputed activations are bit-identical to the stored ones
+    (the forward kernels are deterministic), so the gradient is the same.
     """
 
     def __init__(self, net: synth.NetConfig, weights: Dict[str, np.ndarray],
                  chest: Optional[Dict[str, np.ndarray]] = None, lr: float = 1e-3, gamma: float = 1.0,
-                 beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, precision: str = "fp32"):
+                 beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, precision: str = "fp32",
+                 recompute: Optional[bool] = None, memory_fraction: float = 0.5):
         import torch
         self.torch = torch
         self.precision = precision
+        self.recompute = recompute
+        self.memory_fraction = memory_fraction
+        self.recomputing = False  # mode of the current buffers
         _Ops(None, precision)  # validates the precision
         self.net = net
         self.lr, self.gamma, self.beta1, self.beta2, self.eps = lr, gamma, beta1, beta2, eps
@@ -221,6 +233,25 @@ class Trainer:
         return hdr + self.w[:self.n_blob].cpu().numpy().tobytes()
 
     # -- buffers ------------------------------------------------------------
+    def activation_bytes(self, n: int, U: int, S: int, recompute: bool) -> int:
+        """Device bytes of the saved activations and reverse-pass scratch for
+        a batch of n slots x U users x S subcarriers, in either mode."""
+        net = self.net
+        C, F, R, K, B, mm = net.channels, net.in_features, net.res_blocks, net.iterations, net.num_rx_ant, net.m_max
+        conv = 3 if recompute else 3 * K * R
+        cols = (F + C + (K + 1) * C + 3 * K * C + K * (R + 1) * C + conv * C + K * (C + mm + C + 2 * B)
+                + 4 * C + mm + 2 * B)
+        if net.var_io:
+            H = net.heads
+            cols += 2 * len(H) * C + K * (len(H) * C + sum(H)) + sum(H) + C
+        return 4 * n * U * 14 * S * cols
+
+    def _use_recompute(self, n, U, S) -> bool:
+        if self.recompute is not None:
+            return bool(self.recompute)
+        free, _ = self.torch.cuda.mem_get_info()
+        return self.activation_bytes(n, U, S, False) > self.memory_fraction * free
+
     def _buffers(self, n, U, S):
         key = (n, U, S)
         if key in self._bufs:
@@ -229,13 +260,21 @@ class Trainer:
         net = self.net
         C, F, R, K = net.channels, net.in_features, net.res_blocks, net.iterations
         M = n * U * 14 * S
+        self._bufs = {}  # release the previous shape (and the graph that uses it) before sizing this one
+        self._graph, self._graph_shape = None, None
+        rc = self._use_recompute(n, U, S)
+        self.recomputing = rc
         e = lambda w: torch.empty((M, w), dtype=torch.float32, device="cuda")  # noqa: E731
+        def conv():  # conv activations of every (iteration, block), or one shared
+            if rc:      # set that the reverse pass refills block by block
+                t = e(C)
+                return [[t] * R for _ in range(K)]
+            return [[e(C) for _ in range(R)] for _ in range(K)]
+
         b = {"x": e(F), "P0": e(C), "S": [e(C) for _ in range(K + 1)],
              "h1": [e(C) for _ in range(K)], "msg": [e(C) for _ in range(K)], "a": [e(C) for _ in range(K)],
              "z": [[e(C) for _ in range(R + 1)] for _ in range(K)],
-             "d1": [[e(C) for _ in range(R)] for _ in range(K)],
-             "p1": [[e(C) for _ in range(R)] for _ in range(K)],
-             "d2": [[e(C) for _ in range(R)] for _ in range(K)],
+             "d1": conv(), "p1": conv(), "d2": conv(),
              "r1": [e(C) for _ in range(K)], "l": [e(net.m_max) for _ in range(K)],
              "c1": [e(C) for _ in range(K)], "hh": [e(2 * net.num_rx_ant) for _ in range(K)],
              "gS": e(C), "gz": e(C), "t1": e(C), "t2": e(C), "gl": e(net.m_max),
@@ -367,6 +406,11 @@ class Trainer:
             for r in reversed(range(R)):
                 bq = f"{q}blk{r}."
                 d1, p1, d2 = p(bf["d1"][k][r]), p(bf["p1"][k][r]), p(bf["d2"][k][r])
+                if self.recomputing:  # rebuild this block's conv activations from its input
+                    zr = p(bf["z"][k][r])
+                    ops.dw3(planes, S, C, zr, wp(bq + "dw1"), d1)
+                    dense(d1, C, bq + "pw1", C, C, p1, relu=True)
+                    ops.dw3(planes, S, C, p1, wp(bq + "dw2"), d2, relu=True)
                 dense_bwd(gz, d2, C, bq + "pw2", C, C, gX=t1)
                 ops.relu_mask(M * C, t1, d2)
                 ops.dw3(planes, S, C, t1, wp(bq + "dw2"), t2, flip=True)
@@ -637,7 +681,8 @@ def _make_batch(args):
 
 def fit(workload: synth.Workload, seconds: float, lr: float = 2e-3, lr_final: float = 5e-5, gamma: float = 1.0,
         seed: int = 1, resume: Optional[str] = None, workers: Optional[int] = None, log_every: int = 2000,
-        trainer: Optional[Trainer] = None, precision: str = "fp32", simulator: str = "cpu") -> Trainer:
+        trainer: Optional[Trainer] = None, precision: str = "fp32", simulator: str = "cpu",
+        recompute: Optional[bool] = None) -> Trainer:
     """Train for a wall-clock budget on fresh random batches of ``workload``
     (random MCS association and SNR offsets, Sec. IV-A), with an exponential
     learning-rate decay from lr to lr_final over the budget.  Batches are
@@ -654,7 +699,7 @@ def fit(workload: synth.Workload, seconds: float, lr: float = 2e-3, lr_final: fl
         for k in ("ro2.w", "ro2.b"):
             W[k][...] = 0.0
         Wc["chest.2.w"][...] = 0.0
-        trainer = Trainer(net, W, Wc, lr=lr, gamma=gamma, precision=precision)
+        trainer = Trainer(net, W, Wc, lr=lr, gamma=gamma, precision=precision, recompute=recompute)
     if resume:
         trainer.restore(resume)
     if simulator == "gpu":  # every batch drawn on the device, no host workers
@@ -708,6 +753,8 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32", choices=("fp32", "bf16"), help="GEMM compute of the passes")
     ap.add_argument("--simulator", default="cpu", choices=("cpu", "gpu"),
                     help="draw batches with CPU workers (synth) or on the GPU (nrx_train_simulate)")
+    ap.add_argument("--recompute", default="auto", choices=("auto", "on", "off"),
+                    help="rebuild the conv activations in the reverse pass (auto: when memory asks)")
     ap.add_argument("--checkpoint", default=None, help="write an .npz checkpoint here")
     ap.add_argument("--out", required=True, help="write the inference weight blob here")
     a = ap.parse_args(argv)
@@ -716,7 +763,7 @@ def main(argv=None):
     wl = dataclasses_replace(base, num_prb=a.prb, batch=a.batch, snr_db_range=snr,
                              mcs_choices=tuple(int(v) for v in a.mcs.split(",")))
     tr = fit(wl, a.seconds, lr=a.lr, lr_final=a.lr_final, gamma=a.gamma, resume=a.resume, precision=a.precision,
-             simulator=a.simulator)
+             simulator=a.simulator, recompute={"auto": None, "on": True, "off": False}[a.recompute])
     if a.checkpoint:
         tr.save(a.checkpoint)
     with open(a.out, "wb") as f:

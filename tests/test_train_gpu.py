@@ -223,6 +223,42 @@ def test_graph_step_matches_eager_steps():
     assert graph.t == eager.t == 4
 
 
+def test_recompute_gives_the_same_loss_and_gradient_with_less_memory():
+    """Recomputing each residual block's conv activations in the reverse pass
+    (instead of storing them for every block and iteration) leaves the loss
+    and the gradient unchanged up to the rounding order of atomic reductions,
+    in eager and graph-captured steps, and takes fewer activation bytes; the
+    automatic mode switches to it when the stored activations exceed the
+    memory fraction."""
+    net = synth.NetConfig(num_rx_ant=4, channels=32, res_blocks=2, iterations=2, m_max=4)
+    W, Wc = synth.make_weights(net, seed=21), synth.make_chest_weights(net, seed=22)
+    sl = _slots(net, 2, (2, 4), 3, 6, (2, 11), seed=23)
+    db = train.DeviceBatch(synth.training_batch(sl, 4))
+    keep = train.Trainer(net, W, Wc, gamma=0.5, recompute=False)
+    rec = train.Trainer(net, W, Wc, gamma=0.5, recompute=True)
+    a, b = keep.loss_and_grad(db), rec.loss_and_grad(db)
+    assert not keep.recomputing and rec.recomputing
+    # the forward is the same launch sequence; only the FP64 atomic loss sums may round differently
+    assert np.allclose([a["loss"]] + a["bce"] + a["mse"], [b["loss"]] + b["bce"] + b["mse"], rtol=1e-12, atol=0)
+    ga, gb = keep.grads(), rec.grads()
+    for name, ref in ga.items():
+        assert np.linalg.norm(gb[name] - ref) <= 1e-5 * max(np.linalg.norm(ref), 1e-30), name
+    n, U, S = 3, 2, 72
+    full, small = keep.activation_bytes(n, U, S, False), keep.activation_bytes(n, U, S, True)
+    assert small < full
+    # the saving is exactly the 3 (K R - 1) conv activation tensors
+    assert full - small == 4 * n * U * 14 * S * net.channels * 3 * (net.iterations * net.res_blocks - 1)
+    auto = train.Trainer(net, W, Wc, gamma=0.5, memory_fraction=1e-12)
+    assert abs(auto.loss_and_grad(db)["loss"] - a["loss"]) <= 1e-12 * a["loss"] and auto.recomputing
+    # graph-captured steps with recompute follow the eager steps
+    tb = synth.training_batch(sl, 4)
+    e1 = train.Trainer(net, W, Wc, gamma=0.5, lr=1e-2, recompute=True)
+    g1 = train.Trainer(net, W, Wc, gamma=0.5, lr=1e-2, recompute=True)
+    for _ in range(3):
+        x, y = e1.step(train.DeviceBatch(tb)), g1.graph_step(tb)
+        assert abs(x["loss"] - y["loss"]) < 1e-5 * abs(x["loss"])
+
+
 # ----------------------------------------------------------------------------
 # BF16 tensor-core compute
 # ----------------------------------------------------------------------------
