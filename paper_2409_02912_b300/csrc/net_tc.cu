@@ -35,6 +35,7 @@ struct Op<__nv_bfloat16> {
   static constexpr uint32_t fmt = 1;
   static constexpr bool split = true;
   __device__ static __forceinline__ uint32_t pack(float a, float b) { return tc::pack_bf16x2(a, b); }
+  __device__ static __forceinline__ uint32_t pack_relu(float a, float b) { return tc::pack_relu_bf16x2(a, b); }
   __device__ static __forceinline__ float2 unpack(uint32_t w) { return tc::unpack_bf16x2(w); }
 };
 template <>
@@ -45,6 +46,7 @@ struct Op<__half> {
     __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
   }
+  __device__ static __forceinline__ uint32_t pack_relu(float a, float b) { return tc::pack_relu_f16x2(a, b); }
   __device__ static __forceinline__ float2 unpack(uint32_t w) {
     return __half22float2(*reinterpret_cast<__half2*>(&w));
   }
@@ -496,13 +498,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
       const float* wt = vec + 192 + 32 * hc;
       const float* wf = vec + 256 + 32 * hc;
       unsigned char* rowp = sm + MpL::XCH + r * 128;
+      const float2 pt2 = make_float2(pt, pt), pf2 = make_float2(pf, pf);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         float o[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
+        for (int e = 0; e < 8; e += 2) {  // packed: (acc + b) + pt w_t + pf w_f per channel pair
           const int cc = 8 * k + e;
-          o[e] = acc[cc] + bb[cc] + pt * wt[cc] + pf * wf[cc];
+          float2 x = tc::fadd2(make_float2(acc[cc], acc[cc + 1]), make_float2(bb[cc], bb[cc + 1]));
+          x = tc::ffma2(pt2, make_float2(wt[cc], wt[cc + 1]), x);
+          x = tc::ffma2(pf2, make_float2(wf[cc], wf[cc + 1]), x);
+          o[e] = x.x;
+          o[e + 1] = x.y;
         }
         const int kk = 4 * hc + k;
         *reinterpret_cast<uint4*>(rowp + ((kk ^ (r & 7)) << 4)) = pack8<T>(o);
@@ -783,12 +790,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
       }
       if (rt < NRX_SYMBOLS) {
         uint4* dst = reinterpret_cast<uint4*>(sm + L::ZB + (rt * L::MW + rcol) * 128);
+        if (inside) {  // ReLU(v + b1): packed adds, one ReLU-and-round conversion per pair
+          const float4* b4 = reinterpret_cast<const float4*>(sb1);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          float f[8];
+          for (int k = 0; k < 8; ++k) {
+            uint32_t w[4];
 #pragma unroll
-          for (int z8 = 0; z8 < 8; ++z8) f[z8] = inside ? fmaxf(v[k * 8 + z8] + sb1[k * 8 + z8], 0.f) : 0.f;
-          dst[k ^ (rt & 7)] = pack8<T>(f);
+            for (int j = 0; j < 2; ++j) {
+              const float4 bb = b4[2 * k + j];
+              const float* x = v + 8 * k + 4 * j;
+              const float2 lo = tc::fadd2(make_float2(x[0], x[1]), make_float2(bb.x, bb.y));
+              const float2 hi = tc::fadd2(make_float2(x[2], x[3]), make_float2(bb.z, bb.w));
+              w[2 * j] = Op<T>::pack_relu(lo.x, lo.y);
+              w[2 * j + 1] = Op<T>::pack_relu(hi.x, hi.y);
+            }
+            dst[k ^ (rt & 7)] = make_uint4(w[0], w[1], w[2], w[3]);
+          }
+        } else {  // zero padding of DW2 outside the grid
+#pragma unroll
+          for (int k = 0; k < 8; ++k) dst[k] = make_uint4(0, 0, 0, 0);
         }
       }
     }
@@ -812,7 +832,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
         dw_2col(
             k2, make_float2(0.f, 0.f), [&](int ti, int k) { return Op<T>::unpack(load(ti, k)); },
             [](float2 a, float2 b, float2 c2) { return tc::ffma2(a, b, c2); },
-            [&](int t, int o, float2 v) { store(t, o, Op<T>::pack(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f))); });
+            [&](int t, int o, float2 v) { store(t, o, Op<T>::pack_relu(v.x, v.y)); });
       } else {
         __half2 k2[9];
 #pragma unroll
@@ -856,10 +876,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
       if (rt < NRX_SYMBOLS && rcol < L::TW) {
         const int sr = rcol * NRX_SYMBOLS + rt;
         float4* dst = reinterpret_cast<float4*>(sr < 128 ? sm + L::A + sr * 256 : sm + L::ZB + (sr - 128) * 256);
+        const float4* b4 = reinterpret_cast<const float4*>(sb2);
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-          dst[k ^ (sr & 7)] = make_float4(v[4 * k] + sb2[4 * k], v[4 * k + 1] + sb2[4 * k + 1],
-                                          v[4 * k + 2] + sb2[4 * k + 2], v[4 * k + 3] + sb2[4 * k + 3]);
+        for (int k = 0; k < 16; ++k) {
+          const float4 bb = b4[k];
+          const float2 lo = tc::fadd2(make_float2(v[4 * k], v[4 * k + 1]), make_float2(bb.x, bb.y));
+          const float2 hi = tc::fadd2(make_float2(v[4 * k + 2], v[4 * k + 3]), make_float2(bb.z, bb.w));
+          dst[k ^ (sr & 7)] = make_float4(lo.x, lo.y, hi.x, hi.y);
+        }
       }
     }
     tc::tc_fence_before();
@@ -890,14 +914,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
         const uint32_t sw[4] = {sq[it].x, sq[it].y, sq[it].z, sq[it].w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const float2 f = Op<T>::unpack(rw[k]);
-          o[2 * k] += f.x;
-          o[2 * k + 1] += f.y;
-          if (last) {
-            const float2 g2 = Op<T>::unpack(sw[k]);
-            o[2 * k] += g2.x;
-            o[2 * k + 1] += g2.y;
-          }
+          float2 acc = tc::fadd2(make_float2(o[2 * k], o[2 * k + 1]), Op<T>::unpack(rw[k]));
+          if (last) acc = tc::fadd2(acc, Op<T>::unpack(sw[k]));
+          o[2 * k] = acc.x;
+          o[2 * k + 1] = acc.y;
         }
         *reinterpret_cast<uint4*>(out + tbase + out_off[it]) = pack8<T>(o);
       }

@@ -280,5 +280,19 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 __device__ __forceinline__ float2 unpack_bf16x2(uint32_t w) {
   return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
 }
+// max(x, 0) of a pair, rounded to nearest into one packed bf16x2 / f16x2 word
+// (low half = lo) by a single conversion.
+__device__ __forceinline__ uint32_t pack_relu_bf16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+__device__ __forceinline__ uint32_t pack_relu_f16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+// a + b on a pair (one packed FP32 instruction; a * 1 + b rounds once, like an add).
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return ffma2(a, make_float2(1.f, 1.f), b); }
 
 }  // namespace tc
