@@ -14,6 +14,7 @@ of the same workload per step).
 from __future__ import annotations
 
 import argparse
+import glob
 import hashlib
 import json
 import os
@@ -209,19 +210,29 @@ def run_reference(args, rank, world):
 
 
 def traffic_for(kernel: str, precision: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
-    kernel source has not changed since the capture."""
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if
+    neither the kernel source nor a header of the CUDA sources has changed
+    since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))[f"{kernel}/{precision}"]
     except (OSError, KeyError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_2409_02912_b300", "csrc", rec["source"])
+    return rec["bytes_per_launch"] if kernel_source_sha(rec["source"]) == rec["sha256"] else None
+
+
+def kernel_source_sha(source: str):
+    """SHA-256 over a kernel's .cu file and every header of the CUDA sources."""
+    csrc = os.path.join(ROOT, "paper_2409_02912_b300", "csrc")
+    files = [os.path.join(csrc, source)] + sorted(glob.glob(os.path.join(csrc, "*.cuh")) +
+                                                  glob.glob(os.path.join(csrc, "*.h")))
+    h = hashlib.sha256()
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        for f in files:
+            h.update(open(f, "rb").read())
     except OSError:
         return None
-    return rec["bytes_per_launch"] if sha == rec["sha256"] else None
+    return h.hexdigest()
 
 
 def run_ours(args, rank, world, local):

@@ -52,15 +52,15 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for the phase of `parity` to complete by polling; gives up after
+// Wait for the phase of `parity` to complete (try_wait suspends the thread in
+// hardware until the phase flips or a short system limit); gives up after
 // ~`limit_ns` (or 2^28 polls).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = 1000000000ull) {
-  if (mbar_test_wait(bar, parity)) return true;
+  if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t i = 1; i < (1u << 28); ++i) {
-    __nanosleep(32);  // yield issue slots to the other warps while the MMAs run
-    if (mbar_test_wait(bar, parity)) return true;
-    if ((i & 255) == 0 && globaltimer() - t0 > limit_ns) return false;
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 15) == 0 && globaltimer() - t0 > limit_ns) return false;
   }
   return false;
 }
