@@ -20,7 +20,7 @@ from __future__ import annotations
 
 import dataclasses
 import struct
-from typing import Dict, List, Sequence
+from typing import Dict, List, Optional, Sequence
 
 import numpy as np
 
@@ -134,14 +134,16 @@ WORKLOADS: Dict[str, Workload] = {
 }
 
 
-def draw_slot_config(w: Workload, rng: np.random.Generator) -> SlotConfig:
-    """Draw one slot's per-slot parameters from the workload's distributions."""
-    bits = tuple(int(rng.choice(w.mcs_choices)) for _ in range(w.num_users))
+def draw_slot_config(w: Workload, rng: np.random.Generator, num_users: Optional[int] = None) -> SlotConfig:
+    """Draw one slot's per-slot parameters from the workload's distributions
+    (``num_users`` active users, default all of the workload's)."""
+    U = w.num_users if num_users is None else num_users
+    bits = tuple(int(rng.choice(w.mcs_choices)) for _ in range(U))
     snr = float(rng.uniform(*w.snr_db_range)) if w.snr_db_range[0] != w.snr_db_range[1] \
         else float(w.snr_db_range[0])
     ds = float(rng.uniform(*w.delay_spread_range_s))
     fd = float(rng.uniform(*w.doppler_range_hz))
-    return SlotConfig(num_prb=w.num_prb, num_users=w.num_users, num_rx_ant=w.num_rx_ant,
+    return SlotConfig(num_prb=w.num_prb, num_users=U, num_rx_ant=w.num_rx_ant,
                       dmrs_symbols=tuple(w.dmrs_symbols), bits_per_symbol=bits, snr_db=snr,
                       num_taps=w.num_taps, delay_spread_s=ds, doppler_hz=fd, ula=w.ula)
 
@@ -411,12 +413,21 @@ def snr_offset_db(bits_per_symbol: Sequence[int]) -> float:
     return 3.0 * (m - 2.0) / 2.0 + 1.0 * (len(bits_per_symbol) - 1)
 
 
-def training_slot(w: Workload, rng: np.random.Generator) -> Slot:
+def draw_active_users(num_users: int, rng: np.random.Generator) -> int:
+    """Number of active users of one training batch, 1 <= U_A <= U, from a
+    triangular distribution (Sec. II-B).  The paper does not give its shape;
+    this build's reading is the discrete distribution rising to U,
+    P(U_A = k) = 2 k / (U (U + 1))."""
+    k = np.arange(1, num_users + 1, dtype=np.float64)
+    return int(rng.choice(np.arange(1, num_users + 1), p=k / k.sum()))
+
+
+def training_slot(w: Workload, rng: np.random.Generator, num_users: Optional[int] = None) -> Slot:
     """One training sample: an i.i.d. uniform modulation order per user from
     ``w.mcs_choices`` (random MCS-to-user association, Sec. IV-A), SNR uniform
     in ``w.snr_db_range`` plus ``snr_offset_db``, channel draws as
-    ``draw_slot_config``."""
-    c = draw_slot_config(w, rng)
+    ``draw_slot_config``; ``num_users`` active users (default all)."""
+    c = draw_slot_config(w, rng, num_users)
     c = dataclasses.replace(c, snr_db=c.snr_db + snr_offset_db(c.bits_per_symbol))
     return make_slot(c, rng)
 
@@ -656,10 +667,10 @@ class SimSlot:
     bits_per_symbol: tuple
 
 
-def sim_slot_params(w: Workload, rng: np.random.Generator) -> SimSlot:
+def sim_slot_params(w: Workload, rng: np.random.Generator, num_users: Optional[int] = None) -> SimSlot:
     """Training-sample parameters as ``training_slot`` draws them (random MCS
     association, SNR with the offsets of Sec. IV-A, delay spread, Doppler)."""
-    c = draw_slot_config(w, rng)
+    c = draw_slot_config(w, rng, num_users)
     snr = c.snr_db + snr_offset_db(c.bits_per_symbol)
     return SimSlot(noise_var=float(np.float32(10.0 ** (-snr / 10.0))), delay_spread_s=float(np.float32(c.delay_spread_s)),
                    doppler_hz=float(np.float32(c.doppler_hz)), num_taps=w.num_taps, ula=w.ula,

@@ -16,6 +16,7 @@ trained network exports directly as a weight blob for ``nrx_create``.
 """
 from __future__ import annotations
 
+import collections
 import ctypes
 import math
 import struct
@@ -181,13 +182,12 @@ class Trainer:
         self.m1 = torch.zeros_like(self.w)
         self.m2 = torch.zeros_like(self.w)
         self.t = 0
-        self._bufs: Dict[tuple, dict] = {}
+        self._bufs: "collections.OrderedDict[tuple, dict]" = collections.OrderedDict()
         self.loss_dev = torch.zeros(2 * net.iterations, dtype=torch.float64, device=dev)
         self.lr_t_dev = torch.zeros(1, dtype=torch.float32, device=dev)
         self._lr_host = torch.zeros(1, dtype=torch.float32).pin_memory()
-        self._graph = None
-        self._graph_shape = None
-        self._static = None
+        # captured steps: key -> (graph, its device batch, key of the buffers it uses)
+        self._graphs: Dict[tuple, tuple] = {}
 
     # -- weights ------------------------------------------------------------
     def _wp(self, name: str) -> int:
@@ -252,16 +252,22 @@ class Trainer:
         free, _ = self.torch.cuda.mem_get_info()
         return self.activation_bytes(n, U, S, False) > self.memory_fraction * free
 
+    MAX_SHAPES = 4  # batch shapes kept resident (e.g. one per number of active users)
+
     def _buffers(self, n, U, S):
         key = (n, U, S)
         if key in self._bufs:
+            self._bufs.move_to_end(key)
+            self.recomputing = self._bufs[key]["rc"]
             return self._bufs[key]
         torch = self.torch
         net = self.net
         C, F, R, K = net.channels, net.in_features, net.res_blocks, net.iterations
         M = n * U * 14 * S
-        self._bufs = {}  # release the previous shape (and the graph that uses it) before sizing this one
-        self._graph, self._graph_shape = None, None
+        while len(self._bufs) >= self.MAX_SHAPES:  # drop the oldest shape and the graphs that use it
+            old, _ = self._bufs.popitem(last=False)
+            for gk in [gk for gk, ent in self._graphs.items() if ent[2] == old]:
+                del self._graphs[gk]
         rc = self._use_recompute(n, U, S)
         self.recomputing = rc
         e = lambda w: torch.empty((M, w), dtype=torch.float32, device="cuda")  # noqa: E731
@@ -271,7 +277,7 @@ class Trainer:
                 return [[t] * R for _ in range(K)]
             return [[e(C) for _ in range(R)] for _ in range(K)]
 
-        b = {"x": e(F), "P0": e(C), "S": [e(C) for _ in range(K + 1)],
+        b = {"rc": rc, "x": e(F), "P0": e(C), "S": [e(C) for _ in range(K + 1)],
              "h1": [e(C) for _ in range(K)], "msg": [e(C) for _ in range(K)], "a": [e(C) for _ in range(K)],
              "z": [[e(C) for _ in range(R + 1)] for _ in range(K)],
              "d1": conv(), "p1": conv(), "d2": conv(),
@@ -284,7 +290,7 @@ class Trainer:
             b.update({"P0h": [e(C) for _ in H], "S0h": [e(C) for _ in H],
                       "r1h": [[e(C) for _ in H] for _ in range(K)], "lh": [[e(m) for m in H] for _ in range(K)],
                       "glh": [e(m) for m in H], "gSh": e(C)})
-        self._bufs = {key: b}  # keep one shape resident
+        self._bufs[key] = b
         return b
 
     # -- forward / backward -------------------------------------------------
@@ -406,7 +412,7 @@ class Trainer:
             for r in reversed(range(R)):
                 bq = f"{q}blk{r}."
                 d1, p1, d2 = p(bf["d1"][k][r]), p(bf["p1"][k][r]), p(bf["d2"][k][r])
-                if self.recomputing:  # rebuild this block's conv activations from its input
+                if bf["rc"]:  # rebuild this block's conv activations from its input
                     zr = p(bf["z"][k][r])
                     ops.dw3(planes, S, C, zr, wp(bq + "dw1"), d1)
                     dense(d1, C, bq + "pw1", C, C, p1, relu=True)
@@ -483,46 +489,44 @@ class Trainer:
 
     def graph_step(self, tb) -> Dict[str, List[float]]:
         """``step`` through a CUDA graph of the whole launch sequence, captured
-        on the first call (per batch shape) and replayed after, so the host
+        on the first call per batch shape and replayed after, so the host
         issues one launch per step instead of a few hundred.  ``tb`` is a host
-        ``synth.TrainingBatch`` (uploaded into fixed device buffers) or a
-        ``DeviceBatch`` filled in place (e.g. by ``GpuSimulator``), which must
-        then be the same object at every call."""
-        torch = self.torch
+        ``synth.TrainingBatch`` (uploaded into fixed device buffers of its
+        shape) or a ``DeviceBatch`` filled in place (e.g. by ``GpuSimulator``;
+        one graph per such object).  Graphs of up to ``MAX_SHAPES`` batch
+        shapes stay resident, so batches with different numbers of active
+        users alternate without recapture."""
         if isinstance(tb, DeviceBatch):
-            if self._graph is None or self._static is not tb:
-                self._graph = None
-                self._static = tb
-                self._graph_shape = None
-                self.step(tb)
-                self._capture()
+            key = ("device", id(tb))
+            ent = self._graphs.get(key)
+            if ent is None or ent[1] is not tb:
+                self.step(tb)  # eager step: the buffers exist before capture
+                self._capture(key, tb)
                 return self._read_loss()
-            self._advance()
-            self._graph.replay()
-            return self._read_loss()
-        shape = (tb.y.shape, tb.m_u.shape, tb.bits.shape, tb.dmrs_symbols)
-        if self._graph is None or self._graph_shape != shape:
-            self._graph = None
-            self._static = DeviceBatch(tb)
-            self._graph_shape = shape
-            self.step(self._static)  # eager step: the buffers exist before capture
-            self._capture()
-            return self._read_loss()
-        self._static.load(tb)
+        else:
+            key = ("host", tb.y.shape, tb.m_u.shape, tb.bits.shape, tuple(tb.dmrs_symbols))
+            ent = self._graphs.get(key)
+            if ent is None:
+                static = DeviceBatch(tb)
+                self.step(static)
+                self._capture(key, static)
+                return self._read_loss()
+            ent[1].load(tb)
+        self._buffers(ent[1].n, ent[1].U, ent[1].S)  # mark the shape as recently used
         self._advance()
-        self._graph.replay()
+        ent[0].replay()
         return self._read_loss()
 
-    def _capture(self):
+    def _capture(self, key, static: "DeviceBatch"):
         torch = self.torch
         g = torch.cuda.CUDAGraph()
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
             with torch.cuda.graph(g, stream=side):
-                self._enqueue(self._static, side.cuda_stream, adam=True)
+                self._enqueue(static, side.cuda_stream, adam=True)
         torch.cuda.current_stream().wait_stream(side)
-        self._graph = g
+        self._graphs[key] = (g, static, (static.n, static.U, static.S))
 
     @staticmethod
     def _ok(st, what):
@@ -630,22 +634,32 @@ class GpuSimulator:
     offsets, delay spread, Doppler) from ``synth.sim_slot_params`` on the host,
     every per-RE draw from Philox on the device."""
 
-    def __init__(self, workload: synth.Workload, seed: int = 7, param_seed: int = 11):
+    def __init__(self, workload: synth.Workload, seed: int = 7, param_seed: int = 11, active_users: bool = False):
         import torch
         w = workload
         self.w = w
         self.seed = seed
         self.batch_index = 0
+        self.active_users = active_users  # draw U_A per batch (synth.draw_active_users)
         self.rng = np.random.Generator(np.random.PCG64(param_seed))
-        self.batch = DeviceBatch.empty(w.batch, w.num_users, w.num_rx_ant, w.num_prb, w.net.m_max, w.dmrs_symbols)
+        self.batches: Dict[int, DeviceBatch] = {}  # one device batch per number of active users
+        self.batch = self._batch(w.num_users)
         nbytes = load().nrx_train_sim_scratch_bytes(w.batch, w.num_users, w.num_rx_ant, synth.SIM_MAX_TAPS)
         self.scratch = torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device="cuda")
         self._ds = np.ascontiguousarray(np.asarray(w.dmrs_symbols, dtype=np.int32))
 
-    def draw(self, stream=None) -> DeviceBatch:
-        """Simulate the next batch into ``self.batch`` (asynchronous)."""
+    def _batch(self, U: int) -> DeviceBatch:
         w = self.w
-        params = [synth.sim_slot_params(w, self.rng) for _ in range(w.batch)]
+        if U not in self.batches:
+            self.batches[U] = DeviceBatch.empty(w.batch, U, w.num_rx_ant, w.num_prb, w.net.m_max, w.dmrs_symbols)
+        return self.batches[U]
+
+    def draw(self, stream=None) -> DeviceBatch:
+        """Simulate the next batch (asynchronous) into the device batch of its
+        number of active users, which is returned (and kept as ``self.batch``)."""
+        w = self.w
+        U = synth.draw_active_users(w.num_users, self.rng) if self.active_users else w.num_users
+        params = [synth.sim_slot_params(w, self.rng, U) for _ in range(w.batch)]
         arr = (nrx_sim_slot * w.batch)()
         for i, sp in enumerate(params):
             arr[i].noise_var = sp.noise_var
@@ -655,8 +669,8 @@ class GpuSimulator:
             arr[i].ula = int(sp.ula)
             for u, m in enumerate(sp.bits_per_symbol):
                 arr[i].bits_per_symbol[u] = m
-        b = self.batch
-        st = load().nrx_train_simulate(w.batch, arr, w.num_users, w.num_rx_ant, w.num_prb, len(w.dmrs_symbols),
+        b = self.batch = self._batch(U)
+        st = load().nrx_train_simulate(w.batch, arr, U, w.num_rx_ant, w.num_prb, len(w.dmrs_symbols),
                                        self._ds.ctypes.data, w.net.m_max, self.seed, self.batch_index,
                                        self.scratch.data_ptr(), b.y.data_ptr(), b.dmrs.data_ptr(), b.bits.data_ptr(),
                                        b.m_u.data_ptr(), b.h.data_ptr(), nrx._stream_ptr(stream))
@@ -673,18 +687,21 @@ class GpuSimulator:
 
 
 def _make_batch(args):
-    """Worker: one seeded training batch (runs in a spawned process)."""
-    wl, seed = args
+    """Worker: one seeded training batch (runs in a spawned process); with
+    ``active`` its number of active users is drawn (synth.draw_active_users)."""
+    wl, seed, active = args
     rng = np.random.Generator(np.random.PCG64(seed))
-    return synth.training_batch([synth.training_slot(wl, rng) for _ in range(wl.batch)], wl.net.m_max)
+    U = synth.draw_active_users(wl.num_users, rng) if active else wl.num_users
+    return synth.training_batch([synth.training_slot(wl, rng, U) for _ in range(wl.batch)], wl.net.m_max)
 
 
 def fit(workload: synth.Workload, seconds: float, lr: float = 2e-3, lr_final: float = 5e-5, gamma: float = 1.0,
         seed: int = 1, resume: Optional[str] = None, workers: Optional[int] = None, log_every: int = 2000,
         trainer: Optional[Trainer] = None, precision: str = "fp32", simulator: str = "cpu",
-        recompute: Optional[bool] = None) -> Trainer:
+        recompute: Optional[bool] = None, active_users: bool = True) -> Trainer:
     """Train for a wall-clock budget on fresh random batches of ``workload``
-    (random MCS association and SNR offsets, Sec. IV-A), with an exponential
+    (random MCS association and SNR offsets, Sec. IV-A; with ``active_users``
+    the number of active users drawn per batch, Sec. II-B), with an exponential
     learning-rate decay from lr to lr_final over the budget.  Batches are
     generated by a pool of spawned CPU workers, at most 48 ahead of the GPU;
     each step is one CUDA-graph replay.  The read-out layers start at zero
@@ -703,7 +720,7 @@ def fit(workload: synth.Workload, seconds: float, lr: float = 2e-3, lr_final: fl
     if resume:
         trainer.restore(resume)
     if simulator == "gpu":  # every batch drawn on the device, no host workers
-        sim = GpuSimulator(workload, seed=seed * 1_000_003 + trainer.t)
+        sim = GpuSimulator(workload, seed=seed * 1_000_003 + trainer.t, active_users=active_users)
         t0 = time.time()
         hist = []
         while time.time() - t0 < seconds:
@@ -717,13 +734,13 @@ def fit(workload: synth.Workload, seconds: float, lr: float = 2e-3, lr_final: fl
     pool = mp.get_context("spawn").Pool(nw)
     try:
         seed0 = 1_000_003 * (seed + 1) + trainer.t
-        window = [pool.apply_async(_make_batch, ((workload, seed0 + i),)) for i in range(48)]
+        window = [pool.apply_async(_make_batch, ((workload, seed0 + i, active_users),)) for i in range(48)]
         nxt = seed0 + 48
         t0 = time.time()
         hist = []
         while time.time() - t0 < seconds:
             tb = window.pop(0).get(timeout=300)
-            window.append(pool.apply_async(_make_batch, ((workload, nxt),)))
+            window.append(pool.apply_async(_make_batch, ((workload, nxt, active_users),)))
             nxt += 1
             frac = min(1.0, (time.time() - t0) / seconds)
             trainer.lr = lr * (lr_final / lr) ** frac
@@ -755,6 +772,8 @@ def main(argv=None):
                     help="draw batches with CPU workers (synth) or on the GPU (nrx_train_simulate)")
     ap.add_argument("--recompute", default="auto", choices=("auto", "on", "off"),
                     help="rebuild the conv activations in the reverse pass (auto: when memory asks)")
+    ap.add_argument("--all-users", action="store_true",
+                    help="every batch with all users active (default: U_A drawn per batch, Sec. II-B)")
     ap.add_argument("--checkpoint", default=None, help="write an .npz checkpoint here")
     ap.add_argument("--out", required=True, help="write the inference weight blob here")
     a = ap.parse_args(argv)
@@ -763,7 +782,8 @@ def main(argv=None):
     wl = dataclasses_replace(base, num_prb=a.prb, batch=a.batch, snr_db_range=snr,
                              mcs_choices=tuple(int(v) for v in a.mcs.split(",")))
     tr = fit(wl, a.seconds, lr=a.lr, lr_final=a.lr_final, gamma=a.gamma, resume=a.resume, precision=a.precision,
-             simulator=a.simulator, recompute={"auto": None, "on": True, "off": False}[a.recompute])
+             simulator=a.simulator, recompute={"auto": None, "on": True, "off": False}[a.recompute],
+             active_users=not a.all_users)
     if a.checkpoint:
         tr.save(a.checkpoint)
     with open(a.out, "wb") as f:

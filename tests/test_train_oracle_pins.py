@@ -173,6 +173,28 @@ def test_snr_offset_orders_samples_by_mcs_and_users():
     assert synth.snr_offset_db((2, 2, 2)) > synth.snr_offset_db((2, 2))
 
 
+def test_active_users_follow_the_triangular_distribution():
+    """U_A per batch (Sec. II-B): P(U_A = k) = 2k / (U (U+1)) on 1..U (this
+    build's reading of the triangular distribution), and the drawn number of
+    users reaches the slots of a worker batch."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    for U in (1, 2, 4):
+        n = 40_000
+        draws = np.array([synth.draw_active_users(U, rng) for _ in range(n)])
+        assert draws.min() >= 1 and draws.max() <= U
+        want = 2.0 * np.arange(1, U + 1) / (U * (U + 1))
+        got = np.bincount(draws, minlength=U + 1)[1:] / n
+        assert np.all(np.abs(got - want) <= 4.0 * np.sqrt(want * (1 - want) / n) + 1e-12), (U, got, want)
+    from paper_2409_02912_b300 import train
+    w = synth.Workload(name="active_check", seed_base=1, batch=3, num_prb=1, num_users=4, num_rx_ant=2,
+                       dmrs_symbols=(2,), mcs_choices=(2, 4), snr_db_range=(0.0, 10.0), num_taps=2,
+                       delay_spread_range_s=(1e-8, 5e-8), doppler_range_hz=(0.0, 10.0), ula=False,
+                       net=synth.NetConfig(num_rx_ant=2, channels=8, res_blocks=1, iterations=1, m_max=4))
+    users = {train._make_batch((w, seed, True)).m_u.shape[1] for seed in range(40)}
+    assert users == {1, 2, 3, 4}
+    assert {train._make_batch((w, seed, False)).m_u.shape[1] for seed in range(5)} == {4}
+
+
 def test_training_batch_layout():
     sl = _slots(U=2, bits=(2, 4), n=2)
     tb = synth.training_batch(sl, m_max=6)
