@@ -234,6 +234,18 @@ nrx_status nrx_dmrs_gold(int32_t n_slots, const int32_t* slot_numbers, int32_t n
  */
 nrx_status nrx_check(nrx_ctx* ctx, void* stream);
 
+/*
+ * Failure-path diagnostic (no fault, no hang): enqueue on `stream` one CTA
+ * whose thread 0 waits, with the same bounded mbarrier wait the tensor-core
+ * kernels use, on a barrier that no thread arrives on.  After `limit_us`
+ * microseconds (1..1,000,000) the wait gives up and the kernel sets the
+ * context's device status word exactly as a real timeout does, so the next
+ * nrx_check returns NRX_ETIMEDOUT (and clears it) and the context stays
+ * usable.  NRX_EUNSUPPORTED for an FP32 context (it has no status word),
+ * NRX_EINVAL for a bad limit.
+ */
+nrx_status nrx_expire_wait(nrx_ctx* ctx, int32_t limit_us, void* stream);
+
 /* Network hyper-parameters of the context: B, C, R, N_it, m_max. */
 nrx_status nrx_get_net(const nrx_ctx* ctx, int32_t* num_rx_ant, int32_t* channels,
                        int32_t* res_blocks, int32_t* iterations, int32_t* m_max);

@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "net_tc.h"
+#include "tc.cuh"
 
 namespace {
 
@@ -325,6 +326,30 @@ nrx_status nrx_check(nrx_ctx* ctx, void* stream) {
     }
   }
   return NRX_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// One bounded wait that cannot succeed: nothing arrives on the barrier.
+__global__ void k_expire_wait(uint64_t limit_ns, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+    if (!tc::mbar_wait(&bar, 0, limit_ns)) atomicExch(err, 1);
+  }
+}
+}  // namespace
+
+extern "C" {
+
+nrx_status nrx_expire_wait(nrx_ctx* ctx, int32_t limit_us, void* stream) {
+  if (!ctx || limit_us < 1 || limit_us > 1000000) return NRX_EINVAL;
+  if (!ctx->d_err) return fail(ctx, NRX_EUNSUPPORTED, "no device status word in an FP32 context");
+  k_expire_wait<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>((uint64_t)limit_us * 1000ull, ctx->d_err);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? NRX_OK : cuda_fail(ctx, e, "k_expire_wait");
 }
 
 nrx_status nrx_profile(nrx_ctx* ctx, int32_t enable) {

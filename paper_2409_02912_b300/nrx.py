@@ -23,7 +23,7 @@ EXPORTED = (
     "nrx_create", "nrx_destroy", "nrx_llr_count", "nrx_detect_batch", "nrx_detect", "lmmse_detect_batch",
     "lmmse_detect", "nrx_detect_batch_host", "nrx_copy_state", "nrx_get_net", "nrx_last_launch_count",
     "nrx_last_error", "nrx_status_string", "nrx_profile", "nrx_profile_read", "nrx_detect_noalloc",
-    "nrx_check", "nrx_dmrs_gold",
+    "nrx_check", "nrx_dmrs_gold", "nrx_expire_wait",
 )
 KERNEL_KINDS = 5
 
@@ -89,6 +89,8 @@ def load() -> ctypes.CDLL:
     lib.nrx_profile_read.restype = ctypes.c_int
     lib.nrx_check.argtypes = [P, P]
     lib.nrx_check.restype = ctypes.c_int
+    lib.nrx_expire_wait.argtypes = [P, I32, P]
+    lib.nrx_expire_wait.restype = ctypes.c_int
     lib.nrx_detect_noalloc.argtypes = [P, P, P, CFG, P, P, P]
     lib.nrx_detect_noalloc.restype = ctypes.c_int
     lib.nrx_dmrs_gold.argtypes = [I32, P, I32, I32, I32, I32, P, P, P]
@@ -173,6 +175,11 @@ class Receiver:
     def nrx_check(self, stream=None):
         """Synchronise and raise on a device-side failure (e.g. NRX_ETIMEDOUT)."""
         self._check(self._lib.nrx_check(self.ctx, _stream_ptr(stream)), "nrx_check")
+
+    def nrx_expire_wait(self, limit_us: int, stream=None):
+        """Enqueue a bounded device wait that runs out (see nrx.h); the next
+        ``nrx_check`` raises NRX_ETIMEDOUT."""
+        self._check(self._lib.nrx_expire_wait(self.ctx, int(limit_us), _stream_ptr(stream)), "nrx_expire_wait")
 
     def nrx_profile(self, enable: bool):
         self._check(self._lib.nrx_profile(self.ctx, int(bool(enable))), "nrx_profile")
