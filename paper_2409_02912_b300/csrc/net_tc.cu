@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
 //   PW1 MMA -> TMEM [0,128); epilogue +b1, ReLU, zero outside the grid -> P1
 //   DW2 + ReLU on 14 columns -> A (224 rows)
 //   PW2 MMA -> TMEM [128,256); epilogue +b2 + residual -> z_out, or S += (last)
-// P1 [t][16 columns][64 ch] stores 16-byte chunk k of a row at k ^ (t & 7).
+// P1 [t][16 columns][64 ch] has a symbol stride of 16 rows + 16 bytes (no swizzle).
 // ---------------------------------------------------------------------------
 template <typename P>
 struct BlkLayout {
@@ -562,6 +562,9 @@ struct BlkLayout {
   static constexpr int TOTAL = INBAR + 16;
   static constexpr int DYN = TOTAL + 1024;
   static constexpr uint32_t kInBytes = NRX_SYMBOLS * IW * 128;  // the TMA box [14][IW][64] of 16-bit
+  // P1 [14][MW][64] over ZB: symbol stride MW rows + 16 bytes (bank shift between symbols), no swizzle
+  static constexpr int P1T = MW * 128 + 16;
+  static_assert(NRX_SYMBOLS * P1T <= NRX_SYMBOLS * IW * 128, "P1 fits in the input tile's space");
 };
 
 // Sliding 3x3 depthwise for two adjacent output columns (o = 0, 1) of one
@@ -737,10 +740,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
       const int e = 2 * cg;
       const uint32_t* col = zw + e * 32 + cp;
       unsigned char* dst = a_tile + e * 2048;
-      auto store = [&](int t, int o, uint32_t word) {
-        *reinterpret_cast<uint32_t*>(dst + o * 2048 + (t >> 3) * 1024 + (t & 7) * 128 + ((cpc ^ (t & 7)) << 4) +
-                                     cpl * 4) = word;
-      };
+      uint32_t sp[8];  // this lane's word of row j (< 8) of the column's SW128 block, per j
+#pragma unroll
+      for (int j = 0; j < 8; ++j) sp[j] = tc::smem_u32(dst) + j * 128 + ((cpc ^ j) << 4) + cpl * 4;
+      auto store = [&](int t, int o, uint32_t word) { tc::sts32(sp[t & 7] + o * 2048 + (t >> 3) * 1024, word); };
       if constexpr (P::split) {  // BF16 operands: FP32 packed FMAs
         float2 k1[9];
 #pragma unroll
@@ -789,7 +792,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
         for (int k = 0; k < 64; ++k) v[k] *= rs * ssw[k];
       }
       if (rt < NRX_SYMBOLS) {
-        uint4* dst = reinterpret_cast<uint4*>(sm + L::ZB + (rt * L::MW + rcol) * 128);
+        uint4* dst = reinterpret_cast<uint4*>(sm + L::ZB + rt * L::P1T + rcol * 128);
         if (inside) {  // ReLU(v + b1): packed adds, one ReLU-and-round conversion per pair
           const float4* b4 = reinterpret_cast<const float4*>(sb1);
 #pragma unroll
@@ -804,7 +807,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
               w[2 * j] = Op<T>::pack_relu(lo.x, lo.y);
               w[2 * j + 1] = Op<T>::pack_relu(hi.x, hi.y);
             }
-            dst[k ^ (rt & 7)] = make_uint4(w[0], w[1], w[2], w[3]);
+            dst[k] = make_uint4(w[0], w[1], w[2], w[3]);
           }
         } else {  // zero padding of DW2 outside the grid
 #pragma unroll
@@ -818,13 +821,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
     // warps 0..6 compute output columns 2 cg and 2 cg + 1.
     if (cg < L::TW / 2) {
       const int x = 2 * cg;
-      const uint32_t* col = zw + x * 32 + cpl;
+      const uint32_t* col = reinterpret_cast<const uint32_t*>(sm + L::ZB + x * 128) + cp;
       unsigned char* dst = a_tile + x * 2048;
-      auto store = [&](int t, int o, uint32_t word) {
-        *reinterpret_cast<uint32_t*>(dst + o * 2048 + (t >> 3) * 1024 + (t & 7) * 128 + ((cpc ^ (t & 7)) << 4) +
-                                     cpl * 4) = word;
-      };
-      auto load = [&](int ti, int k) { return col[(ti * L::MW + k) * 32 + ((cpc ^ (ti & 7)) << 2)]; };
+      uint32_t sp[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) sp[j] = tc::smem_u32(dst) + j * 128 + ((cpc ^ j) << 4) + cpl * 4;
+      auto store = [&](int t, int o, uint32_t word) { tc::sts32(sp[t & 7] + o * 2048 + (t >> 3) * 1024, word); };
+      auto load = [&](int ti, int k) { return col[(ti * L::P1T + k * 128) / 4]; };
       if constexpr (P::split) {
         float2 k2[9];
 #pragma unroll

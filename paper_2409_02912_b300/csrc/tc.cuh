@@ -292,6 +292,11 @@ __device__ __forceinline__ uint32_t pack_relu_f16x2(float lo, float hi) {
   asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
   return d;
 }
+// 32-bit store to a shared-memory address (state space known: no address
+// conversion, and the caller's precomputed address + constant folds).
+__device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v));
+}
 // a + b on a pair (one packed FP32 instruction; a * 1 + b rounds once, like an add).
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return ffma2(a, make_float2(1.f, 1.f), b); }
 
