@@ -203,14 +203,16 @@ struct MpLayout {
   static constexpr int VEC = WC + wbytes<P>();  // b1, bin, -, pe_t, pe_f, sW1, sWS, sWC: 8 x 64 floats
   static constexpr int RSC = VEC + 8 * 64 * 4;   // E4M3 row scales of A_S and A_G: 2 x 128 floats
   static constexpr int BAR = RSC + (P::fp8 ? 256 * 4 : 0);
-  static constexpr int TOTAL = BAR + 16;
+  static constexpr int INBAR = BAR + 16;  // mbarrier of the S-rows bulk tensor copy (16-bit modes)
+  static constexpr int TOTAL = INBAR + 16;
   static constexpr int DYN = TOTAL + 1024;
 };
 
 template <typename P>
 __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC w,
                                                        const typename P::T* __restrict__ state,
-                                                       typename P::T* __restrict__ z, int nre, int tiles_per_slot) {
+                                                       typename P::T* __restrict__ z, int nre, int tiles_per_slot,
+                                                       const __grid_constant__ CUtensorMap smap) {
   using T = typename P::T;
   using MpL = MpLayout<P>;
   extern __shared__ unsigned char smem_raw[];
@@ -234,10 +236,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
   }
   float* rsc_s = reinterpret_cast<float*>(sm + MpL::RSC);  // row scales of A_S (FP8)
   float* rsc_g = rsc_s + 128;                               // row scales of A_G (FP8)
+  uint64_t* in_bar = reinterpret_cast<uint64_t*>(sm + MpL::INBAR);
+  if (tid == 0) tc::mbar_init(in_bar, 1);  // made visible by the fence and barrier in tc_setup
+  uint32_t in_phase = 0;
+  bool tma_pending = false;
   TcCta c;
   tc_setup(c, reinterpret_cast<uint64_t*>(sm + MpL::BAR), reinterpret_cast<uint32_t*>(sm + MpL::BAR + 8),
            P::fp8 ? 256 : 128);
-  const uint32_t sa_s = tc::smem_u32(sm + MpL::A_S), sa_g = tc::smem_u32(sm + MpL::A_G);
   const uint32_t sw1 = tc::smem_u32(sm + MpL::W1), sws = tc::smem_u32(sm + MpL::WS),
                  swc = tc::smem_u32(sm + MpL::WC);
   const int n_re = NRX_SYMBOLS * S;
@@ -247,12 +252,40 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
   const uint32_t tlane = (uint32_t)(q * 32) << 16;
   bool timed_out = false;
   float* xch = reinterpret_cast<float*>(sm + MpL::XCH);
+  // 16-bit modes: the S rows of a tile ([U][nre][64], zero past the REs) arrive
+  // by one bulk tensor copy with the 128-byte swizzle, i.e. directly in the
+  // SW128 operand layout.  The two 16 KB operand buffers swap roles every
+  // tile: the next tile's S goes into this tile's G buffer as soon as PW2 is
+  // done with it, so the copy overlaps this tile's z epilogue.
+  auto issue_s = [&](int t_next, unsigned char* dst) {
+    tc::mbar_arrive_expect_tx(in_bar, (uint32_t)(U * nre * 128));
+    tc::tma_load_3d(dst, &smap, 0, (t_next % tiles_per_slot) * nre, (t_next / tiles_per_slot) * U, in_bar);
+  };
+  int par = 0;
+  if constexpr (!P::fp8) {
+    if (blockIdx.x < n_tiles) {
+      if (tid == 0) issue_s(blockIdx.x, sm + MpL::A_S);
+      tma_pending = true;
+    }
+  }
 
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int sl = tile / tiles_per_slot;
     const int re0 = (tile % tiles_per_slot) * nre;
-    // S rows -> A_S (SW128), zero for rows beyond the users / REs.
-    {
+    unsigned char* const s_buf = sm + (par ? MpL::A_G : MpL::A_S);
+    unsigned char* const g_buf = sm + (par ? MpL::A_S : MpL::A_G);
+    const uint32_t sa_s = tc::smem_u32(s_buf), sa_g = tc::smem_u32(g_buf);
+    if constexpr (!P::fp8) {  // wait (bounded) for this tile's S rows
+      bool ok = true;
+      if (tid == 0) ok = tc::mbar_wait(in_bar, in_phase);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(w.err, 1);
+        timed_out = true;
+        break;  // tma_pending stays set: the teardown waits for this phase
+      }
+      in_phase ^= 1u;
+      tma_pending = false;
+    } else {  // FP8: S rows -> E4M3 A_S with per-row scales, zero beyond the users / REs
       uint4 v[4];
 #pragma unroll
       for (int it = 0; it < 4; ++it) {
@@ -285,21 +318,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
           const float sc = e4m3_scale(am), inv = 1.f / sc;
           const uint2 q = make_uint2(e4m3x2(f[0] * inv, f[1] * inv) | (e4m3x2(f[2] * inv, f[3] * inv) << 16),
                                      e4m3x2(f[4] * inv, f[5] * inv) | (e4m3x2(f[6] * inv, f[7] * inv) << 16));
-          *reinterpret_cast<uint2*>(sm + MpL::A_S + (row >> 3) * 1024 + (row & 7) * 128 +
+          *reinterpret_cast<uint2*>(s_buf + (row >> 3) * 1024 + (row & 7) * 128 +
                                     (((ch >> 1) ^ (row & 7)) << 4) + (ch & 1) * 8) = q;
           if (ch == 0) rsc_s[row] = sc;
-        } else {
-          *reinterpret_cast<uint4*>(sm + MpL::A_S + (row >> 3) * 1024 + (row & 7) * 128 + ((ch ^ (row & 7)) << 4)) =
-              v[it];
         }
       }
-    }
-    {  // L2 prefetch of the next tile's rows
-      const int nt = tile + gridDim.x;
-      if (nt < n_tiles && tid < 128) {
-        const int nsl = nt / tiles_per_slot, nre0 = (nt % tiles_per_slot) * nre;
-        const int u = tid / nre, j = tid % nre, re = nre0 + j;
-        if (u < U && re < n_re) tc::prefetch_l2(state + (((size_t)nsl * U + u) * n_re + re) * C64);
+      {  // L2 prefetch of the next tile's rows
+        const int nt = tile + gridDim.x;
+        if (nt < n_tiles && tid < 128) {
+          const int nsl = nt / tiles_per_slot, nre0 = (nt % tiles_per_slot) * nre;
+          const int u = tid / nre, j = tid % nre, re = nre0 + j;
+          if (u < U && re < n_re) tc::prefetch_l2(state + (((size_t)nsl * U + u) * n_re + re) * C64);
+        }
       }
     }
     tc::fence_async_smem();
@@ -366,7 +396,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
                 a.w += hv[v].w;
               }
             const int row = u * nre + j;
-            *reinterpret_cast<uint2*>(sm + MpL::A_G + tc::sw128_offset(row, 4 * cq)) =
+            *reinterpret_cast<uint2*>(g_buf + tc::sw128_offset(row, 4 * cq)) =
                 make_uint2(Op<T>::pack(a.x, a.y), Op<T>::pack(a.z, a.w));
           }
         }
@@ -435,13 +465,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
             for (int o = 1; o < 16; o <<= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
             const float sc = e4m3_scale(am), inv = 1.f / sc;
             if (valid) {
-              *reinterpret_cast<uint32_t*>(sm + MpL::A_G + (row >> 3) * 1024 + (row & 7) * 128 +
+              *reinterpret_cast<uint32_t*>(g_buf + (row >> 3) * 1024 + (row & 7) * 128 +
                                            (((cq >> 2) ^ (row & 7)) << 4) + (cq & 3) * 4) =
                   e4m3x2(a.x * inv, a.y * inv) | (e4m3x2(a.z * inv, a.w * inv) << 16);
               if (cq == 0) rsc_g[row] = sc;
             }
           } else if (valid) {
-            *reinterpret_cast<uint2*>(sm + MpL::A_G + tc::sw128_offset(row, 4 * cq)) =
+            *reinterpret_cast<uint2*>(g_buf + tc::sw128_offset(row, 4 * cq)) =
                 make_uint2(Op<T>::pack(a.x, a.y), Op<T>::pack(a.z, a.w));
           }
         }
@@ -460,6 +490,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
     if (!tc_wait(c, w.err)) {
       timed_out = true;
       break;
+    }
+    if constexpr (!P::fp8) {  // both operand buffers are free: the next tile's S into this tile's G buffer
+      const int nt = tile + gridDim.x;
+      if (nt < n_tiles) {
+        if (tid == 0) issue_s(nt, g_buf);
+        tma_pending = true;
+      }
+      par ^= 1;
     }
     // z = acc + b + (U-1) Win_a b2 + PE terms -> 16-bit staging [128][128 B] in
     // the exchange region; 16-byte chunk k of a row stored at k ^ (r & 7)
@@ -529,6 +567,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
     }
     __syncthreads();
   }
+  if (tma_pending && tid == 0) tc::mbar_wait(in_bar, in_phase, 100000000ull);  // let a copy in flight land
   tc_teardown(c, P::fp8 ? 256 : 128, timed_out);
 }
 
@@ -1257,6 +1296,9 @@ nrx_status upload_tc_weights(int mode, int C, int R, int N_it, const std::vector
   return NRX_OK;
 }
 
+template <typename T>
+cudaError_t state_rows_map(CUtensorMap* map, const T* base, int planes, int n_re, int nre, int U);
+
 template <typename P>
 cudaError_t launch_mp_tc(const Geometry& g, const IterWeightsTC& w, const typename P::T* state, typename P::T* z,
                          cudaStream_t st) {
@@ -1266,8 +1308,15 @@ cudaError_t launch_mp_tc(const Geometry& g, const IterWeightsTC& w, const typena
   const int tiles = g.n_slots * tps;
   const int smem = MpLayout<P>::DYN;
   ensure_smem<k_mp_tc<P>>(smem);
+  CUtensorMap smap;
+  memset(&smap, 0, sizeof(smap));
+  if constexpr (!P::fp8) {
+    if (reinterpret_cast<uintptr_t>(state) & 15) return cudaErrorInvalidValue;  // TMA global address alignment
+    const cudaError_t e = state_rows_map(&smap, state, g.n_slots * g.U, NRX_SYMBOLS * g.S, nre, g.U);
+    if (e != cudaSuccess) return e;
+  }
   const int grid = grid_for(smem, 2, tiles);
-  k_mp_tc<P><<<grid, kThreads, smem, st>>>(g, w, state, z, nre, tps);
+  k_mp_tc<P><<<grid, kThreads, smem, st>>>(g, w, state, z, nre, tps, smap);
   return cudaGetLastError();
 }
 
@@ -1301,6 +1350,25 @@ cudaError_t activation_map(CUtensorMap* map, const T* base, int planes, int S, i
       sizeof(T) == 2 && std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const CUresult r = enc(map, dt, 3, const_cast<T*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// 3-D map of the state [planes][n_re][64] for the message-passing tiles: box
+// [U planes][nre REs][64 channels], 128-byte swizzle (the SW128 operand
+// layout), zero fill past the REs.
+template <typename T>
+cudaError_t state_rows_map(CUtensorMap* map, const T* base, int planes, int n_re, int nre, int U) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {64, (cuuint64_t)n_re, (cuuint64_t)planes};
+  const cuuint64_t strides[2] = {64 * sizeof(T), (cuuint64_t)n_re * 64 * sizeof(T)};
+  const cuuint32_t box[3] = {64, (cuuint32_t)nre, (cuuint32_t)U};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUtensorMapDataType dt =
+      std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const CUresult r = enc(map, dt, 3, const_cast<T*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
