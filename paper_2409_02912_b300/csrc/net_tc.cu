@@ -973,8 +973,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
 }
 
 // ---------------------------------------------------------------------------
-// ReadoutLLRs + masking: 128 data REs of one (slot, user) per tile;
-// h = ReLU(S W_o1^T + b) by MMA, then the m_u outputs on the CUDA cores.
+// ReadoutLLRs + masking: 128 subcarriers of one data symbol of one (slot,
+// user) per tile (the last chunk of a symbol ragged); h = ReLU(S W_o1^T + b)
+// by MMA, then the m_u outputs on the CUDA cores.  In the 16-bit modes the
+// tile's state rows arrive by one bulk tensor copy with the 128-byte swizzle
+// (the operand layout, zero past the symbol's end), and the next tile's copy
+// is issued as soon as the MMA has read the tile, overlapping the epilogue.
 // ---------------------------------------------------------------------------
 template <typename P>
 struct RoLayout {
@@ -985,14 +989,15 @@ struct RoLayout {
   static constexpr int B2 = B1 + 256;
   static constexpr int SC = B2 + 64;   // E4M3: weight scales [64], row scales [128]
   static constexpr int BAR = SC + 192 * 4;
-  static constexpr int TOTAL = BAR + 16;
+  static constexpr int INBAR = BAR + 16;
+  static constexpr int TOTAL = INBAR + 16;
   static constexpr int DYN = TOTAL + 1024;
 };
 
 template <typename P>
 __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, ReadoutWeightsTC w,
                                                     const typename P::T* __restrict__ state, float* __restrict__ llr,
-                                                    int tiles_per_su) {
+                                                    int tiles_per_su, const __grid_constant__ CUtensorMap rmap) {
   using T = typename P::T;
   using L = RoLayout<P>;
   extern __shared__ unsigned char smem_raw[];
@@ -1003,16 +1008,33 @@ __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, R
   float* sb2 = reinterpret_cast<float*>(sm + L::B2);
   float* ssc = reinterpret_cast<float*>(sm + L::SC);  // [64] weight scales, then [128] row scales
   int loaded = -1;  // Var-IO head whose weights are in shared memory
+  uint64_t* in_bar = reinterpret_cast<uint64_t*>(sm + L::INBAR);
+  if (tid == 0) tc::mbar_init(in_bar, 1);  // made visible by the fence and barrier in tc_setup
+  uint32_t in_phase = 0;
+  bool tma_pending = false;
   TcCta c;
   tc_setup(c, reinterpret_cast<uint64_t*>(sm + L::BAR), reinterpret_cast<uint32_t*>(sm + L::BAR + 8), 64);
   const uint32_t sa = tc::smem_u32(sm + L::A), sw1 = tc::smem_u32(sm + L::W1);
   const int U = g.U, S = g.S;
   const int n_tiles = g.n_slots * U * tiles_per_su;
+  const int chunks = (S + 127) / 128;  // 128-subcarrier chunks per data symbol
   const int row = warp * 32 + lane;
   bool timed_out = false;
+  auto issue_rows = [&](int t_next) {
+    const int su_n = t_next / tiles_per_su, k = t_next % tiles_per_su;
+    tc::mbar_arrive_expect_tx(in_bar, 128u * 128u);
+    tc::tma_load_3d(sm + L::A, &rmap, 0, (k % chunks) * 128, su_n * NRX_SYMBOLS + g.data_t[k / chunks], in_bar);
+  };
+  if constexpr (!P::fp8) {
+    if (blockIdx.x < n_tiles) {
+      if (tid == 0) issue_rows(blockIdx.x);
+      tma_pending = true;
+    }
+  }
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int su = tile / tiles_per_su, sl = su / U, u = su % U;
-    const int r0 = (tile % tiles_per_su) * 128;
+    const int dsym = (tile % tiles_per_su) / chunks, s0 = ((tile % tiles_per_su) % chunks) * 128;
+    const int t_sym = g.data_t[dsym];
     const size_t base = (size_t)su * NRX_SYMBOLS * S;
     const int head = tab.head[sl][u];
     if (head != loaded) {
@@ -1032,17 +1054,24 @@ __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, R
       }
       loaded = head;
     }
-    {
+    if constexpr (!P::fp8) {  // wait (bounded) for this tile's state rows
+      bool ok = true;
+      if (tid == 0) ok = tc::mbar_wait(in_bar, in_phase);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(w.err, 1);
+        timed_out = true;
+        break;  // tma_pending stays set: the teardown waits for this phase
+      }
+      in_phase ^= 1u;
+      tma_pending = false;
+    } else {
       uint4 v[8];
 #pragma unroll
       for (int it = 0; it < 8; ++it) {
         const int i = tid + it * 128;
-        const int rw = i >> 3, ch = i & 7, rd = r0 + rw;
+        const int rw = i >> 3, ch = i & 7, s = s0 + rw;
         v[it] = make_uint4(0, 0, 0, 0);
-        if (rd < g.n_data) {
-          const int t = g.data_t[rd / S], s = rd % S;
-          v[it] = __ldg(reinterpret_cast<const uint4*>(state + (base + (size_t)t * S + s) * C64) + ch);
-        }
+        if (s < S) v[it] = __ldg(reinterpret_cast<const uint4*>(state + (base + (size_t)t_sym * S + s) * C64) + ch);
       }
 #pragma unroll
       for (int it = 0; it < 8; ++it) {
@@ -1068,8 +1097,6 @@ __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, R
               make_uint2(e4m3x2(f[0] * inv, f[1] * inv) | (e4m3x2(f[2] * inv, f[3] * inv) << 16),
                          e4m3x2(f[4] * inv, f[5] * inv) | (e4m3x2(f[6] * inv, f[7] * inv) << 16));
           if (ch == 0) ssc[64 + rw] = sc;
-        } else {
-          *reinterpret_cast<uint4*>(sm + L::A + (rw >> 3) * 1024 + (rw & 7) * 128 + ((ch ^ (rw & 7)) << 4)) = v[it];
         }
       }
     }
@@ -1084,10 +1111,17 @@ __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, R
       timed_out = true;
       break;
     }
+    if constexpr (!P::fp8) {  // the MMA has read the tile: the next tile's rows into A
+      const int nt = tile + gridDim.x;
+      if (nt < n_tiles) {
+        if (tid == 0) issue_rows(nt);
+        tma_pending = true;
+      }
+    }
     float h[64];
     tc::tmem_row64(c.tmem + ((uint32_t)(warp * 32) << 16), h);
-    const int rd = r0 + row;
-    if (rd < g.n_data) {
+    const int rd = dsym * S + s0 + row;  // data RE index
+    if (s0 + row < S) {
       if constexpr (P::fp8) {
         const float rs = ssc[64 + row];
 #pragma unroll
@@ -1107,6 +1141,7 @@ __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, R
     tc::tc_fence_before();
     __syncthreads();
   }
+  if (tma_pending && tid == 0) tc::mbar_wait(in_bar, in_phase, 100000000ull);  // let a copy in flight land
   tc_teardown(c, 64, timed_out);
 }
 
@@ -1392,16 +1427,41 @@ cudaError_t launch_block_tc(const Geometry& g, const IterWeightsTC& w, int r, co
   return cudaGetLastError();
 }
 
+// 3-D map of the state [planes x 14][S][64] for the read-out tiles: box
+// [1 symbol][128 subcarriers][64 channels], 128-byte swizzle, zero fill past S.
+template <typename T>
+cudaError_t readout_rows_map(CUtensorMap* map, const T* base, int planes, int S) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {64, (cuuint64_t)S, (cuuint64_t)planes * NRX_SYMBOLS};
+  const cuuint64_t strides[2] = {64 * sizeof(T), (cuuint64_t)S * 64 * sizeof(T)};
+  const cuuint32_t box[3] = {64, 128, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUtensorMapDataType dt =
+      std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const CUresult r = enc(map, dt, 3, const_cast<T*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <typename P>
 cudaError_t launch_readout_tc(const Geometry& g, const SlotTable& tab, const ReadoutWeightsTC& w,
                               const typename P::T* state, float* llr, cudaStream_t st) {
   if (g.C != 64) return cudaErrorInvalidValue;
-  const int tpsu = (g.n_data + 127) / 128;
+  const int tpsu = (NRX_SYMBOLS - g.n_dmrs) * ((g.S + 127) / 128);  // (data symbol, 128-subcarrier chunk)
   const int tiles = g.n_slots * g.U * tpsu;
   const int smem = RoLayout<P>::DYN;
   ensure_smem<k_readout_tc<P>>(smem);
+  CUtensorMap rmap;
+  memset(&rmap, 0, sizeof(rmap));
+  if constexpr (!P::fp8) {
+    if (reinterpret_cast<uintptr_t>(state) & 15) return cudaErrorInvalidValue;  // TMA global address alignment
+    const cudaError_t e = readout_rows_map(&rmap, state, g.n_slots * g.U, g.S);
+    if (e != cudaSuccess) return e;
+  }
   const int grid = grid_for(smem, 8, tiles);  // 8 x 64 TMEM columns per SM
-  k_readout_tc<P><<<grid, 128, smem, st>>>(g, tab, w, state, llr, tpsu);
+  k_readout_tc<P><<<grid, 128, smem, st>>>(g, tab, w, state, llr, tpsu, rmap);
   return cudaGetLastError();
 }
 
