@@ -212,7 +212,8 @@ template <typename P>
 __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC w,
                                                        const typename P::T* __restrict__ state,
                                                        typename P::T* __restrict__ z, int nre, int tiles_per_slot,
-                                                       const __grid_constant__ CUtensorMap smap) {
+                                                       const __grid_constant__ CUtensorMap smap,
+                                                       const __grid_constant__ CUtensorMap zmap) {
   using T = typename P::T;
   using MpL = MpLayout<P>;
   extern __shared__ unsigned char smem_raw[];
@@ -338,6 +339,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
       tc::tc_fence_after();
       gemm64<P>(c.tmem, sa_s, sw1, false);
       tc::mma_commit(c.bar);
+      if constexpr (!P::fp8) tc::bulk_wait_read_all();  // the previous z store has read the staging
     }
     if (!tc_wait(c, w.err)) {
       timed_out = true;
@@ -554,19 +556,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
       }
     }
     tc::tc_fence_before();
-    __syncthreads();
-    // coalesced store: 8 threads per 128-byte row
+    if constexpr (!P::fp8) {
+      // the staging is the 128-byte-swizzled box [U][nre][64]: one bulk tensor
+      // store to z (rows past the REs are not written)
+      tc::fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc::tma_store_3d(&zmap, 0, re0, sl * U, sm + MpL::XCH);
+        tc::bulk_commit();
+      }
+    } else {
+      __syncthreads();
+      // coalesced store: 8 threads per 128-byte row
 #pragma unroll
-    for (int it = 0; it < 4; ++it) {
-      const int i = tid + it * kThreads;
-      const int row = i >> 3, ch = i & 7;
-      const int u = row / nre, j = row % nre, re = re0 + j;
-      if (u < U && re < n_re)
-        reinterpret_cast<uint4*>(z + (((size_t)sl * U + u) * n_re + re) * C64)[ch] =
-            *reinterpret_cast<const uint4*>(sm + MpL::XCH + row * 128 + ((ch ^ (row & 7)) << 4));
+      for (int it = 0; it < 4; ++it) {
+        const int i = tid + it * kThreads;
+        const int row = i >> 3, ch = i & 7;
+        const int u = row / nre, j = row % nre, re = re0 + j;
+        if (u < U && re < n_re)
+          reinterpret_cast<uint4*>(z + (((size_t)sl * U + u) * n_re + re) * C64)[ch] =
+              *reinterpret_cast<const uint4*>(sm + MpL::XCH + row * 128 + ((ch ^ (row & 7)) << 4));
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
+  if constexpr (!P::fp8)
+    if (tid == 0) tc::bulk_wait_all();  // the last z store has landed
   if (tma_pending && tid == 0) tc::mbar_wait(in_bar, in_phase, 100000000ull);  // let a copy in flight land
   tc_teardown(c, P::fp8 ? 256 : 128, timed_out);
 }
@@ -1343,15 +1358,18 @@ cudaError_t launch_mp_tc(const Geometry& g, const IterWeightsTC& w, const typena
   const int tiles = g.n_slots * tps;
   const int smem = MpLayout<P>::DYN;
   ensure_smem<k_mp_tc<P>>(smem);
-  CUtensorMap smap;
+  CUtensorMap smap, zmap;
   memset(&smap, 0, sizeof(smap));
+  memset(&zmap, 0, sizeof(zmap));
   if constexpr (!P::fp8) {
-    if (reinterpret_cast<uintptr_t>(state) & 15) return cudaErrorInvalidValue;  // TMA global address alignment
-    const cudaError_t e = state_rows_map(&smap, state, g.n_slots * g.U, NRX_SYMBOLS * g.S, nre, g.U);
+    if ((reinterpret_cast<uintptr_t>(state) | reinterpret_cast<uintptr_t>(z)) & 15)
+      return cudaErrorInvalidValue;  // TMA global address alignment
+    cudaError_t e = state_rows_map(&smap, state, g.n_slots * g.U, NRX_SYMBOLS * g.S, nre, g.U);
+    if (e == cudaSuccess) e = state_rows_map(&zmap, z, g.n_slots * g.U, NRX_SYMBOLS * g.S, nre, g.U);
     if (e != cudaSuccess) return e;
   }
   const int grid = grid_for(smem, 2, tiles);
-  k_mp_tc<P><<<grid, kThreads, smem, st>>>(g, w, state, z, nre, tps, smap);
+  k_mp_tc<P><<<grid, kThreads, smem, st>>>(g, w, state, z, nre, tps, smap, zmap);
   return cudaGetLastError();
 }
 

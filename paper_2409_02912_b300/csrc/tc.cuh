@@ -297,6 +297,20 @@ __device__ __forceinline__ uint32_t pack_relu_f16x2(float lo, float hi) {
 __device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
   asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v));
 }
+// TMA: store the box at coordinates (x, y, z) of `map` from shared memory at
+// src as one bulk async-group operation (coordinates not negative; elements
+// outside the tensor are not written).
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int x, int y, int z, const void* src) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Wait until the committed bulk stores have read their shared-memory source /
+// have completed.
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // a + b on a pair (one packed FP32 instruction; a * 1 + b rounds once, like an add).
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return ffma2(a, make_float2(1.f, 1.f), b); }
 
