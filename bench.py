@@ -378,10 +378,24 @@ def run_ours(args, rank, world, local):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             rx.nrx_detect_batch_host(y_h, d_h, w.dmrs_symbols, bits, l_h, stream=stream)
+        sync_s = (time.perf_counter() - t0) / args.steps
+        # pipelined: every step still uploads its grid and pilots and downloads
+        # its LLRs (two output buffers in turn), overlapped with the
+        # neighbouring steps' compute; timed from the first upload to the
+        # last download
+        l_h2 = [l_h, torch.empty(n_llr, dtype=torch.float32).pin_memory()]
+        for k in range(3):
+            rx.nrx_detect_batch_host_async(y_h, d_h, w.dmrs_symbols, bits, l_h2[k & 1])
+        rx.nrx_host_drain()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            rx.nrx_detect_batch_host_async(y_h, d_h, w.dmrs_symbols, bits, l_h2[k & 1])
+        rx.nrx_host_drain()
         e2e_s = (time.perf_counter() - t0) / args.steps
         extras["e2e"] = {"value": res_step / e2e_s, "unit": UNIT,
                          "h2d_bytes_per_step": int(y_h.numel() * 8 + d_h.numel() * 8),
-                         "d2h_bytes_per_step": int(n_llr * 4)}
+                         "d2h_bytes_per_step": int(n_llr * 4), "mode": "pipelined host calls",
+                         "synchronous_value": res_step / sync_s}
         # matched BLER: the trained network on a coded sweep of the 24-PRB two-user workload
         from paper_2409_02912_b300 import evaluate
         with open(evaluate.TRAINED_MU2, "rb") as f:

@@ -174,6 +174,28 @@ nrx_status nrx_detect_batch_host(nrx_ctx* ctx, int32_t n_slots, const void* y_ho
                                  float* llr_host, void* stream);
 
 /*
+ * Pipelined form of nrx_detect_batch_host for a stream of batches: enqueue the
+ * upload of y_host and of the pilots, the NRX, and the download of the LLRs
+ * into llr_host, and return without waiting.  The context runs uploads,
+ * compute and downloads on three internal streams with two staging sets, so
+ * consecutive calls overlap: call k + 1 uploads while call k computes, and
+ * call k downloads while call k + 1 computes.  Calls complete in order.
+ * Arguments as nrx_detect_batch_host; cfgs and bits are read before the call
+ * returns, but y_host, the pilots (cfgs[i].dmrs_seq) and llr_host must stay
+ * valid and unmodified until nrx_host_drain returns.  Host buffers should be
+ * pinned.  Every other entry point drains the pipeline before it runs; device
+ * calls issued on a stream of their own must have completed before a
+ * pipelined call is made (the context's scratch is shared).
+ */
+nrx_status nrx_detect_batch_host_async(nrx_ctx* ctx, int32_t n_slots, const void* y_host,
+                                       const nrx_slot_cfg* cfgs, const int32_t* bits_per_symbol,
+                                       float* llr_host);
+
+/* Wait for every pipelined call of the context; report device-side failures
+ * as nrx_check does (NRX_ETIMEDOUT, NRX_ECUDA), else NRX_OK. */
+nrx_status nrx_host_drain(nrx_ctx* ctx);
+
+/*
  * Copy the CGNN state S (after the iterations run by the last nrx_detect*
  * call on this context) of batch slot `slot` into state_out: device float32
  * [num_users][14][S][C].  Ordered on `stream` after that call.

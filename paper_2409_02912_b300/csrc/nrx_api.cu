@@ -47,6 +47,16 @@ struct nrx_ctx {
   float2* y_stage = nullptr;
   float* llr_stage = nullptr;
   float2* dmrs_stage = nullptr;
+  size_t y_stage_bytes = 0, llr_stage_bytes = 0, dmrs_stage_bytes = 0;
+  // pipelined host-buffer calls: a second staging set, upload / compute /
+  // download streams and per-set events (created on the first such call)
+  float2* y_stage2 = nullptr;
+  float* llr_stage2 = nullptr;
+  float2* dmrs_stage2 = nullptr;
+  cudaStream_t h2d_st = nullptr, cmp_st = nullptr, d2h_st = nullptr;
+  cudaEvent_t ev_in[2] = {}, ev_cmp[2] = {}, ev_out[2] = {};
+  int64_t host_calls = 0;
+  bool host_inflight = false;
   // per-kernel event timing
   bool profiling = false;
   std::vector<cudaEvent_t> ev_free;
@@ -311,6 +321,13 @@ const char* nrx_last_error(const nrx_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 int32_t nrx_last_launch_count(const nrx_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
 
+nrx_status nrx_host_drain(nrx_ctx* ctx) {
+  if (!ctx) return NRX_EINVAL;
+  if (!ctx->host_inflight) return NRX_OK;
+  ctx->host_inflight = false;
+  return nrx_check(ctx, ctx->d2h_st);  // the download stream ends every pipelined call
+}
+
 nrx_status nrx_check(nrx_ctx* ctx, void* stream) {
   if (!ctx) return NRX_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -410,6 +427,16 @@ void nrx_destroy(nrx_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  for (int b = 0; b < 2; ++b) {
+    if (ctx->ev_in[b]) cudaEventDestroy(ctx->ev_in[b]);
+    if (ctx->ev_cmp[b]) cudaEventDestroy(ctx->ev_cmp[b]);
+    if (ctx->ev_out[b]) cudaEventDestroy(ctx->ev_out[b]);
+  }
+  for (cudaStream_t s : {ctx->h2d_st, ctx->cmp_st, ctx->d2h_st})
+    if (s) cudaStreamDestroy(s);
+  cudaFree(ctx->y_stage2);
+  cudaFree(ctx->llr_stage2);
+  cudaFree(ctx->dmrs_stage2);
   cudaFree(ctx->w_f32);
   cudaFree(ctx->w_tc);
   cudaFree(ctx->state);
@@ -617,6 +644,9 @@ nrx_status nrx_create(const void* weights, size_t weights_bytes, int32_t num_rx_
     nrx_destroy(ctx);
     return NRX_ENOMEM;
   }
+  ctx->y_stage_bytes = y_bytes;
+  ctx->llr_stage_bytes = llr_bytes;
+  ctx->dmrs_stage_bytes = dmrs_bytes;
   *out = ctx;
   return NRX_OK;
 }
@@ -624,6 +654,10 @@ nrx_status nrx_create(const void* weights, size_t weights_bytes, int32_t num_rx_
 nrx_status nrx_detect_batch(nrx_ctx* ctx, int32_t n_slots, const void* y, const nrx_slot_cfg* cfgs,
                             const int32_t* bits, float* llr, void* stream) {
   if (!ctx) return NRX_EINVAL;
+  if (ctx->host_inflight) {  // pipelined host calls share the scratch: finish them first
+    const nrx_status d = nrx_host_drain(ctx);
+    if (d != NRX_OK) return d;
+  }
   ctx->last_launches = 0;
   if (!y || !llr || !aligned(y, 16) || !aligned(llr, 4))
     return fail(ctx, NRX_EINVAL, "y must be 16-byte aligned and llr 4-byte aligned (non-null)");
@@ -643,6 +677,10 @@ nrx_status nrx_detect(nrx_ctx* ctx, const void* y, const nrx_slot_cfg* cfg, cons
 
 nrx_status lmmse_detect_batch(nrx_ctx* ctx, int32_t n_slots, const void* y, const nrx_slot_cfg* cfgs,
                               const int32_t* bits, float* llr, void* stream) {
+  if (ctx && ctx->host_inflight) {
+    const nrx_status d = nrx_host_drain(ctx);
+    if (d != NRX_OK) return d;
+  }
   if (!ctx) return NRX_EINVAL;
   ctx->last_launches = 0;
   if (!y || !llr || !aligned(y, 16) || !aligned(llr, 4))
@@ -671,6 +709,10 @@ nrx_status lmmse_detect(nrx_ctx* ctx, const void* y, const nrx_slot_cfg* cfg, co
 nrx_status nrx_detect_batch_host(nrx_ctx* ctx, int32_t n_slots, const void* y_host, const nrx_slot_cfg* cfgs,
                                  const int32_t* bits, float* llr_host, void* stream) {
   if (!ctx) return NRX_EINVAL;
+  if (ctx->host_inflight) {  // pipelined host calls share the scratch: finish them first
+    const nrx_status d = nrx_host_drain(ctx);
+    if (d != NRX_OK) return d;
+  }
   ctx->last_launches = 0;
   if (!y_host || !llr_host) return fail(ctx, NRX_EINVAL, "null host buffer");
   Geometry g;
@@ -699,7 +741,62 @@ nrx_status nrx_detect_batch_host(nrx_ctx* ctx, int32_t n_slots, const void* y_ho
   return NRX_OK;
 }
 
+nrx_status nrx_detect_batch_host_async(nrx_ctx* ctx, int32_t n_slots, const void* y_host, const nrx_slot_cfg* cfgs,
+                                       const int32_t* bits, float* llr_host) {
+  if (!ctx) return NRX_EINVAL;
+  ctx->last_launches = 0;
+  if (!y_host || !llr_host) return fail(ctx, NRX_EINVAL, "null host buffer");
+  Geometry g;
+  SlotTable tab;
+  int its = 0;
+  size_t total = 0;
+  nrx_status st = prepare(ctx, n_slots, cfgs, bits, true, false, &g, &tab, &its, &total);
+  if (st != NRX_OK) return st;
+  cudaError_t e = cudaSuccess;
+  if (!ctx->h2d_st) {  // first pipelined call: streams, events, second staging set
+    for (cudaStream_t* s : {&ctx->h2d_st, &ctx->cmp_st, &ctx->d2h_st})
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+      for (cudaEvent_t* ev : {&ctx->ev_in[b], &ctx->ev_cmp[b], &ctx->ev_out[b]})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->y_stage2, ctx->y_stage_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->llr_stage2, ctx->llr_stage_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->dmrs_stage2, ctx->dmrs_stage_bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pipeline set-up");
+  }
+  // call k uses staging set k % 2; the set is free once call k - 2 has downloaded
+  const int b = (int)(ctx->host_calls & 1);
+  float2* ys = b ? ctx->y_stage2 : ctx->y_stage;
+  float2* ds = b ? ctx->dmrs_stage2 : ctx->dmrs_stage;
+  float* ls = b ? ctx->llr_stage2 : ctx->llr_stage;
+  if (ctx->host_calls >= 2) e = cudaStreamWaitEvent(ctx->h2d_st, ctx->ev_out[b], 0);
+  const size_t y_bytes = (size_t)n_slots * g.B * NRX_SYMBOLS * g.S * sizeof(float2);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ys, y_host, y_bytes, cudaMemcpyHostToDevice, ctx->h2d_st);
+  const size_t per = (size_t)g.n_dmrs * (g.S / 2);
+  for (int i = 0; i < n_slots && e == cudaSuccess; ++i) {
+    e = cudaMemcpyAsync(ds + i * per, cfgs[i].dmrs_seq, per * sizeof(float2), cudaMemcpyHostToDevice, ctx->h2d_st);
+    tab.dmrs[i] = ds + i * per;
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_in[b], ctx->h2d_st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cmp_st, ctx->ev_in[b], 0);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "pipelined upload");
+  ctx->host_inflight = true;
+  st = run_nrx(ctx, g, tab, its, ys, ls, ctx->cmp_st);
+  if (st != NRX_OK) return st;
+  e = cudaEventRecord(ctx->ev_cmp[b], ctx->cmp_st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->d2h_st, ctx->ev_cmp[b], 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(llr_host, ls, total * sizeof(float), cudaMemcpyDeviceToHost, ctx->d2h_st);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_out[b], ctx->d2h_st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "pipelined download");
+  ctx->host_calls++;
+  return NRX_OK;
+}
+
 nrx_status nrx_copy_state(nrx_ctx* ctx, int32_t slot, float* out, void* stream) {
+  if (ctx && ctx->host_inflight) {
+    const nrx_status d = nrx_host_drain(ctx);
+    if (d != NRX_OK) return d;
+  }
   if (!ctx) return NRX_EINVAL;
   if (!ctx->have_state) return fail(ctx, NRX_EINVAL, "no nrx_detect call yet");
   const Geometry& g = ctx->last_geo;

@@ -23,7 +23,7 @@ EXPORTED = (
     "nrx_create", "nrx_destroy", "nrx_llr_count", "nrx_detect_batch", "nrx_detect", "lmmse_detect_batch",
     "lmmse_detect", "nrx_detect_batch_host", "nrx_copy_state", "nrx_get_net", "nrx_last_launch_count",
     "nrx_last_error", "nrx_status_string", "nrx_profile", "nrx_profile_read", "nrx_detect_noalloc",
-    "nrx_check", "nrx_dmrs_gold", "nrx_expire_wait",
+    "nrx_check", "nrx_dmrs_gold", "nrx_expire_wait", "nrx_detect_batch_host_async", "nrx_host_drain",
 )
 KERNEL_KINDS = 5
 
@@ -90,6 +90,10 @@ def load() -> ctypes.CDLL:
     lib.nrx_check.argtypes = [P, P]
     lib.nrx_check.restype = ctypes.c_int
     lib.nrx_expire_wait.argtypes = [P, I32, P]
+    lib.nrx_detect_batch_host_async.argtypes = [P, I32, P, CFG, P, P]
+    lib.nrx_detect_batch_host_async.restype = ctypes.c_int
+    lib.nrx_host_drain.argtypes = [P]
+    lib.nrx_host_drain.restype = ctypes.c_int
     lib.nrx_expire_wait.restype = ctypes.c_int
     lib.nrx_detect_noalloc.argtypes = [P, P, P, CFG, P, P, P]
     lib.nrx_detect_noalloc.restype = ctypes.c_int
@@ -243,6 +247,24 @@ class Receiver:
         st = self._lib.nrx_detect_batch_host(self.ctx, n, yp, cfgs, bits.ctypes.data, lp, _stream_ptr(stream))
         self._check(st, "nrx_detect_batch_host")
         return llr_host
+
+    def nrx_detect_batch_host_async(self, y_host, dmrs_host, dmrs_symbols, bits, llr_host, iterations: int = 0):
+        """Pipelined host-buffer call (see nrx.h): returns at once; y_host,
+        dmrs_host and llr_host must stay alive and unchanged until
+        ``nrx_host_drain``."""
+        yp, dp, lp = (_host_ptr(a) for a in (y_host, dmrs_host, llr_host))
+        n, B, T, S = tuple(y_host.shape)
+        bits = _bits_array(bits).reshape(n, -1)
+        U = bits.shape[1]
+        per = len(dmrs_symbols) * (S // 2) * 8
+        cfgs = make_cfgs(n, S // 12, U, dmrs_symbols, [dp + i * per for i in range(n)], [1.0] * n, iterations)
+        self._check(self._lib.nrx_detect_batch_host_async(self.ctx, n, yp, cfgs, bits.ctypes.data, lp),
+                    "nrx_detect_batch_host_async")
+        return llr_host
+
+    def nrx_host_drain(self):
+        """Wait for every pipelined call; raise on a device-side failure."""
+        self._check(self._lib.nrx_host_drain(self.ctx), "nrx_host_drain")
 
     def nrx_copy_state(self, slot: int, num_users: int, S: int, stream=None):
         import torch

@@ -109,6 +109,42 @@ def test_host_buffer_entry_point_matches_device_call():
     assert np.array_equal(out.numpy(), dev)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_pipelined_host_calls_match_synchronous_ones(prec):
+    """Pipelined host-buffer calls (uploads, compute and downloads of
+    consecutive batches overlapped on the context's streams, two staging
+    sets) give each batch the LLRs of a synchronous call, in order; a later
+    device call drains the pipeline first."""
+    import torch
+    w, slots = H.slots_for("mu2_4rx_24prb", 6)
+    groups = [slots[0:2], slots[2:4], slots[4:6]]
+    rx = _receiver(w.net, groups[0], prec)
+    ins, refs = [], []
+    for gsl in groups:
+        y_h = torch.from_numpy(synth.stack_batch(gsl)).pin_memory()
+        d_h = torch.from_numpy(np.stack([s.dmrs for s in gsl])).pin_memory()
+        bits = [list(s.cfg.bits_per_symbol) for s in gsl]
+        n = sum(s.cfg.num_data_symbols * s.cfg.num_subcarriers * sum(s.cfg.bits_per_symbol) for s in gsl)
+        ref = torch.empty(n, dtype=torch.float32).pin_memory()
+        rx.nrx_detect_batch_host(y_h, d_h, w.dmrs_symbols, bits, ref)
+        ins.append((y_h, d_h, bits, n))
+        refs.append(ref.numpy().copy())
+    outs = []
+    for k in range(7):
+        y_h, d_h, bits, n = ins[k % 3]
+        out = torch.full((n,), float("nan"), dtype=torch.float32).pin_memory()
+        rx.nrx_detect_batch_host_async(y_h, d_h, w.dmrs_symbols, bits, out)
+        outs.append(out)
+    rx.nrx_host_drain()
+    for k, out in enumerate(outs):
+        assert np.array_equal(out.numpy(), refs[k % 3]), k
+    y, dmrs, bits, _ = H.device_inputs(groups[1])
+    rx.nrx_detect_batch_host_async(ins[0][0], ins[0][1], w.dmrs_symbols, ins[0][2], outs[0])  # left in flight
+    dev = rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits).cpu().numpy()
+    assert np.array_equal(dev, refs[1]) and np.array_equal(outs[0].numpy(), refs[0])
+    rx.close()
+
+
 def test_invalid_arguments_launch_nothing():
     w, slots = H.slots_for("mu2_4rx_24prb", 2)
     rx = _receiver(w.net, slots)
