@@ -51,6 +51,8 @@ __global__ void __launch_bounds__(256) k_state_init(Geometry g, SlotTable tab, c
   const int S = g.S;
   const int tps = (S + TW - 1) / TW;
   const int n_tiles = g.n_slots * g.U * tps;
+  tc::pdl_launch_dependents();
+  tc::pdl_wait();  // the previous kernel may still read the state this kernel writes
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int su = tile / tps, u = su % g.U, sl = su / g.U;
     const int s0 = (tile % tps) * TW - 1;
@@ -173,8 +175,7 @@ cudaError_t launch_si(const Geometry& g, const SlotTable& tab, const float2* y, 
   if (per_sm < 1) per_sm = 1;
   const int tiles = g.n_slots * g.U * ((g.S + kStateInitTile - 1) / kStateInitTile);
   const int grid = tiles < per_sm * sm_count() ? tiles : per_sm * sm_count();
-  k_state_init<C, B, OutT><<<grid, 256, smem, st>>>(g, tab, y, w, s_out);
-  return cudaGetLastError();
+  return launch_pdl(k_state_init<C, B, OutT>, grid, 256, smem, st, g, tab, y, w, s_out);
 }
 
 template <int C, typename OutT>

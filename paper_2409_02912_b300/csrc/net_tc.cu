@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
                                                        const __grid_constant__ CUtensorMap zmap) {
   using T = typename P::T;
   using MpL = MpLayout<P>;
+  tc::pdl_launch_dependents();
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = align1024(smem_raw);
   float* vec = reinterpret_cast<float*>(sm + MpL::VEC);
@@ -263,6 +264,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
     tc::tma_load_3d(dst, &smap, 0, (t_next % tiles_per_slot) * nre, (t_next / tiles_per_slot) * U, in_bar);
   };
   int par = 0;
+  tc::pdl_wait();  // weights are in shared memory; from here on the previous kernel's output is read
   if constexpr (!P::fp8) {
     if (blockIdx.x < n_tiles) {
       if (tid == 0) issue_s(blockIdx.x, sm + MpL::A_S);
@@ -688,6 +690,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
                                                            const __grid_constant__ CUtensorMap zmap) {
   using T = typename P::T;
   using L = BlkLayout<P>;
+  tc::pdl_launch_dependents();
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = align1024(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -749,6 +752,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
   const int out_c8 = tid & 7;
   const int cpc = cp >> 2, cpl = cp & 3;  // 16-byte chunk and word within it of this channel pair
   bool timed_out = false;
+  tc::pdl_wait();  // weights are in shared memory; from here on the previous kernel's output is read
 
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int su = tile / tps;  // slot * U + user
@@ -1015,6 +1019,7 @@ __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, R
                                                     int tiles_per_su, const __grid_constant__ CUtensorMap rmap) {
   using T = typename P::T;
   using L = RoLayout<P>;
+  tc::pdl_launch_dependents();
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = align1024(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1040,6 +1045,7 @@ __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, R
     tc::mbar_arrive_expect_tx(in_bar, 128u * 128u);
     tc::tma_load_3d(sm + L::A, &rmap, 0, (k % chunks) * 128, su_n * NRX_SYMBOLS + g.data_t[k / chunks], in_bar);
   };
+  tc::pdl_wait();  // from here on the previous kernel's output is read
   if constexpr (!P::fp8) {
     if (blockIdx.x < n_tiles) {
       if (tid == 0) issue_rows(blockIdx.x);
@@ -1369,8 +1375,7 @@ cudaError_t launch_mp_tc(const Geometry& g, const IterWeightsTC& w, const typena
     if (e != cudaSuccess) return e;
   }
   const int grid = grid_for(smem, 2, tiles);
-  k_mp_tc<P><<<grid, kThreads, smem, st>>>(g, w, state, z, nre, tps, smap, zmap);
-  return cudaGetLastError();
+  return launch_pdl(k_mp_tc<P>, grid, kThreads, smem, st, g, w, state, z, nre, tps, smap, zmap);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no direct
@@ -1439,10 +1444,8 @@ cudaError_t launch_block_tc(const Geometry& g, const IterWeightsTC& w, int r, co
   const cudaError_t e = activation_map(&zmap, z_in, g.n_slots * g.U, g.S, BlkLayout<P>::IW);
   if (e != cudaSuccess) return e;
   const int grid = grid_for(smem, 2, tiles);
-  k_block_tc<P><<<grid, kThreads, smem, st>>>(g, w.pw1[r], w.pw2[r], w.pw1_b[r], w.pw2_b[r], w.dw1[r], w.dw2[r],
-                                               w.pw1_sc[r], w.pw2_sc[r], z_in, z_out, state, last ? 1 : 0, w.err,
-                                               zmap);
-  return cudaGetLastError();
+  return launch_pdl(k_block_tc<P>, grid, kThreads, smem, st, g, w.pw1[r], w.pw2[r], w.pw1_b[r], w.pw2_b[r],
+                    w.dw1[r], w.dw2[r], w.pw1_sc[r], w.pw2_sc[r], z_in, z_out, state, last ? 1 : 0, w.err, zmap);
 }
 
 // 3-D map of the state [planes x 14][S][64] for the read-out tiles: box
@@ -1479,8 +1482,7 @@ cudaError_t launch_readout_tc(const Geometry& g, const SlotTable& tab, const Rea
     if (e != cudaSuccess) return e;
   }
   const int grid = grid_for(smem, 8, tiles);  // 8 x 64 TMEM columns per SM
-  k_readout_tc<P><<<grid, 128, smem, st>>>(g, tab, w, state, llr, tpsu, rmap);
-  return cudaGetLastError();
+  return launch_pdl(k_readout_tc<P>, grid, 128, smem, st, g, tab, w, state, llr, tpsu, rmap);
 }
 
 template <typename T>

@@ -311,6 +311,10 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 // have completed.
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Programmatic dependent launch: let the next kernel on the stream start its
+// prologue now / wait until the previous kernel's writes are visible.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 // a + b on a pair (one packed FP32 instruction; a * 1 + b rounds once, like an add).
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return ffma2(a, make_float2(1.f, 1.f), b); }
 
