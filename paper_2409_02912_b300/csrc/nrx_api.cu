@@ -325,7 +325,13 @@ nrx_status nrx_host_drain(nrx_ctx* ctx) {
   if (!ctx) return NRX_EINVAL;
   if (!ctx->host_inflight) return NRX_OK;
   ctx->host_inflight = false;
-  return nrx_check(ctx, ctx->d2h_st);  // the download stream ends every pipelined call
+  // the download stream ends every completed call; the others matter after a
+  // call that failed part-way
+  const cudaError_t a = cudaStreamSynchronize(ctx->h2d_st);
+  const cudaError_t b = cudaStreamSynchronize(ctx->cmp_st);
+  if (a != cudaSuccess) return cuda_fail(ctx, a, "upload stream");
+  if (b != cudaSuccess) return cuda_fail(ctx, b, "compute stream");
+  return nrx_check(ctx, ctx->d2h_st);
 }
 
 nrx_status nrx_check(nrx_ctx* ctx, void* stream) {
