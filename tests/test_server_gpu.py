@@ -57,9 +57,13 @@ def _settle_captures(srv, quiet_s=0.2, limit_s=10.0):
             return
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
-def test_llrs_do_not_depend_on_batch_company(precision):
-    blob = synth.pack_weights(NET, synth.make_weights(NET))
+@pytest.mark.parametrize("precision,var_io", [("fp32", False), ("bf16", False), ("bf16", True)])
+def test_llrs_do_not_depend_on_batch_company(precision, var_io):
+    """Each slot's LLRs are the same served alone, in a mixed batch, replayed
+    from a captured graph, or through the direct entry point; with Var-IO
+    weights every user of a mixed batch runs its own modulation's heads."""
+    net = synth.dataclasses.replace(NET, var_io=var_io)
+    blob = synth.pack_weights(net, synth.make_weights(net))
     srv = server.Server(blob, 4, [4, 8], max_users=2, max_batch=8, precision=precision, deadline_us=1e7)
     try:
         slots = _slots(8, 2, 6, seed=300)
