@@ -9,7 +9,13 @@
 // All kernels are persistent (grid = min(tiles, SMs x CTAs/SM)), load their
 // weights into shared memory once, and wait for MMA completion on an mbarrier
 // with a bounded wait: on timeout they set the context's error word, wait once
-// more for their own MMAs, release TMEM and return.
+// more for their own MMAs (and bulk copies in flight), release TMEM and return.
+// Activation tiles move by bulk tensor copies (TMA) where their layout allows:
+// the residual block's input tile with its halo, the message-passing S rows
+// and z tile and the read-out rows in the 128-byte-swizzled operand layout.
+// Kernels are launched with programmatic stream serialisation: each starts
+// its prologue while its predecessor finishes and waits (griddepcontrol)
+// before reading that predecessor's output.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
