@@ -90,13 +90,12 @@ __device__ __forceinline__ float e4m3_scale(float amax) { return amax > 0.f ? am
 constexpr int kTileBytes = 16384;  // 128 x 64 16-bit operand tile
 
 int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
+  static const int n = [] {  // thread-safe one-time initialisation (serving calls from several threads)
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 148;
+  }();
   return n;
 }
 

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/nrx_train.h"
+#include "kernels.h"
 #include "tc.cuh"
 
 namespace {
@@ -175,12 +176,7 @@ nrx_status nrx_train_gemm_bf16(int32_t M, int32_t N, int32_t K, const float* A, 
                                void* stream) {
   if (M < 1 || N < 1 || K < 1 || !A || !B || !C || split_k < 1 || split_k > 65535) return NRX_EINVAL;
   if ((split_k > 1 && !accumulate) || (accumulate && (bias || R || relu))) return NRX_EINVAL;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
-      return NRX_ECUDA;
-    attr = true;
-  }
+  if (ensure_smem<k_gemm_bf16>(kSmemBytes) != cudaSuccess) return NRX_ECUDA;
   GemmArgs g;
   g.M = M;
   g.N = N;
