@@ -682,7 +682,7 @@ class GpuSimulator:
 
 
 # ----------------------------------------------------------------------------
-# Training driver
+# Training loop
 # ----------------------------------------------------------------------------
 
 
