@@ -83,7 +83,7 @@ typedef struct nrx_ctx nrx_ctx;
 typedef enum {
   NRX_OK = 0,
   NRX_EINVAL = 1,        /* bad argument; nothing was launched */
-  NRX_ENOMEM = 2,        /* device allocation failed (nrx_create only) */
+  NRX_ENOMEM = 2,        /* device allocation failed (nrx_create, first pipelined host call) */
   NRX_ECUDA = 3,         /* a CUDA call failed; see nrx_last_error */
   NRX_ETIMEDOUT = 4,     /* a bounded device-side wait gave up */
   NRX_EUNSUPPORTED = 5   /* valid but not supported by this build/context */
@@ -183,7 +183,9 @@ nrx_status nrx_detect_batch_host(nrx_ctx* ctx, int32_t n_slots, const void* y_ho
  * Arguments as nrx_detect_batch_host; cfgs and bits are read before the call
  * returns, but y_host, the pilots (cfgs[i].dmrs_seq) and llr_host must stay
  * valid and unmodified until nrx_host_drain returns.  Host buffers should be
- * pinned.  Every other entry point drains the pipeline before it runs; device
+ * pinned.  The first call creates the context's streams and a second staging
+ * set (NRX_ENOMEM if that does not fit; a later call retries).  Every other
+ * entry point drains the pipeline before it runs; device
  * calls issued on a stream of their own must have completed before a
  * pipelined call is made (the context's scratch is shared).
  */

@@ -57,6 +57,7 @@ struct nrx_ctx {
   cudaEvent_t ev_in[2] = {}, ev_cmp[2] = {}, ev_out[2] = {};
   int64_t host_calls = 0;
   bool host_inflight = false;
+  bool pipeline_ready = false;  // all of the above created
   // per-kernel event timing
   bool profiling = false;
   std::vector<cudaEvent_t> ev_free;
@@ -759,16 +760,21 @@ nrx_status nrx_detect_batch_host_async(nrx_ctx* ctx, int32_t n_slots, const void
   nrx_status st = prepare(ctx, n_slots, cfgs, bits, true, false, &g, &tab, &its, &total);
   if (st != NRX_OK) return st;
   cudaError_t e = cudaSuccess;
-  if (!ctx->h2d_st) {  // first pipelined call: streams, events, second staging set
+  if (!ctx->pipeline_ready) {  // first pipelined call: streams, events, second staging set (all or nothing)
     for (cudaStream_t* s : {&ctx->h2d_st, &ctx->cmp_st, &ctx->d2h_st})
-      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+      if (e == cudaSuccess && !*s) e = cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b)
       for (cudaEvent_t* ev : {&ctx->ev_in[b], &ctx->ev_cmp[b], &ctx->ev_out[b]})
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->y_stage2, ctx->y_stage_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->llr_stage2, ctx->llr_stage_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->dmrs_stage2, ctx->dmrs_stage_bytes);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "pipeline set-up");
+        if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess && !ctx->y_stage2) e = cudaMalloc(&ctx->y_stage2, ctx->y_stage_bytes);
+    if (e == cudaSuccess && !ctx->llr_stage2) e = cudaMalloc(&ctx->llr_stage2, ctx->llr_stage_bytes);
+    if (e == cudaSuccess && !ctx->dmrs_stage2) e = cudaMalloc(&ctx->dmrs_stage2, ctx->dmrs_stage_bytes);
+    if (e != cudaSuccess) {  // what was created is kept (nrx_destroy releases it); the next call retries the rest
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? fail(ctx, NRX_ENOMEM, "pipeline staging")
+                                            : cuda_fail(ctx, e, "pipeline set-up");
+    }
+    ctx->pipeline_ready = true;
   }
   // call k uses staging set k % 2; the set is free once call k - 2 has downloaded
   const int b = (int)(ctx->host_calls & 1);
