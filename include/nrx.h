@@ -159,6 +159,7 @@ nrx_status nrx_detect(nrx_ctx* ctx, const void* y, const nrx_slot_cfg* cfg,
 nrx_status lmmse_detect_batch(nrx_ctx* ctx, int32_t n_slots, const void* y, const nrx_slot_cfg* cfgs,
                               const int32_t* bits_per_symbol, float* llr, void* stream);
 
+/* Single slot: lmmse_detect_batch with n_slots = 1. */
 nrx_status lmmse_detect(nrx_ctx* ctx, const void* y, const nrx_slot_cfg* cfg,
                         const int32_t* bits_per_symbol, float* llr, void* stream);
 
@@ -284,7 +285,9 @@ nrx_status nrx_get_net(const nrx_ctx* ctx, int32_t* num_rx_ant, int32_t* channel
  * kinds if reset != 0.  NRX_EINVAL for an unknown kind.
  */
 #define NRX_KERNEL_KINDS 5
+/* Turn the per-kernel event timing on (enable != 0) or off. */
 nrx_status nrx_profile(nrx_ctx* ctx, int32_t enable);
+/* Totals of kernel kind `kind` (name: static string owned by the library). */
 nrx_status nrx_profile_read(nrx_ctx* ctx, int32_t kind, const char** name, double* total_ms,
                             int64_t* launches, int32_t reset);
 

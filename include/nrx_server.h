@@ -139,6 +139,9 @@ nrx_status nrx_server_poll(nrx_server* srv, nrx_completion* out, int32_t max_out
  * NRX_ETIMEDOUT). */
 nrx_status nrx_server_drain(nrx_server* srv, int32_t timeout_ms);
 
+/* Copy the server's counters (nrx_server_stats: served / fallback / rejected
+ * slots, launches, graph replays, admitted batch capacities, device bytes)
+ * into *out.  NRX_EINVAL for null arguments. */
 nrx_status nrx_server_get_stats(const nrx_server* srv, nrx_server_stats* out);
 
 #ifdef __cplusplus

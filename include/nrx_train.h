@@ -182,8 +182,15 @@ typedef struct {
   int32_t bits_per_symbol[4];
 } nrx_sim_slot;
 
+/* Bytes of device scratch nrx_train_simulate needs for n_slots slots of
+ * num_users users, num_rx_ant antennas and up to max_taps taps (0 for
+ * arguments out of range). */
 size_t nrx_train_sim_scratch_bytes(int32_t n_slots, int32_t num_users, int32_t num_rx_ant, int32_t max_taps);
 
+/* Draw one training batch on `stream` as described above: per-slot
+ * parameters in slots[n_slots] (host), batch index `batch` and `seed` select
+ * the Philox counters; outputs in device memory (layouts above).  NRX_EINVAL
+ * for out-of-range arguments, NRX_ECUDA on a launch failure. */
 nrx_status nrx_train_simulate(int32_t n_slots, const nrx_sim_slot* slots, int32_t num_users, int32_t num_rx_ant,
                               int32_t num_prb, int32_t num_dmrs_symbols, const int32_t* dmrs_symbols, int32_t m_max,
                               uint64_t seed, uint32_t batch, void* scratch, void* y, void* dmrs, uint8_t* bits,

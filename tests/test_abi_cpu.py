@@ -137,3 +137,23 @@ def test_server_structs_and_validation(lib):
         setattr(c, field, bad)
         assert sl.nrx_server_create(buf, len(blob), 2, ctypes.byref(c), ctypes.byref(h)) == nrx.NRX_EINVAL, field
     assert sl.nrx_server_now_ns() > 0
+
+
+def test_every_header_function_is_documented():
+    """Each function the C headers declare is directly preceded by its own
+    comment (arguments, layout, ownership, errors)."""
+    import glob
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    missing = []
+    for h in sorted(glob.glob(os.path.join(root, "include", "*.h"))):
+        lines = open(h).read().splitlines()
+        for i, line in enumerate(lines):
+            m = re.match(r"^\s*(?:const\s+)?(?:nrx_status|void|size_t|int32_t|int64_t|char\s*\*|const char\s*\*)"
+                         r"\s*\*?\s*(\w+)\s*\(", line)
+            if not m:
+                continue
+            prev = next((lines[j].strip() for j in range(i - 1, -1, -1) if lines[j].strip()), "")
+            if not (prev.endswith("*/") or prev.startswith("//")):
+                missing.append(f"{os.path.basename(h)}:{m.group(1)}")
+    assert not missing, missing
