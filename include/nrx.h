@@ -164,6 +164,19 @@ nrx_status lmmse_detect(nrx_ctx* ctx, const void* y, const nrx_slot_cfg* cfg,
                         const int32_t* bits_per_symbol, float* llr, void* stream);
 
 /*
+ * Number of REs whose LMMSE solve (lmmse_detect*) ran in FP64 on this
+ * context since it was created or last reset.  The per-RE solve of the
+ * LS + LMMSE receiver is FP32 except (a) every RE of a slot whose SNR
+ * 10 log10(1/N0) exceeds 20 dB (noise_var < 0.01), and (b) any RE whose FP32
+ * Cholesky factor of G = H^H H + N0 I has a non-positive pivot or pivots
+ * that spread by more than 1e6; those are solved in FP64 (the channel
+ * estimates and the demapper stay FP32).  Synchronises `stream`, copies the
+ * counter into *count and, if `reset` is non-zero, sets it to zero.
+ * NRX_EINVAL for a null argument, NRX_ECUDA on a CUDA error.
+ */
+nrx_status lmmse_fp64_count(nrx_ctx* ctx, int64_t* count, int32_t reset, void* stream);
+
+/*
  * End-to-end variant of nrx_detect_batch on HOST buffers: y_host (complex64,
  * same layout), each cfgs[i].dmrs_seq a HOST pointer, llr_host float32.
  * Copies the inputs into context-owned device staging buffers, runs the NRX,
@@ -220,12 +233,19 @@ nrx_status nrx_copy_state(nrx_ctx* ctx, int32_t slot, float* state_out, void* st
  * weights in kernel layout, the rest three FP32 activation tensors of
  * num_users * 14 * 12*num_prb * C floats each.  Larger slots are rejected with
  * NRX_EINVAL (e.g. C=64: up to 4 users x 27 PRB, 2 users x 55 PRB, 1 user x
- * 110 PRB).  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * 110 PRB).  The network must fit too: at most 121 layer tensors in its
+ * iterations (N_it * (6 + 6 R) <= 121) and at most 1 MiB of weights in kernel
+ * layout (C=64, R=2: N_it <= 7); larger nets get NRX_EINVAL from the header
+ * alone, before anything is launched.  Every call re-lays the weights into
+ * the array (one extra launch, up to 1 MiB of traffic).  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress) and
+ * keeps it for the life of the process; make that first call before any
+ * stream capture, and do not use this entry point across a cudaDeviceReset
+ * (the kept address would be stale).
  * Every call shares the array and keeps the last call's contents (each kernel
  * writes scratch before reading it, so nothing needs clearing); calls whose
  * executions overlap on the GPU race on it and must be ordered.
- * Errors: NRX_EINVAL (bad header, slot, sizes beyond the limit, alignment),
+ * Errors: NRX_EINVAL (bad header, net or slot beyond the limits, alignment),
  * NRX_ECUDA.
  */
 nrx_status nrx_detect_noalloc(const void* weights_header, const float* weights_dev, const void* y,

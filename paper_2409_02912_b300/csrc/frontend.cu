@@ -208,10 +208,13 @@ template cudaError_t launch_state_init<__half>(const Geometry&, const SlotTable&
 // LS + LMMSE + max-log.  Per data RE: H = interpolated LS estimates [B x U],
 // G = H^H H + N0 I, Cholesky G = L L^H, xhat = G^-1 H^H y,
 // d_u = [G^-1 H^H H]_uu, xt_u = xhat_u / d_u, var_u = 1/d_u - 1, then max-log
-// over the user's Gray QAM (per I/Q PAM dimension).  FP32; a RE whose
-// Cholesky pivots spread by more than 1e6 (or is not positive) is redone in
-// FP64.
+// over the user's Gray QAM (per I/Q PAM dimension).  FP32, with the solve
+// taken in FP64 for every RE of a slot whose SNR 10 log10(1/N0) exceeds
+// 20 dB (N0 < kLmmseF64NoiseVar), and for any RE whose FP32 Cholesky pivots
+// spread by more than 1e6 (or is not positive definite).  The REs solved in
+// FP64 are counted in *f64_count.
 // ---------------------------------------------------------------------------
+constexpr float kLmmseF64NoiseVar = 0.01f;  // 10 log10(1/N0) > 20 dB
 template <typename T>
 struct Cx {
   T re, im;
@@ -400,7 +403,7 @@ __device__ __forceinline__ void qam_maxlog_store(float xr, float xi, float inv_v
 
 template <int TW, int U, int B>
 __global__ void __launch_bounds__(256) k_lmmse(Geometry g, SlotTable tab, const float2* __restrict__ y,
-                                               float* __restrict__ llr) {
+                                               float* __restrict__ llr, unsigned long long* __restrict__ f64_count) {
   __shared__ float2 hf[U][2][B][TW];
   const int tile = blockIdx.x, sl = blockIdx.y;
   const int S = g.S;
@@ -417,8 +420,10 @@ __global__ void __launch_bounds__(256) k_lmmse(Geometry g, SlotTable tab, const 
   }
   __syncthreads();
   const float n0 = tab.noise_var[sl];
+  const bool high_snr = n0 < kLmmseF64NoiseVar;  // uniform over the CTA: no divergence
   const int n_data_sym = NRX_SYMBOLS - g.n_dmrs;
   const int dl = g.n_dmrs - 1;
+  unsigned n_f64 = 0;
   for (int i = threadIdx.x; i < n_data_sym * TW; i += blockDim.x) {
     const int e = i % TW, di = i / TW;
     const int s = tile * TW + e;
@@ -437,7 +442,7 @@ __global__ void __launch_bounds__(256) k_lmmse(Geometry g, SlotTable tab, const 
     }
     Cx<float> xh[U];
     float dd[U], ee[U], xr[U], xi[U], iv[U];
-    if (lmmse_solve<float, U, B>(H, yv, n0, xh, dd, ee)) {
+    if (!high_snr && lmmse_solve<float, U, B>(H, yv, n0, xh, dd, ee)) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const float inv_d = 1.f / dd[u];
@@ -447,6 +452,7 @@ __global__ void __launch_bounds__(256) k_lmmse(Geometry g, SlotTable tab, const 
       }
     } else {
       lmmse_solve_f64<U, B>(H, yv, n0, xr, xi, iv);
+      ++n_f64;
     }
     const int r = di * S + s;
 #pragma unroll
@@ -461,35 +467,39 @@ __global__ void __launch_bounds__(256) k_lmmse(Geometry g, SlotTable tab, const 
         qam_maxlog_store<3>(xr[u], xi[u], iv[u], dst);
     }
   }
+  // every thread leaves the loop above, so the whole warp takes part
+  n_f64 = __reduce_add_sync(0xffffffffu, n_f64);
+  if (f64_count && (threadIdx.x & 31) == 0 && n_f64) atomicAdd(f64_count, (unsigned long long)n_f64);
 }
 
 template <int U, int B>
 static cudaError_t launch_lmmse_ub(const Geometry& g, const SlotTable& tab, const float2* y, float* llr,
-                                   cudaStream_t st) {
+                                   unsigned long long* f64_count, cudaStream_t st) {
   constexpr int TW = 32;
   dim3 grid((g.S + TW - 1) / TW, g.n_slots);
-  k_lmmse<TW, U, B><<<grid, 256, 0, st>>>(g, tab, y, llr);
+  k_lmmse<TW, U, B><<<grid, 256, 0, st>>>(g, tab, y, llr, f64_count);
   return cudaGetLastError();
 }
 
 template <int B>
 static cudaError_t launch_lmmse_b(const Geometry& g, const SlotTable& tab, const float2* y, float* llr,
-                                  cudaStream_t st) {
+                                  unsigned long long* f64_count, cudaStream_t st) {
   switch (g.U) {
-    case 1: return launch_lmmse_ub<1, B>(g, tab, y, llr, st);
-    case 2: return launch_lmmse_ub<2, B>(g, tab, y, llr, st);
-    case 3: return launch_lmmse_ub<3, B>(g, tab, y, llr, st);
-    case 4: return launch_lmmse_ub<4, B>(g, tab, y, llr, st);
+    case 1: return launch_lmmse_ub<1, B>(g, tab, y, llr, f64_count, st);
+    case 2: return launch_lmmse_ub<2, B>(g, tab, y, llr, f64_count, st);
+    case 3: return launch_lmmse_ub<3, B>(g, tab, y, llr, f64_count, st);
+    case 4: return launch_lmmse_ub<4, B>(g, tab, y, llr, f64_count, st);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_lmmse(const Geometry& g, const SlotTable& tab, const float2* y, float* llr, cudaStream_t st) {
+cudaError_t launch_lmmse(const Geometry& g, const SlotTable& tab, const float2* y, float* llr,
+                         unsigned long long* f64_count, cudaStream_t st) {
   switch (g.B) {
-    case 1: return launch_lmmse_b<1>(g, tab, y, llr, st);
-    case 2: return launch_lmmse_b<2>(g, tab, y, llr, st);
-    case 4: return launch_lmmse_b<4>(g, tab, y, llr, st);
-    case 8: return launch_lmmse_b<8>(g, tab, y, llr, st);
+    case 1: return launch_lmmse_b<1>(g, tab, y, llr, f64_count, st);
+    case 2: return launch_lmmse_b<2>(g, tab, y, llr, f64_count, st);
+    case 4: return launch_lmmse_b<4>(g, tab, y, llr, f64_count, st);
+    case 8: return launch_lmmse_b<8>(g, tab, y, llr, f64_count, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -109,7 +109,9 @@ template <typename OutT>
 cudaError_t launch_state_init(const Geometry& g, const SlotTable& tab, const float2* y, const InitWeights& w,
                               OutT* s_out, cudaStream_t st);
 
-cudaError_t launch_lmmse(const Geometry& g, const SlotTable& tab, const float2* y, float* llr, cudaStream_t st);
+// f64_count (nullable): incremented by the number of REs solved in FP64.
+cudaError_t launch_lmmse(const Geometry& g, const SlotTable& tab, const float2* y, float* llr,
+                         unsigned long long* f64_count, cudaStream_t st);
 
 // FP32 CUDA-core network kernels.
 cudaError_t launch_mp_f32(const Geometry& g, const IterWeightsF32& w, const float* state, float* z,

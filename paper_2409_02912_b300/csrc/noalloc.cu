@@ -10,11 +10,14 @@
 // device array below instead of context workspaces.
 //
 // The array costs kScratchBytes on every GPU that loads this library, for the
-// life of the process.  All calls share it and it keeps the last call's
-// contents; every kernel of the forward pass writes each scratch element
-// before reading it, so nothing needs clearing between calls.  Calls whose
-// executions overlap on the GPU (different streams, or different host threads
-// without ordering) race on the array: order them.
+// life of the process.  Every call first copies the weights from the caller's
+// blob into the array's weight region in kernel layout (one extra launch, up
+// to 1 MiB of traffic), since the array may hold another net.  All calls
+// share it and it keeps the last call's contents; every kernel of the forward
+// pass writes each scratch element before reading it, so nothing needs
+// clearing between calls.  Calls whose executions overlap on the GPU
+// (different streams, or different host threads without ordering) race on
+// the array: order them.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -38,7 +41,10 @@ void* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  The first call
 // on each device looks it up with cudaGetSymbolAddress (host code cannot use
-// the array's name as a device pointer).
+// the array's name as a device pointer) and keeps it for the life of the
+// process: after a cudaDeviceReset the module is loaded again and the kept
+// address is stale, so this entry point must not be used across a device
+// reset.
 nrx_status scratch_address(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return NRX_ECUDA;
@@ -98,6 +104,19 @@ extern "C" nrx_status nrx_detect_noalloc(const void* weights_header, const float
                                               (long long)R * (2 * (9 * C + (long long)C * C + C))) +
                            (long long)C * C + C + (long long)m_max * C + m_max;
   if (h[7] != expect) return NRX_EINVAL;
+  // The copy plan and the weight region are fixed-size: reject nets that do
+  // not fit from the header alone, before anything is built.  Ops: StateInit
+  // (3), per iteration 6 + 6 R, read-out (4).  Floats: each tensor rounded up
+  // to a multiple of 4.
+  if (7 + N_it * (6 + 6 * R) > kMaxOps) return NRX_EINVAL;
+  {
+    const size_t cc = align4((size_t)C * C), c1 = align4(C), c9 = align4(9 * (size_t)C);
+    const size_t floats = align4((size_t)C * F) + c1 + c9 +
+                          (size_t)N_it * (2 * cc + 2 * c1 + align4((size_t)C * (2 * C + 2)) + c1 +
+                                          (size_t)R * (2 * c9 + 2 * cc + 2 * c1)) +
+                          cc + c1 + align4((size_t)m_max * C) + align4(m_max);
+    if (floats * sizeof(float) > kWeightBytes) return NRX_EINVAL;
+  }
 
   // Slot geometry and per-slot table (one slot).
   const nrx_slot_cfg& c = *cfg;
@@ -141,8 +160,13 @@ extern "C" nrx_status nrx_detect_noalloc(const void* weights_header, const float
   CopyPlan plan;
   memset(&plan, 0, sizeof(plan));
   size_t src = 0, dst = 0;
+  bool plan_full = false;
   auto add = [&](int n_out, int n_in, bool tr) {
     const size_t at = dst;
+    if (plan.n_ops == kMaxOps) {  // unreachable after the header checks; never write past the table
+      plan_full = true;
+      return at;
+    }
     plan.op[plan.n_ops++] = {(int)src, (int)dst, n_out, n_in, tr ? 1 : 0};
     src += (size_t)n_out * n_in;
     dst = align4(dst + (size_t)n_out * n_in);
@@ -168,7 +192,7 @@ extern "C" nrx_status nrx_detect_noalloc(const void* weights_header, const float
   }
   const size_t o_ro1 = add(C, C, true), o_ro1b = add(1, C, false), o_ro2 = add(m_max, C, false),
                o_ro2b = add(1, m_max, false);
-  if (plan.n_ops > kMaxOps) return NRX_EINVAL;
+  if (plan_full) return NRX_EINVAL;
 
   // Scratch budget: weights in the first MiB, then S, z_a, z_b.
   const size_t act = (size_t)g.U * NRX_SYMBOLS * g.S * C;

@@ -38,6 +38,7 @@ struct nrx_ctx {
   int n_heads = 1;
   int8_t head_of_bits[9] = {};  // modulation order -> head
   int* d_err = nullptr;  // device word set by a bounded wait that gave up (tensor-core path)
+  unsigned long long* d_f64 = nullptr;  // LMMSE: REs solved in FP64 since the last reset
   // workspaces [max_slots][max_users][14][S_max][C]
   void* state = nullptr;
   void* z_a = nullptr;
@@ -452,6 +453,7 @@ void nrx_destroy(nrx_ctx* ctx) {
   cudaFree(ctx->y_stage);
   cudaFree(ctx->llr_stage);
   cudaFree(ctx->dmrs_stage);
+  cudaFree(ctx->d_f64);
   for (auto& r : ctx->ev_pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -646,10 +648,15 @@ nrx_status nrx_create(const void* weights, size_t weights_bytes, int32_t num_rx_
   if (cudaMalloc(&ctx->state, act_bytes) != cudaSuccess || cudaMalloc(&ctx->z_a, act_bytes) != cudaSuccess ||
       cudaMalloc(&ctx->z_b, act_bytes) != cudaSuccess || cudaMalloc(&ctx->y_stage, y_bytes) != cudaSuccess ||
       cudaMalloc(&ctx->llr_stage, llr_bytes) != cudaSuccess ||
-      cudaMalloc(&ctx->dmrs_stage, dmrs_bytes) != cudaSuccess) {
+      cudaMalloc(&ctx->dmrs_stage, dmrs_bytes) != cudaSuccess ||
+      cudaMalloc(&ctx->d_f64, sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     nrx_destroy(ctx);
     return NRX_ENOMEM;
+  }
+  if (cudaMemset(ctx->d_f64, 0, sizeof(unsigned long long)) != cudaSuccess) {
+    nrx_destroy(ctx);
+    return NRX_ECUDA;
   }
   ctx->y_stage_bytes = y_bytes;
   ctx->llr_stage_bytes = llr_bytes;
@@ -701,7 +708,7 @@ nrx_status lmmse_detect_batch(nrx_ctx* ctx, int32_t n_slots, const void* y, cons
   cudaError_t e;
   {
     KernelTimer kt(ctx, K_LMMSE, static_cast<cudaStream_t>(stream));
-    e = launch_lmmse(g, tab, static_cast<const float2*>(y), llr, static_cast<cudaStream_t>(stream));
+    e = launch_lmmse(g, tab, static_cast<const float2*>(y), llr, ctx->d_f64, static_cast<cudaStream_t>(stream));
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "lmmse");
   ctx->last_launches = 1;
@@ -711,6 +718,22 @@ nrx_status lmmse_detect_batch(nrx_ctx* ctx, int32_t n_slots, const void* y, cons
 nrx_status lmmse_detect(nrx_ctx* ctx, const void* y, const nrx_slot_cfg* cfg, const int32_t* bits, float* llr,
                         void* stream) {
   return lmmse_detect_batch(ctx, 1, y, cfg, bits, llr, stream);
+}
+
+nrx_status lmmse_fp64_count(nrx_ctx* ctx, int64_t* count, int32_t reset, void* stream) {
+  if (!ctx || !count) return NRX_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stream");
+  unsigned long long v = 0;
+  e = cudaMemcpy(&v, ctx->d_f64, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "read FP64 RE count");
+  *count = (int64_t)v;
+  if (reset) {
+    e = cudaMemset(ctx->d_f64, 0, sizeof(v));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reset FP64 RE count");
+  }
+  return NRX_OK;
 }
 
 nrx_status nrx_detect_batch_host(nrx_ctx* ctx, int32_t n_slots, const void* y_host, const nrx_slot_cfg* cfgs,

@@ -24,6 +24,7 @@ EXPORTED = (
     "lmmse_detect", "nrx_detect_batch_host", "nrx_copy_state", "nrx_get_net", "nrx_last_launch_count",
     "nrx_last_error", "nrx_status_string", "nrx_profile", "nrx_profile_read", "nrx_detect_noalloc",
     "nrx_check", "nrx_dmrs_gold", "nrx_expire_wait", "nrx_detect_batch_host_async", "nrx_host_drain",
+    "lmmse_fp64_count",
 )
 KERNEL_KINDS = 5
 
@@ -99,6 +100,8 @@ def load() -> ctypes.CDLL:
     lib.nrx_detect_noalloc.restype = ctypes.c_int
     lib.nrx_dmrs_gold.argtypes = [I32, P, I32, I32, I32, I32, P, P, P]
     lib.nrx_dmrs_gold.restype = ctypes.c_int
+    lib.lmmse_fp64_count.argtypes = [P, ctypes.POINTER(ctypes.c_int64), I32, P]
+    lib.lmmse_fp64_count.restype = ctypes.c_int
     lib.nrx_status_string.argtypes = [ctypes.c_int]
     lib.nrx_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -184,6 +187,13 @@ class Receiver:
         """Enqueue a bounded device wait that runs out (see nrx.h); the next
         ``nrx_check`` raises NRX_ETIMEDOUT."""
         self._check(self._lib.nrx_expire_wait(self.ctx, int(limit_us), _stream_ptr(stream)), "nrx_expire_wait")
+
+    def lmmse_fp64_count(self, reset: bool = False, stream=None) -> int:
+        """REs whose LMMSE solve ran in FP64 since creation or the last reset."""
+        n = ctypes.c_int64()
+        self._check(self._lib.lmmse_fp64_count(self.ctx, ctypes.byref(n), int(bool(reset)), _stream_ptr(stream)),
+                    "lmmse_fp64_count")
+        return int(n.value)
 
     def nrx_profile(self, enable: bool):
         self._check(self._lib.nrx_profile(self.ctx, int(bool(enable))), "nrx_profile")

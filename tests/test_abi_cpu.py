@@ -157,3 +157,23 @@ def test_every_header_function_is_documented():
             if not (prev.endswith("*/") or prev.startswith("//")):
                 missing.append(f"{os.path.basename(h)}:{m.group(1)}")
     assert not missing, missing
+
+
+def _noalloc_header(B, C, R, N_it, m_max):
+    F = 4 * B + 2
+    n = (C * F + C + 9 * C + N_it * (2 * (C * C + C) + C * (2 * C + 2) + C + R * 2 * (9 * C + C * C + C))
+         + C * C + C + m_max * C + m_max)
+    return np.array([0x5758524E, 1, B, C, R, N_it, m_max, n], dtype=np.int32)
+
+
+@pytest.mark.parametrize("B,C,R,N_it", [(4, 64, 4, 16), (4, 64, 4, 5), (4, 32, 2, 7), (4, 64, 1, 10)])
+def test_noalloc_rejects_nets_beyond_its_tables_without_a_gpu(lib, B, C, R, N_it):
+    """Nets whose copy plan (7 + N_it (6 + 6R) tensors > 128) or kernel-layout
+    weights (> 1 MiB) exceed the allocation-free entry point's fixed tables
+    are rejected from the header alone, before any CUDA call: the pointers
+    below are aligned stand-ins that are never dereferenced."""
+    hdr = _noalloc_header(B, C, R, N_it, 6)
+    cfg = nrx.make_cfgs(1, 2, 2, (2, 11), [0x10000], [1.0])
+    bits = np.array([2, 4], dtype=np.int32)
+    st = lib.nrx_detect_noalloc(hdr.ctypes.data, 0x20000, 0x30000, cfg, bits.ctypes.data, 0x40000, None)
+    assert st == nrx.NRX_EINVAL

@@ -29,13 +29,79 @@ def _receiver(net, slots, prec="fp32"):
 
 
 @pytest.mark.parametrize("workload", ["su_2rx_4prb", "mu2_4rx_24prb", "mu4_4rx_273prb"])
-def test_lmmse_parity(workload):
+def test_lmmse_parity(workload, record_property):
     w, slots = H.slots_for(workload)
     rx = _receiver(w.net, slots)
     y, dmrs, bits, nv = H.device_inputs(slots)
     llr = rx.lmmse_detect_batch(y, dmrs, w.dmrs_symbols, bits, nv).cpu().numpy()
     assert rx.last_launch_count() == 1
-    errs = H.rel_errors(llr, H.oracle_lmmse(slots), slots)
+    refs = H.oracle_lmmse(slots)
+    errs = H.rel_errors(llr, refs, slots)
+    med, p99 = H.elementwise_rel(llr, refs, slots)
+    n64 = rx.lmmse_fp64_count()
+    record_property("elementwise_rel_median_p99", (med, p99))
+    record_property("fp64_res", n64)
+    print(f"LMMSE {workload}: worst {max(errs):.2e}, elementwise median {med:.2e} p99 {p99:.2e}, FP64 REs {n64}")
+    assert max(errs) <= TOL_FP32, errs
+
+
+def _lmmse_batch(slots):
+    """LS + LMMSE over a batch; returns the LLRs and the count of REs solved
+    in FP64 (then reset, which is checked)."""
+    c = slots[0].cfg
+    net = synth.NetConfig(num_rx_ant=c.num_rx_ant, channels=32, res_blocks=1, iterations=1, m_max=6)
+    rx = nrx.Receiver(synth.pack_weights(net, synth.make_weights(net)), c.num_rx_ant, c.num_users, c.num_prb,
+                      len(slots), "fp32")
+    y, dmrs, bits, nv = H.device_inputs(slots)
+    llr = rx.lmmse_detect_batch(y, dmrs, c.dmrs_symbols, bits, nv).cpu().numpy()
+    n64 = rx.lmmse_fp64_count(reset=True)
+    assert rx.lmmse_fp64_count() == 0
+    rx.close()
+    return llr, n64
+
+
+@pytest.mark.parametrize("num_users", [2, 3, 4])
+def test_lmmse_fp64_redo_high_snr(num_users):
+    """Nearly collinear users (one shared steering vector plus a 1e-3
+    perturbation) at 35 and 40 dB: every RE of those slots is solved in FP64
+    (the 20 dB switch), a 10 dB slot in the same batch is not.  On these
+    slots an FP32 solve of the FP32 channel estimates errs by up to 5e-3 (CPU
+    emulation); the FP64 solve stays within the FP32 bound of the oracle."""
+    slots = [H.collinear_slot(num_users, 6, 35.0, 1e-3, 401 + num_users),
+             H.collinear_slot(num_users, 6, 10.0, 1e-3, 501 + num_users),
+             H.collinear_slot(num_users, 6, 40.0, 1e-3, 601 + num_users)]
+    llr, n64 = _lmmse_batch(slots)
+    n_data = slots[0].cfg.num_data_symbols * slots[0].cfg.num_subcarriers
+    assert n64 == 2 * n_data, (n64, n_data)
+    refs = H.oracle_lmmse(slots)
+    errs = H.rel_errors(llr, refs, slots)
+    med, p99 = H.elementwise_rel(llr, refs, slots)
+    print(f"FP64 redo, high SNR, U={num_users}: worst {max(errs):.2e}, median {med:.2e}, p99 {p99:.2e}")
+    assert max(errs) <= TOL_FP32, errs
+
+
+@pytest.mark.parametrize("num_users", [2, 3, 4])
+def test_lmmse_fp64_redo_pivot_spread(num_users):
+    """The pivot criterion at 19 dB (below the SNR switch): a strong, nearly
+    collinear channel gives FP32 Cholesky pivots that spread by far more than
+    1e6 on every RE of one slot, while an ordinary slot in the same batch has
+    none.  The construction keeps the FP32 LS + interpolation exact, so the
+    FP64 solve reproduces the oracle to demapper rounding (1e-5 here), where
+    an FP32 solve of the same REs errs by 0.1 to 2 (CPU emulation): a bound
+    that only the FP64 branch meets."""
+    ill = H.exact_pivot_slot(num_users, 3, 19.0, 700 + num_users)
+    rng = np.random.Generator(np.random.PCG64(800 + num_users))
+    cfg = synth.SlotConfig(num_prb=3, num_users=num_users, num_rx_ant=4, dmrs_symbols=(2,),
+                           bits_per_symbol=ill.cfg.bits_per_symbol, snr_db=10.0, num_taps=4,
+                           delay_spread_s=100e-9, doppler_hz=0.0, ula=False)
+    slots = [ill, synth.make_slot(cfg, rng)]
+    llr, n64 = _lmmse_batch(slots)
+    n_data = ill.cfg.num_data_symbols * ill.cfg.num_subcarriers
+    assert n64 == n_data, (n64, n_data)
+    refs = H.oracle_lmmse(slots)
+    errs = H.rel_errors(llr, refs, slots)
+    print(f"FP64 redo, pivot spread, U={num_users}: per (slot, user) {['%.1e' % e for e in errs]}")
+    assert max(errs[:num_users]) <= 1e-5, errs
     assert max(errs) <= TOL_FP32, errs
 
 
