@@ -1439,6 +1439,7 @@ cudaError_t state_rows_map(CUtensorMap* map, const T* base, int planes, int n_re
 template <typename P>
 cudaError_t launch_block_tc(const Geometry& g, const IterWeightsTC& w, int r, const typename P::T* z_in,
                             typename P::T* z_out, typename P::T* state, bool last, cudaStream_t st) {
+  if constexpr (!P::fp8) return launch_block16_tc<typename P::T>(g, w, r, z_in, z_out, state, last, st);
   if (g.C != 64) return cudaErrorInvalidValue;
   if (reinterpret_cast<uintptr_t>(z_in) & 15) return cudaErrorInvalidValue;  // TMA global address alignment
   const int tps = (g.S + BlkLayout<P>::TW - 1) / BlkLayout<P>::TW;
