@@ -155,6 +155,24 @@ def blas_threads() -> int:
         return os.cpu_count() or 1
 
 
+def oracle_cpu_baseline(slots, W64, net, sample: str) -> dict:
+    """The FP64 oracle timed on the host cores twice over the same slots: with
+    its BLAS pool limited to one thread and with the default pool (numpy's
+    matmuls are the only multi-threaded part).  `value` is the all-core rate;
+    `cores` the BLAS threads that run used; `nproc` the host's CPU count."""
+    w = synth.WORKLOADS[WORKLOAD]
+    n_res = len(slots) * res_per_slot(w)
+    try:
+        from threadpoolctl import threadpool_limits
+        with threadpool_limits(limits=1, user_api="blas"):
+            single = n_res / oracle_slot_seconds(slots, W64, net)
+    except ImportError:
+        single = None
+    allc = n_res / oracle_slot_seconds(slots, W64, net)
+    return {"value": allc, "unit": UNIT, "cores": blas_threads(), "nproc": os.cpu_count(), "kind": "oracle",
+            "single_thread_value": single, "all_core_value": allc, "sample": sample}
+
+
 def res_per_slot(w: synth.Workload) -> int:
     return synth.NUM_SYMBOLS * 12 * w.num_prb
 
@@ -195,6 +213,12 @@ def run_reference(args, rank, world):
     total = sum(secs)
     value = args.steps * res_per_slot(w) / total
     cores = blas_threads()
+    try:  # the same oracle with one BLAS thread, on one slot
+        from threadpoolctl import threadpool_limits
+        with threadpool_limits(limits=1, user_api="blas"):
+            single = res_per_slot(w) / oracle_slot_seconds([slots[0]], W64, w.net)
+    except ImportError:
+        single = None
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
@@ -202,8 +226,10 @@ def run_reference(args, rank, world):
         "data": "synthetic", "config": {"workload": WORKLOAD, "slots_per_step": 1, "users": w.num_users,
                                         "num_rx_ant": w.num_rx_ant, "num_prb": w.num_prb,
                                         "net": "C64 R2 N_it2 m_max6"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} slots of {WORKLOAD}, one per step, FP64 numpy oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "nproc": os.cpu_count(), "kind": "oracle",
+                         "single_thread_value": single, "all_core_value": value,
+                         "sample": f"{args.steps} slots of {WORKLOAD}, one per step, FP64 numpy oracle "
+                                   "(single-thread figure: one more slot with one BLAS thread)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -428,9 +454,8 @@ def run_ours(args, rank, world, local):
         extras["serving"] = serving
         # CPU baseline: the FP64 oracle on one slot of the same workload
         W64 = {k: v.astype(np.float64) for k, v in synth.make_weights(net).items()}
-        secs = oracle_slot_seconds(slots[:1], W64, net)
-        extras["cpu_baseline"] = {"value": res_per_slot(w) / secs, "unit": UNIT, "cores": blas_threads(),
-                                  "kind": "oracle", "sample": f"1 slot of {WORKLOAD} (45864 REs), FP64 numpy oracle"}
+        extras["cpu_baseline"] = oracle_cpu_baseline(
+            slots[:1], W64, net, f"1 slot of {WORKLOAD} (45864 REs), FP64 numpy oracle, single-thread and all-core")
 
     # roofline of the dominant kernel: bound by its arithmetic intensity
     pk, src = peaks()
