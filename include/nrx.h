@@ -177,6 +177,21 @@ nrx_status lmmse_detect(nrx_ctx* ctx, const void* y, const nrx_slot_cfg* cfg,
 nrx_status lmmse_fp64_count(nrx_ctx* ctx, int64_t* count, int32_t reset, void* stream);
 
 /*
+ * Bounds-checked build (the library compiled with -DNRX_DEBUG, e.g.
+ * libnrx_debug.so from the package's build script): every instrumented
+ * shared-memory and global index of the kernels is checked against the
+ * extent of the array it addresses, and an index outside it is counted and
+ * its access skipped (no device assertion, no fault).  Returns the number of
+ * such indices since the last reset (all kernels, all devices' records read
+ * on the current device) and the site number, index and extent of the first;
+ * clears the records if `reset` is non-zero.  Call with no kernel running.
+ * NRX_EUNSUPPORTED from the regular build, NRX_EINVAL for a null
+ * `violations`, NRX_ECUDA on a CUDA error.
+ */
+nrx_status nrx_debug_counters(int64_t* violations, int32_t* first_site, int64_t* first_index,
+                              int64_t* first_extent, int32_t reset);
+
+/*
  * End-to-end variant of nrx_detect_batch on HOST buffers: y_host (complex64,
  * same layout), each cfgs[i].dmrs_seq a HOST pointer, llr_host float32.
  * Copies the inputs into context-owned device staging buffers, runs the NRX,

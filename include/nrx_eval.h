@@ -7,6 +7,8 @@
  * and 171 octal, zero-tail terminated), so that receivers' LLRs can be
  * compared at matched BLER.  The decoder is the soft-input Viterbi algorithm
  * over the 64-state trellis.  The paper has no counterpart of this code.
+ * It also decodes a 5G-structured quasi-cyclic LDPC code (nrx_ldpc_decode)
+ * for transport-block error rates closer to the paper's (Fig. 3).
  *
  * Trellis conventions (shared with the transmitter in synth.py):
  *   state = the six most recent inputs, newest in bit 5; input u moves state
@@ -44,6 +46,42 @@ extern "C" {
  */
 nrx_status nrx_conv_decode(int32_t n_blocks, int32_t n_info, const float* llr, const int64_t* block_offset,
                            const int32_t* perm, uint8_t* info_bits, void* stream);
+
+/*
+ * Layered normalised min-sum decoding of n_blocks code blocks of a
+ * quasi-cyclic LDPC code with the TS 38.212 Sec. 5.3.2 structure (the
+ * transport-block code the paper's receiver feeds, Sec. II; base graph given
+ * by the caller), including the rate recovery of TS 38.212 Sec. 5.4.2.
+ *   llr           device float32: block b's E received LLRs (Eq. 2 sign,
+ *                 ln P(c=1)/P(c=0)) in transmission order start at
+ *                 llr[block_offset[b]]
+ *   block_offset  device int64 [n_blocks]
+ *   E, qm         bits per block (a multiple of qm) and bits per modulation
+ *                 symbol of the qm-row bit interleaver (1..8)
+ *   Z, kb, mb     lifting size (1..384), systematic base columns, base rows
+ *                 (1..64); nb = kb + mb codeword columns, the first 2 Z
+ *                 codeword bits punctured, the circular buffer the other
+ *                 (nb - 2) Z bits, read from its start (redundancy version 0)
+ *   row_ptr, col, shift   HOST int32 edge lists of the base graph in row-major
+ *                 order (row r's edges row_ptr[r] .. row_ptr[r+1]-1; column
+ *                 in [0, nb); circulant shift >= 0, reduced mod Z): check
+ *                 r Z + i meets variable col Z + ((i + shift) mod Z); at most
+ *                 320 edges, 1..16 per row
+ *   iterations    1..100 full passes over the rows in order; with stop_early
+ *                 non-zero, decoding stops after a pass whose hard decisions
+ *                 satisfy every check
+ *   alpha         > 0, the min-sum normalisation (e.g. 0.75)
+ *   c2v           device float32 scratch of n_blocks * nnz * Z values
+ *                 (caller-owned; contents on return unspecified)
+ *   info_bits     device uint8 [n_blocks][kb Z]: decoded systematic bits
+ * One CTA of Z threads per block; the block's nb Z posteriors in shared
+ * memory.  NRX_EINVAL on bad arguments (nothing launched), NRX_ECUDA on a
+ * launch error.
+ */
+nrx_status nrx_ldpc_decode(int32_t n_blocks, const float* llr, const int64_t* block_offset, int32_t E, int32_t qm,
+                           int32_t Z, int32_t kb, int32_t mb, const int32_t* row_ptr, const int32_t* col,
+                           const int32_t* shift, int32_t iterations, float alpha, int32_t stop_early, float* c2v,
+                           uint8_t* info_bits, void* stream);
 
 #ifdef __cplusplus
 }

@@ -1,9 +1,10 @@
-"""Block error rates of the receivers' LLRs with the (133, 171) convolutional
-code (``include/nrx_eval.h``): coded slots from the transmitter in
-``synth``, GPU Viterbi decoding, and the SNR at a target BLER.
+"""Block error rates of the receivers' LLRs (``include/nrx_eval.h``): with
+the (133, 171) convolutional code (GPU Viterbi decoding) and with the
+5G-structured LDPC code (transport blocks, GPU layered min-sum decoding);
+coded slots from the transmitter in ``synth``; the SNR at a target BLER.
 
-Decoding runs in ``libnrx.so`` (``nrx_conv_decode``); this module marshals
-arguments and counts errors.
+Decoding runs in ``libnrx.so`` (``nrx_conv_decode``, ``nrx_ldpc_decode``);
+this module marshals arguments and counts errors.
 """
 from __future__ import annotations
 
@@ -15,7 +16,7 @@ import numpy as np
 
 from . import nrx, synth
 
-EVAL_EXPORTED = ("nrx_conv_decode",)
+EVAL_EXPORTED = ("nrx_conv_decode", "nrx_ldpc_decode")
 
 _configured = False
 
@@ -27,6 +28,9 @@ def load():
         P, I32 = ctypes.c_void_p, ctypes.c_int32
         lib.nrx_conv_decode.argtypes = [I32, I32, P, P, P, P, P]
         lib.nrx_conv_decode.restype = ctypes.c_int
+        lib.nrx_ldpc_decode.argtypes = [I32, P, P, I32, I32, I32, I32, I32, P, P, P, I32, ctypes.c_float, I32, P, P,
+                                        P]
+        lib.nrx_ldpc_decode.restype = ctypes.c_int
         _configured = True
     return lib
 
@@ -43,6 +47,24 @@ def conv_decode(llr, block_offset, n_info: int, perm=None, out=None, stream=None
                                 None if perm is None else perm.data_ptr(), out.data_ptr(), nrx._stream_ptr(stream))
     if st != nrx.NRX_OK:
         raise nrx.NrxError(st, "nrx_conv_decode")
+    return out
+
+
+def ldpc_decode(llr, block_offset, E: int, qm: int, Z: int, bg: synth.LdpcBaseGraph, iterations: int = 20,
+                alpha: float = 0.75, stop_early: bool = True, stream=None):
+    """Layered min-sum decoding (``nrx_ldpc_decode``) of the code blocks whose
+    E received LLRs start at the device int64 offsets ``block_offset`` of the
+    device float32 vector ``llr``; returns device uint8 [n_blocks, kb Z]."""
+    import torch
+    nb = int(block_offset.numel())
+    row_ptr, col, shift = (np.ascontiguousarray(a, dtype=np.int32) for a in bg.edges())
+    out = torch.empty((nb, bg.kb * Z), dtype=torch.uint8, device=llr.device)
+    c2v = torch.empty(max(1, nb * int(row_ptr[-1]) * Z), dtype=torch.float32, device=llr.device)
+    st = load().nrx_ldpc_decode(nb, llr.data_ptr(), block_offset.data_ptr(), E, qm, Z, bg.kb, bg.mb,
+                                row_ptr.ctypes.data, col.ctypes.data, shift.ctypes.data, iterations, alpha,
+                                int(bool(stop_early)), c2v.data_ptr(), out.data_ptr(), nrx._stream_ptr(stream))
+    if st != nrx.NRX_OK:
+        raise nrx.NrxError(st, "nrx_ldpc_decode")
     return out
 
 
@@ -95,6 +117,65 @@ def block_errors(llr, batch: CodedBatch) -> tuple:
                       torch.from_numpy(batch.perm).to(dev)).cpu().numpy()
     err = dec != batch.info
     return int(err.any(axis=1).sum()), int(err.shape[0]), int(err.sum()), int(err.size)
+
+
+@dataclasses.dataclass
+class LdpcBatch:
+    """Same-geometry slots whose users each carry one transport block of
+    rate-matched LDPC code blocks (``synth.make_ldpc_slot``)."""
+
+    slots: List[synth.Slot]
+    bg: synth.LdpcBaseGraph
+    users: List[List[synth.LdpcUser]]   # per slot, per user
+    stream_offset: List[List[int]]       # per slot, per user: first LLR of the user in the packed vector
+
+    @property
+    def bits(self) -> List[List[int]]:
+        return [list(s.cfg.bits_per_symbol) for s in self.slots]
+
+    @property
+    def noise_vars(self) -> List[float]:
+        return [s.cfg.noise_var for s in self.slots]
+
+
+def ldpc_batch(cfgs: Sequence[synth.SlotConfig], seeds: Sequence[int], bg: Optional[synth.LdpcBaseGraph] = None,
+               rate: float = 0.5) -> LdpcBatch:
+    bg = synth.ldpc_base_graph() if bg is None else bg
+    slots, users, offs = [], [], []
+    base = 0
+    for cfg, seed in zip(cfgs, seeds):
+        sl, us = synth.make_ldpc_slot(cfg, np.random.Generator(np.random.PCG64(seed)), bg, rate)
+        n_data = cfg.num_data_symbols * cfg.num_subcarriers
+        o = []
+        for m in cfg.bits_per_symbol:
+            o.append(base)
+            base += n_data * m
+        slots.append(sl)
+        users.append(us)
+        offs.append(o)
+    return LdpcBatch(slots=slots, bg=bg, users=users, stream_offset=offs)
+
+
+def tb_errors(llr, batch: LdpcBatch, iterations: int = 20) -> tuple:
+    """(transport-block errors, transport blocks) of a packed device LLR
+    vector of ``batch``: a user's block is in error when any of its code
+    blocks decodes to a wrong information bit.  Code blocks with the same
+    (Z, E, modulation order) are decoded in one call."""
+    import torch
+    groups = {}
+    for si, (sl, us, offs) in enumerate(zip(batch.slots, batch.users, batch.stream_offset)):
+        for ui, (cu, o, m) in enumerate(zip(us, offs, sl.cfg.bits_per_symbol)):
+            for c in range(cu.info.shape[0]):
+                groups.setdefault((cu.Z, cu.E, m), []).append((si, ui, o + c * cu.E, cu.info[c]))
+    bad = set()
+    for (Z, E, m), items in groups.items():
+        offs = torch.tensor([it[2] for it in items], dtype=torch.int64, device=llr.device)
+        dec = ldpc_decode(llr, offs, E, m, Z, batch.bg, iterations=iterations).cpu().numpy()
+        for (si, ui, _, info), d in zip(items, dec):
+            if not np.array_equal(d, info):
+                bad.add((si, ui))
+    n_tb = sum(len(us) for us in batch.users)
+    return len(bad), n_tb
 
 
 def snr_at_bler(snrs: Sequence[float], bler: Sequence[float], target: float = 0.1) -> Optional[float]:

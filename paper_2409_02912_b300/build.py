@@ -14,6 +14,10 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libnrx.so")
 BUILD_DIR = os.path.join(PKG, "_build")
+# bounds-checked variant: every instrumented kernel index checked, violations
+# counted (nrx_debug_counters) and their accesses skipped
+LIB_DEBUG = os.path.join(PKG, "libnrx_debug.so")
+BUILD_DIR_DEBUG = os.path.join(PKG, "_build_debug")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -37,16 +41,19 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 
-def build(verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile every ``csrc/*.cu`` and link ``libnrx.so``; returns its path."""
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(verbose: bool = False, ptxas_info: bool = False, debug: bool = False) -> str:
+    """Compile every ``csrc/*.cu`` and link ``libnrx.so`` (with ``debug``, the
+    bounds-checked ``libnrx_debug.so``, built with -DNRX_DEBUG); returns its
+    path."""
+    bdir, lib = (BUILD_DIR_DEBUG, LIB_DEBUG) if debug else (BUILD_DIR, LIB)
+    os.makedirs(bdir, exist_ok=True)
     objs = []
     changed = False
     for src in sources():
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
         objs.append(obj)
         if _stale(obj, src) or ptxas_info:
-            cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+            cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *(["-DNRX_DEBUG"] if debug else []), "-c", src, "-o", obj]
             if ptxas_info:
                 cmd += ["-Xptxas", "-v"]
             if verbose:
@@ -57,15 +64,14 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed on {src}")
             changed = True
-    if changed or not os.path.exists(LIB):
-        cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+    if changed or not os.path.exists(lib):
+        cmd = [nvcc(), *ARCH, "-shared", "-o", lib, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed")
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    build(verbose="-v" in sys.argv, ptxas_info="--ptxas-info" in sys.argv)
-    print(LIB)
+    print(build(verbose="-v" in sys.argv, ptxas_info="--ptxas-info" in sys.argv, debug="--debug" in sys.argv))

@@ -99,13 +99,32 @@ static_assert(Lay<__nv_bfloat16>::DYN <= 232448, "shared memory per CTA");
 static_assert(kBuf % 1024 == 0 && (kM1Row * 128) % 1024 == 0, "SW128 atoms stay 1024-byte aligned");
 static_assert(kM1Row + 128 == kRows, "the two M tiles cover the operand rows");
 
+extern __shared__ unsigned char nrx_dyn_smem[];  // the kernel's dynamic shared memory (same base)
+// Bounds-checked build: is [a, a + bytes) inside the dynamic shared memory?
+__device__ __forceinline__ bool smem_ok(uint32_t a, uint32_t bytes, int site) {
+#ifdef NRX_DEBUG
+  uint32_t size;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(size));
+  const uint32_t lo = tc::smem_u32(nrx_dyn_smem);
+  return NRX_IN((long long)a - lo + bytes - 1, size, site) && NRX_IN((long long)a - lo, size, site);
+#else
+  (void)a;
+  (void)bytes;
+  (void)site;
+  return true;
+#endif
+}
 __device__ __forceinline__ uint32_t lds32(uint32_t a) {
-  uint32_t v;
-  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+  uint32_t v = 0;
+  if (smem_ok(a, 4, 401)) asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
   return v;
 }
+__device__ __forceinline__ void sts32c(uint32_t a, uint32_t v) {
+  if (smem_ok(a, 4, 402)) tc::sts32(a, v);
+}
 __device__ __forceinline__ void sts128(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w));
+  if (smem_ok(a, 16, 403))
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w));
 }
 
 // try_wait with a suspend-time hint: a thread whose phase is not complete
@@ -198,7 +217,7 @@ __device__ __forceinline__ void dw_pair(const float* __restrict__ taps, int cp, 
       if (kRelu) v = __hmax2(v, zero);
       word = *reinterpret_cast<uint32_t*>(&v);
     }
-    tc::sts32(out_addr[o] + t * 2048, word);
+    sts32c(out_addr[o] + t * 2048, word);
   };
   auto step = [&](int ti, bool prefetch) {
     if (prefetch)
@@ -404,6 +423,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int vt0 = blockIdx.x * 2 + grp, vstride = gridDim.x * 2;
   tc::pdl_wait();  // from here on the previous kernel's output is read
   if (leader && vt0 < n_tiles) {
+    NRX_IN(vt0 / tps, n_tiles / tps, 404);
     tc::mbar_arrive_expect_tx(in_bar, kInBytes);
     tc::tma_load_3d(g_in, &in_map, 0, (vt0 % tps) * kTW - 2, (vt0 / tps) * NRX_SYMBOLS, in_bar);
     in_pending = true;
@@ -445,6 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (leader && last) {  // state tile for the last block; OUT (same buffer) was read by the previous store
       tc::bulk_wait_read_all();
       tc::mbar_arrive_expect_tx(st_bar, kInBytes);
+      NRX_IN(s0 + kTW - 1, S, 405);
       tc::tma_load_3d(g_so, &st_map, 0, s0 - 2, su * NRX_SYMBOLS, st_bar);
       st_pending = true;
     }
@@ -510,6 +531,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // the next tile's input: IN / P1 is free (DW2 is past the barrier)
           const int nt = tile + vstride;
           if (nt < n_tiles) {
+            NRX_IN(nt / tps, n_tiles / tps, 406);
             tc::mbar_arrive_expect_tx(in_bar, kInBytes);
             tc::tma_load_3d(g_in, &in_map, 0, (nt % tps) * kTW - 2, (nt / tps) * NRX_SYMBOLS, in_bar);
             in_pending = true;
@@ -538,7 +560,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::fence_async_smem();
     tc::tc_fence_before();
     group_sync(bar_id);
-    if (leader) {
+    if (leader && NRX_IN(s0 + kTW - 1, S, 407) && NRX_IN(su, n_tiles / tps, 407)) {
       tc::tma_store_3d(&out_map, 0, s0, su * NRX_SYMBOLS, g_so);
       tc::bulk_commit();
     }
@@ -619,3 +641,5 @@ template cudaError_t launch_block16_tc<__nv_bfloat16>(const Geometry&, const Ite
                                                      __nv_bfloat16*, __nv_bfloat16*, bool, cudaStream_t);
 template cudaError_t launch_block16_tc<__half>(const Geometry&, const IterWeightsTC&, int, const __half*, __half*,
                                               __half*, bool, cudaStream_t);
+
+NRX_DEBUG_READER(debug_read_block_tc)

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "debug.cuh"
+
 #define NRX_MAX_USERS 4
 #define NRX_MAX_RX 8
 #define NRX_MAX_LAUNCH_SLOTS 64
@@ -31,6 +33,7 @@ struct SlotTable {
   int8_t bits[NRX_MAX_LAUNCH_SLOTS][NRX_MAX_USERS];  // m_u per slot and user
   int32_t llr_off[NRX_MAX_LAUNCH_SLOTS][NRX_MAX_USERS];  // float offset of user u's LLRs
   int8_t head[NRX_MAX_LAUNCH_SLOTS][NRX_MAX_USERS];  // Var-IO head of the user's modulation order (0 otherwise)
+  long long llr_total;  // floats of the call's packed LLR vector (bounds-checked build)
 };
 
 // ---------------------------------------------------------------------------
@@ -49,10 +52,11 @@ __device__ __forceinline__ bool occ_shared(int u, int U) { return (u ^ 1) < U; }
 
 // LS on comb position m of user u on DMRS symbol index d:
 //   y(2m+g) * conj(p) / |p|^2,  p = w_u(m) r(m).
-__device__ __forceinline__ float2 ls_pilot(const float2* __restrict__ y_bt,  // y[b][t][:]
-                                           const float2* __restrict__ r,     // r of this DMRS symbol
-                                           int u, int m) {
+__device__ __forceinline__ float2 ls_pilot(const float2* __restrict__ y_bt,  // y[b][t][:S]
+                                           const float2* __restrict__ r,     // r of this DMRS symbol, [S/2]
+                                           int u, int m, int S) {
   const int g = u >> 1;
+  if (!NRX_IN(m, S / 2, 1) || !NRX_IN(2 * m + g, S, 2)) return make_float2(0.f, 0.f);
   float2 p = __ldg(r + m);
   if ((u & 1) && (m & 1)) p = make_float2(-p.x, -p.y);
   const float inv = 1.0f / (p.x * p.x + p.y * p.y);
@@ -62,12 +66,12 @@ __device__ __forceinline__ float2 ls_pilot(const float2* __restrict__ y_bt,  // 
 
 // Estimate number n of user u (after OCC de-spread when the group is shared).
 __device__ __forceinline__ float2 ls_estimate(const float2* __restrict__ y_bt, const float2* __restrict__ r,
-                                              int u, int U, int n) {
+                                              int u, int U, int n, int S) {
   if (occ_shared(u, U)) {
-    float2 a = ls_pilot(y_bt, r, u, 2 * n), b = ls_pilot(y_bt, r, u, 2 * n + 1);
+    float2 a = ls_pilot(y_bt, r, u, 2 * n, S), b = ls_pilot(y_bt, r, u, 2 * n + 1, S);
     return make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
   }
-  return ls_pilot(y_bt, r, u, n);
+  return ls_pilot(y_bt, r, u, n, S);
 }
 
 // Frequency-interpolated estimate of user u at subcarrier s on one DMRS symbol,
@@ -78,12 +82,12 @@ __device__ __forceinline__ float2 ls_interp_freq(const float2* __restrict__ y_bt
   const int spacing = sh ? 4 : 2;
   const int off = sh ? 1 + (u >> 1) : (u >> 1);
   const int N = sh ? S / 4 : S / 2;
-  if (s <= off) return ls_estimate(y_bt, r, u, U, 0);
+  if (s <= off) return ls_estimate(y_bt, r, u, U, 0, S);
   const int last = off + spacing * (N - 1);
-  if (s >= last) return ls_estimate(y_bt, r, u, U, N - 1);
+  if (s >= last) return ls_estimate(y_bt, r, u, U, N - 1, S);
   const int n = (s - off) / spacing;
   const float a = (float)(s - (off + spacing * n)) / (float)spacing;
-  float2 e0 = ls_estimate(y_bt, r, u, U, n), e1 = ls_estimate(y_bt, r, u, U, n + 1);
+  float2 e0 = ls_estimate(y_bt, r, u, U, n, S), e1 = ls_estimate(y_bt, r, u, U, n + 1, S);
   return make_float2(e0.x + a * (e1.x - e0.x), e0.y + a * (e1.y - e0.y));
 }
 

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_state_init(Geometry g, SlotTable tab, c
         const int td = d == 0 ? g.td0 : g.td1;
         v = ls_interp_freq(ys + ((size_t)b * NRX_SYMBOLS + td) * S, tab.dmrs[sl] + (size_t)d * (S / 2), u, g.U, S, s);
       }
-      hf[(d * B + b) * EW + e] = v;
+      if (NRX_IN((d * B + b) * EW + e, 2 * B * EW, 101)) hf[(d * B + b) * EW + e] = v;
     }
     __syncthreads();
     // features of RE tid (registers) and the input layer, channel quad by quad
@@ -93,13 +93,16 @@ __global__ void __launch_bounds__(256) k_state_init(Geometry g, SlotTable tab, c
         float x[F];
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-          const float2 v = __ldg(ys + ((size_t)b * NRX_SYMBOLS + t) * S + s);
+          const size_t yi = ((size_t)b * NRX_SYMBOLS + t) * S + s;
+          const float2 v = NRX_IN(yi, (size_t)B * NRX_SYMBOLS * S, 102) ? __ldg(ys + yi) : make_float2(0.f, 0.f);
           x[2 * b] = v.x;
           x[2 * b + 1] = v.y;
         }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-          const float2 hv = interp_time(g, t, hf[b * EW + e], hf[((g.n_dmrs - 1) * B + b) * EW + e]);
+          const int i1 = ((g.n_dmrs - 1) * B + b) * EW + e;
+          if (!NRX_IN(b * EW + e, 2 * B * EW, 103) || !NRX_IN(i1, 2 * B * EW, 103)) continue;
+          const float2 hv = interp_time(g, t, hf[b * EW + e], hf[i1]);
           x[2 * B + 2 * b] = hv.x;
           x[2 * B + 2 * b + 1] = hv.y;
         }
@@ -136,10 +139,14 @@ __global__ void __launch_bounds__(256) k_state_init(Geometry g, SlotTable tab, c
             kk,
             [&](int ti, int k) {
               const int r = ti * EW + xc + k;
-              return *reinterpret_cast<const float2*>(h + r * C + (((cp >> 1) ^ (r & (NQ - 1))) << 2) + (cp & 1) * 2);
+              const int hi = r * C + (((cp >> 1) ^ (r & (NQ - 1))) << 2) + (cp & 1) * 2;
+              return NRX_IN(hi + 1, NRE * C, 104) ? *reinterpret_cast<const float2*>(h + hi) : make_float2(0.f, 0.f);
             },
             [&](int t, float2 v) {
-              store_pair<OutT>(out_base + ((size_t)t * S + s) * C + 2 * cp, fmaxf(v.x, 0.f), fmaxf(v.y, 0.f));
+              const size_t oi = ((size_t)t * S + s) * C + 2 * cp;
+              if (NRX_IN(oi + 1, (size_t)NRX_SYMBOLS * S * C, 105) &&
+                  NRX_IN(su, (long long)g.n_slots * g.U, 106))
+                store_pair<OutT>(out_base + oi, fmaxf(v.x, 0.f), fmaxf(v.y, 0.f));
             });
       }
     }
@@ -416,7 +423,7 @@ __global__ void __launch_bounds__(256) k_lmmse(Geometry g, SlotTable tab, const 
       const int td = d == 0 ? g.td0 : g.td1;
       v = ls_interp_freq(ys + ((size_t)b * NRX_SYMBOLS + td) * S, tab.dmrs[sl] + (size_t)d * (S / 2), u, U, S, s);
     }
-    hf[u][d][b][e] = v;
+    if (NRX_IN(((u * 2 + d) * B + b) * TW + e, U * 2 * B * TW, 107)) hf[u][d][b][e] = v;
   }
   __syncthreads();
   const float n0 = tab.noise_var[sl];
@@ -432,7 +439,8 @@ __global__ void __launch_bounds__(256) k_lmmse(Geometry g, SlotTable tab, const 
     Cx<float> H[U][B], yv[B];
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-      const float2 v = __ldg(ys + ((size_t)b * NRX_SYMBOLS + t) * S + s);
+      const size_t yi = ((size_t)b * NRX_SYMBOLS + t) * S + s;
+      const float2 v = NRX_IN(yi, (size_t)B * NRX_SYMBOLS * S, 108) ? __ldg(ys + yi) : make_float2(0.f, 0.f);
       yv[b] = {v.x, v.y};
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -459,6 +467,7 @@ __global__ void __launch_bounds__(256) k_lmmse(Geometry g, SlotTable tab, const 
     for (int u = 0; u < U; ++u) {
       const int m = tab.bits[sl][u];
       float* dst = llr + tab.llr_off[sl][u] + (size_t)r * m;
+      if (!NRX_IN(tab.llr_off[sl][u] + (long long)r * m + m - 1, tab.llr_total, 109)) continue;
       if (m == 2)
         qam_maxlog_store<1>(xr[u], xi[u], iv[u], dst);
       else if (m == 4)
@@ -503,3 +512,5 @@ cudaError_t launch_lmmse(const Geometry& g, const SlotTable& tab, const float2* 
   }
   return cudaErrorInvalidValue;
 }
+
+NRX_DEBUG_READER(debug_read_frontend)

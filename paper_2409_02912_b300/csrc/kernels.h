@@ -46,6 +46,16 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 
 constexpr int kStateInitTile = 16;  // subcarriers per StateInit CTA
 
+// Bounds-checked build records, one per instrumented source file (debug.cuh):
+// [0] violations, [1] site, [2] index and [3] extent of the first.  Without
+// NRX_DEBUG they read as zero.
+cudaError_t debug_read_frontend(unsigned long long* out, bool reset);
+cudaError_t debug_read_net_f32(unsigned long long* out, bool reset);
+cudaError_t debug_read_net_tc(unsigned long long* out, bool reset);
+cudaError_t debug_read_block_tc(unsigned long long* out, bool reset);
+cudaError_t debug_read_ldpc(unsigned long long* out, bool reset);
+cudaError_t debug_read_train(unsigned long long* out, bool reset);
+
 template <typename T>
 __device__ __forceinline__ T store_cast(float v);
 template <>

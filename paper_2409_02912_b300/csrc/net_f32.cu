@@ -68,8 +68,9 @@ __global__ void __launch_bounds__(kThreads) k_mp_f32(Geometry g, IterWeightsF32 
     const int c = i % C, row = i / C;
     const int u = row / Cf::kRE, re = re0 + row % Cf::kRE;
     float v = 0.f;
-    if (u < U && re < n_re) v = __ldg(state + (((size_t)sl * U + u) * n_re + re) * C + c);
-    sa[row * Cf::LD + c] = v;
+    const size_t si = (((size_t)sl * U + u) * n_re + re) * C + c;
+    if (u < U && re < n_re && NRX_IN(si, (size_t)g.n_slots * U * n_re * C, 201)) v = __ldg(state + si);
+    if (NRX_IN(row * Cf::LD + c, Cf::ROWS * Cf::LD, 202)) sa[row * Cf::LD + c] = v;
   }
   __syncthreads();
   const int cg = threadIdx.x % Cf::CG, rg = threadIdx.x / Cf::CG;
@@ -126,7 +127,8 @@ __global__ void __launch_bounds__(kThreads) k_mp_f32(Geometry g, IterWeightsF32 
     o.y = fmaf(pf, wf.y, fmaf(pt, wt.y, acc[i][1]));
     o.z = fmaf(pf, wf.z, fmaf(pt, wt.z, acc[i][2]));
     o.w = fmaf(pf, wf.w, fmaf(pt, wt.w, acc[i][3]));
-    *reinterpret_cast<float4*>(z + (((size_t)sl * U + u) * n_re + re) * C + c0) = o;
+    const size_t zi = (((size_t)sl * U + u) * n_re + re) * C + c0;
+    if (NRX_IN(zi + 3, (size_t)g.n_slots * U * n_re * C, 203)) *reinterpret_cast<float4*>(z + zi) = o;
   }
 }
 
@@ -179,7 +181,9 @@ __global__ void __launch_bounds__(kThreads) k_block_f32(Geometry g, const float*
     const int c = i % C, e = (i / C) % Cf::IW, t = i / (C * Cf::IW);
     const int s = s0 - 2 + e;
     float v = 0.f;
-    if (s >= 0 && s < S) v = __ldg(z_in + (base + (size_t)t * S + s) * C + c);
+    const size_t act = (size_t)g.n_slots * g.U * NRX_SYMBOLS * S * C;
+    if (s >= 0 && s < S && NRX_IN((base + (size_t)t * S + s) * C + c, act, 204))
+      v = __ldg(z_in + (base + (size_t)t * S + s) * C + c);
     zin[(t * Cf::IW + e) * Cf::LD + c] = v;
   }
   __syncthreads();
@@ -245,6 +249,7 @@ __global__ void __launch_bounds__(kThreads) k_block_f32(Geometry g, const float*
       const float* res = zin + (t * Cf::IW + x + 2) * Cf::LD + c0;
       float4 o = make_float4(acc[i][0] + res[0], acc[i][1] + res[1], acc[i][2] + res[2], acc[i][3] + res[3]);
       const size_t off = (base + (size_t)t * S + s) * C + c0;
+      if (!NRX_IN(off + 3, (size_t)g.n_slots * g.U * NRX_SYMBOLS * S * C, 205)) continue;
       if (last) {
         float4 sv = *reinterpret_cast<const float4*>(state + off);
         sv.x += o.x;
@@ -293,7 +298,8 @@ __global__ void __launch_bounds__(kThreads) k_readout_f32(Geometry g, SlotTable 
     float v = 0.f;
     if (r < g.n_data) {
       const int t = g.data_t[r / S], s = r % S;
-      v = __ldg(state + (base + (size_t)t * S + s) * C + c);
+      if (NRX_IN((base + (size_t)t * S + s) * C + c, (size_t)g.n_slots * g.U * NRX_SYMBOLS * S * C, 206))
+        v = __ldg(state + (base + (size_t)t * S + s) * C + c);
     }
     sa[j * Cf::LD + c] = v;
   }
@@ -316,7 +322,7 @@ __global__ void __launch_bounds__(kThreads) k_readout_f32(Geometry g, SlotTable 
     float a = __ldg(ro2_b + o);
     const float* wr = ro2 + o * C;
     for (int k = 0; k < C; ++k) a = fmaf(__ldg(wr + k), sb[j * Cf::LD + k], a);
-    dst[(size_t)r * m + o] = a;
+    if (NRX_IN(tab.llr_off[sl][u] + (long long)r * m + o, tab.llr_total, 207)) dst[(size_t)r * m + o] = a;
   }
 }
 
@@ -378,3 +384,5 @@ cudaError_t launch_readout_f32(const Geometry& g, const SlotTable& tab, const Re
   }
   return cudaGetLastError();
 }
+
+NRX_DEBUG_READER(debug_read_net_f32)

@@ -265,6 +265,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
   // tile: the next tile's S goes into this tile's G buffer as soon as PW2 is
   // done with it, so the copy overlaps this tile's z epilogue.
   auto issue_s = [&](int t_next, unsigned char* dst) {
+    NRX_IN((t_next % tiles_per_slot) * nre, n_re, 301);
+    NRX_IN((t_next / tiles_per_slot) * U, g.n_slots * U, 302);
     tc::mbar_arrive_expect_tx(in_bar, (uint32_t)(U * nre * 128));
     tc::tma_load_3d(dst, &smap, 0, (t_next % tiles_per_slot) * nre, (t_next / tiles_per_slot) * U, in_bar);
   };
@@ -301,7 +303,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
         const int row = i >> 3, ch = i & 7;
         const int u = row / nre, j = row % nre, re = re0 + j;
         v[it] = make_uint4(0, 0, 0, 0);
-        if (u < U && re < n_re)
+        if (u < U && re < n_re &&
+            NRX_IN((((size_t)sl * U + u) * n_re + re) * C64, (size_t)g.n_slots * U * n_re * C64, 303))
           v[it] = __ldg(reinterpret_cast<const uint4*>(state + (((size_t)sl * U + u) * n_re + re) * C64) + ch);
       }
 #pragma unroll
@@ -569,6 +572,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
       tc::fence_async_smem();
       __syncthreads();
       if (tid == 0) {
+        NRX_IN(re0, n_re, 304);
+        NRX_IN(sl * U, g.n_slots * U, 304);
         tc::tma_store_3d(&zmap, 0, re0, sl * U, sm + MpL::XCH);
         tc::bulk_commit();
       }
@@ -580,7 +585,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_mp_tc(Geometry g, IterWeightsTC
         const int i = tid + it * kThreads;
         const int row = i >> 3, ch = i & 7;
         const int u = row / nre, j = row % nre, re = re0 + j;
-        if (u < U && re < n_re)
+        if (u < U && re < n_re &&
+            NRX_IN((((size_t)sl * U + u) * n_re + re) * C64 + 8 * ch + 7, (size_t)g.n_slots * U * n_re * C64, 305))
           reinterpret_cast<uint4*>(z + (((size_t)sl * U + u) * n_re + re) * C64)[ch] =
               *reinterpret_cast<const uint4*>(sm + MpL::XCH + row * 128 + ((ch ^ (row & 7)) << 4));
       }
@@ -769,6 +775,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
     // that ended it, and their generic writes were fenced for the async proxy.
     if (tid == 0) {
       tc::mbar_arrive_expect_tx(in_bar, L::kInBytes);
+      NRX_IN(s0, S, 306);
+      NRX_IN(su, g.n_slots * U, 306);
       tc::tma_load_3d(sm + L::ZB, &zmap, 0, s0 - 2, su * NRX_SYMBOLS, in_bar);
     }
     tma_pending = true;
@@ -964,7 +972,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
       for (int it = 0; it < kOutIt; ++it) {
         rq[it] = make_uint4(0, 0, 0, 0);
         sq[it] = make_uint4(0, 0, 0, 0);
-        if (s0 + out_x[it] < S) {
+        if (s0 + out_x[it] < S &&
+            NRX_IN(tbase + out_off[it] + 7, (size_t)g.n_slots * U * NRX_SYMBOLS * S * C64, 307)) {
           rq[it] = __ldg(reinterpret_cast<const uint4*>(z_in + tbase + out_off[it]));
           if (last) sq[it] = *reinterpret_cast<const uint4*>(state + tbase + out_off[it]);  // written here
         }
@@ -972,7 +981,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_block_tc(Geometry g, const uint
 #pragma unroll
       for (int it = 0; it < kOutIt; ++it) {
         if (s0 + out_x[it] >= S) continue;
+        if (!NRX_IN(tbase + out_off[it] + 7, (size_t)g.n_slots * U * NRX_SYMBOLS * S * C64, 308)) continue;
         const int sr = out_sr[it];
+        if (!NRX_IN(sr, NRX_SYMBOLS * L::TW, 309)) continue;
         const float4* src = reinterpret_cast<const float4*>(sr < 128 ? sm + L::A + sr * 256 : sm + L::ZB + (sr - 128) * 256);
         const float4 a = src[(2 * out_c8) ^ (sr & 7)], b = src[(2 * out_c8 + 1) ^ (sr & 7)];
         float o[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
@@ -1047,6 +1058,9 @@ __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, R
   bool timed_out = false;
   auto issue_rows = [&](int t_next) {
     const int su_n = t_next / tiles_per_su, k = t_next % tiles_per_su;
+    NRX_IN((k % chunks) * 128, S, 310);
+    NRX_IN(k / chunks, NRX_SYMBOLS - g.n_dmrs, 310);
+    NRX_IN(su_n, g.n_slots * U, 310);
     tc::mbar_arrive_expect_tx(in_bar, 128u * 128u);
     tc::tma_load_3d(sm + L::A, &rmap, 0, (k % chunks) * 128, su_n * NRX_SYMBOLS + g.data_t[k / chunks], in_bar);
   };
@@ -1097,7 +1111,9 @@ __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, R
         const int i = tid + it * 128;
         const int rw = i >> 3, ch = i & 7, s = s0 + rw;
         v[it] = make_uint4(0, 0, 0, 0);
-        if (s < S) v[it] = __ldg(reinterpret_cast<const uint4*>(state + (base + (size_t)t_sym * S + s) * C64) + ch);
+        if (s < S && NRX_IN((base + (size_t)t_sym * S + s) * C64 + 8 * ch + 7,
+                            (size_t)g.n_slots * U * NRX_SYMBOLS * S * C64, 311))
+          v[it] = __ldg(reinterpret_cast<const uint4*>(state + (base + (size_t)t_sym * S + s) * C64) + ch);
       }
 #pragma unroll
       for (int it = 0; it < 8; ++it) {
@@ -1158,6 +1174,7 @@ __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, R
       const int m = tab.bits[sl][u];
       float* dst = llr + tab.llr_off[sl][u] + (size_t)rd * m;
       for (int o = 0; o < m; ++o) {
+        if (!NRX_IN(tab.llr_off[sl][u] + (long long)rd * m + o, tab.llr_total, 312)) break;
         float a = sb2[o];
 #pragma unroll
         for (int k = 0; k < 64; ++k) a = fmaf(w2[o * 64 + k], h[k], a);
@@ -1508,3 +1525,5 @@ NRX_INSTANTIATE(PolFP16)
 NRX_INSTANTIATE(PolFP8)
 template cudaError_t launch_to_f32<__nv_bfloat16>(const __nv_bfloat16*, float*, size_t, cudaStream_t);
 template cudaError_t launch_to_f32<__half>(const __half*, float*, size_t, cudaStream_t);
+
+NRX_DEBUG_READER(debug_read_net_tc)

@@ -155,6 +155,7 @@ extern "C" nrx_status nrx_detect_noalloc(const void* weights_header, const float
     tab.llr_off[0][u] = (int32_t)off;
     off += (size_t)g.n_data * m;
   }
+  tab.llr_total = (long long)off;
 
   // Weight layout plan (same layout the context path builds on the host).
   CopyPlan plan;

@@ -196,6 +196,7 @@ nrx_status prepare(nrx_ctx* ctx, int32_t n_slots, const nrx_slot_cfg* cfgs, cons
   }
   *iterations = its;
   *llr_total = off;
+  tab->llr_total = (long long)off;
   return NRX_OK;
 }
 
@@ -718,6 +719,43 @@ nrx_status lmmse_detect_batch(nrx_ctx* ctx, int32_t n_slots, const void* y, cons
 nrx_status lmmse_detect(nrx_ctx* ctx, const void* y, const nrx_slot_cfg* cfg, const int32_t* bits, float* llr,
                         void* stream) {
   return lmmse_detect_batch(ctx, 1, y, cfg, bits, llr, stream);
+}
+
+nrx_status nrx_debug_counters(int64_t* violations, int32_t* first_site, int64_t* first_index,
+                              int64_t* first_extent, int32_t reset) {
+#ifndef NRX_DEBUG
+  (void)violations;
+  (void)first_site;
+  (void)first_index;
+  (void)first_extent;
+  (void)reset;
+  return NRX_EUNSUPPORTED;
+#else
+  if (!violations) return NRX_EINVAL;
+  cudaError_t (*const readers[])(unsigned long long*, bool) = {debug_read_frontend, debug_read_net_f32,
+                                                               debug_read_net_tc,   debug_read_block_tc,
+                                                               debug_read_ldpc,     debug_read_train};
+  int64_t total = 0;
+  bool have_first = false;
+  for (auto rd : readers) {
+    unsigned long long rec[4];
+    if (rd(rec, reset != 0) != cudaSuccess) return NRX_ECUDA;
+    total += (int64_t)rec[0];
+    if (rec[0] && !have_first) {
+      have_first = true;
+      if (first_site) *first_site = (int32_t)rec[1];
+      if (first_index) *first_index = (int64_t)rec[2];
+      if (first_extent) *first_extent = (int64_t)rec[3];
+    }
+  }
+  if (!have_first) {
+    if (first_site) *first_site = 0;
+    if (first_index) *first_index = 0;
+    if (first_extent) *first_extent = 0;
+  }
+  *violations = total;
+  return NRX_OK;
+#endif
 }
 
 nrx_status lmmse_fp64_count(nrx_ctx* ctx, int64_t* count, int32_t reset, void* stream) {

@@ -521,3 +521,5 @@ nrx_status nrx_train_adam(int64_t n, float* w, const float* g, float* m1, float*
 }
 
 }  // extern "C"
+
+NRX_DEBUG_READER(debug_read_train)

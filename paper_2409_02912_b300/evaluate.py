@@ -2,8 +2,9 @@
 on coded synthetic slots: BLER over an SNR grid and the SNR at 10% BLER,
 the operating point at which the paper compares receivers (Sec. IV).
 
-Every step runs in ``libnrx.so`` (detection and Viterbi decoding); this
-module draws the slots (``synth``), calls the receivers and counts errors.
+Every step runs in ``libnrx.so`` (detection, Viterbi and LDPC decoding);
+this module draws the slots (``synth``), calls the receivers and counts
+errors.
 """
 from __future__ import annotations
 
@@ -39,6 +40,7 @@ class Sweep:
     slots_per_point: int = 32
     n_info: int = 1024
     seed: int = 900
+    ldpc_rate: float = 0.5
 
 
 def sweep_batches(sw: Sweep):
@@ -58,17 +60,44 @@ def sweep_batches(sw: Sweep):
     return out
 
 
+def ldpc_sweep_batches(sw: Sweep, bg=None):
+    """The sweep's slot draws (different seeds from the convolutional-code
+    slots) carrying LDPC transport blocks at rate ``sw.ldpc_rate``."""
+    bg = synth.ldpc_base_graph() if bg is None else bg
+    out = []
+    for k, snr in enumerate(sw.snrs):
+        cfgs, seeds = [], []
+        for i in range(sw.slots_per_point):
+            seed = sw.seed * 100_000 + 50_000 + k * 1_000 + i
+            rng = np.random.Generator(np.random.PCG64(seed))
+            cfgs.append(synth.SlotConfig(num_prb=sw.num_prb, num_users=sw.num_users, num_rx_ant=sw.num_rx_ant,
+                                         dmrs_symbols=sw.dmrs_symbols, bits_per_symbol=(sw.bits,) * sw.num_users,
+                                         snr_db=float(snr), num_taps=12,
+                                         delay_spread_s=float(rng.uniform(10e-9, 300e-9)),
+                                         doppler_hz=float(rng.uniform(0.0, 400.0)), ula=True))
+            seeds.append(seed + 7)
+        out.append(bler.ldpc_batch(cfgs, seeds, bg, sw.ldpc_rate))
+    return out
+
+
 def compare(blob: bytes, precisions: Sequence[str] = ("fp32", "bf16", "fp16", "fp8"), sw: Sweep = Sweep(),
-            batches=None, untrained_blob: Optional[bytes] = None, early_exit: bool = True) -> Dict[str, dict]:
+            batches=None, untrained_blob: Optional[bytes] = None, early_exit: bool = True,
+            ldpc: bool = True, ldpc_batches=None) -> Dict[str, dict]:
     """BLER curves and SNR at 10% BLER of the NRX (each precision) and of
     LS+LMMSE on the same coded slots; with ``early_exit`` also the FP32 NRX
     stopped after each number of CGNN iterations below N_it (the multi-loss
-    read-outs, Sec. II-B and Sec. IV-B)."""
+    read-outs, Sec. II-B and Sec. IV-B).  With ``ldpc``, each receiver also
+    gets a transport-block error rate curve with the LDPC code ("tbler_ldpc"
+    and "snr_at_10pct_tbler_ldpc"), on slots of its own."""
     import torch
     batches = sweep_batches(sw) if batches is None else batches
+    if ldpc and ldpc_batches is None:
+        ldpc_batches = ldpc_sweep_batches(sw)
     n = sw.slots_per_point
     dev = [(torch.from_numpy(synth.stack_batch(b.slots)).cuda(),
             torch.from_numpy(np.stack([s.dmrs for s in b.slots])).cuda()) for b in batches]
+    ldev = [] if not ldpc else [(torch.from_numpy(synth.stack_batch(b.slots)).cuda(),
+                                 torch.from_numpy(np.stack([s.dmrs for s in b.slots])).cuda()) for b in ldpc_batches]
     res: Dict[str, dict] = {}
 
     def run(name, rx, fn):
@@ -78,6 +107,13 @@ def compare(blob: bytes, precisions: Sequence[str] = ("fp32", "bf16", "fp16", "f
             e, nb, _, _ = bler.block_errors(llr, b)
             curve.append(e / max(nb, 1))
         res[name] = {"bler": curve, "snr_at_10pct": bler.snr_at_bler(sw.snrs, curve, 0.1)}
+        if ldpc:
+            tcurve = []
+            for b, (y, dm) in zip(ldpc_batches, ldev):
+                e, nt = bler.tb_errors(fn(rx, b, y, dm), b)
+                tcurve.append(e / max(nt, 1))
+            res[name]["tbler_ldpc"] = tcurve
+            res[name]["snr_at_10pct_tbler_ldpc"] = bler.snr_at_bler(sw.snrs, tcurve, 0.1)
 
     def nrx_fn(rx, b, y, dm):
         return rx.nrx_detect_batch(y, dm, sw.dmrs_symbols, b.bits)
@@ -101,4 +137,9 @@ def compare(blob: bytes, precisions: Sequence[str] = ("fp32", "bf16", "fp16", "f
         rx.close()
     res["_sweep"] = {"snrs": list(sw.snrs), "blocks_per_point": int(batches[0].info.shape[0]),
                      "slots_per_point": n, "num_prb": sw.num_prb, "bits": sw.bits}
+    if ldpc:
+        b0 = ldpc_batches[0]
+        res["_sweep"]["ldpc"] = {"transport_blocks_per_point": sum(len(u) for u in b0.users),
+                                 "code_blocks_per_tb": int(b0.users[0][0].info.shape[0]),
+                                 "Z": int(b0.users[0][0].Z), "E": int(b0.users[0][0].E), "rate": sw.ldpc_rate}
     return res

@@ -13,7 +13,9 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libnrx.so")
+# The library the binding loads: libnrx.so, or another build of the same
+# sources named by NRX_LIBRARY (the bounds-checked libnrx_debug.so).
+_LIB_PATH = os.environ.get("NRX_LIBRARY") or os.path.join(os.path.dirname(os.path.abspath(__file__)), "libnrx.so")
 
 NRX_OK, NRX_EINVAL, NRX_ENOMEM, NRX_ECUDA, NRX_ETIMEDOUT, NRX_EUNSUPPORTED = range(6)
 NRX_FP32, NRX_BF16, NRX_FP16, NRX_FP8 = 0, 1, 2, 3
@@ -24,7 +26,7 @@ EXPORTED = (
     "lmmse_detect", "nrx_detect_batch_host", "nrx_copy_state", "nrx_get_net", "nrx_last_launch_count",
     "nrx_last_error", "nrx_status_string", "nrx_profile", "nrx_profile_read", "nrx_detect_noalloc",
     "nrx_check", "nrx_dmrs_gold", "nrx_expire_wait", "nrx_detect_batch_host_async", "nrx_host_drain",
-    "lmmse_fp64_count",
+    "lmmse_fp64_count", "nrx_debug_counters",
 )
 KERNEL_KINDS = 5
 
@@ -100,12 +102,26 @@ def load() -> ctypes.CDLL:
     lib.nrx_detect_noalloc.restype = ctypes.c_int
     lib.nrx_dmrs_gold.argtypes = [I32, P, I32, I32, I32, I32, P, P, P]
     lib.nrx_dmrs_gold.restype = ctypes.c_int
+    lib.nrx_debug_counters.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(I32),
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), I32]
+    lib.nrx_debug_counters.restype = ctypes.c_int
     lib.lmmse_fp64_count.argtypes = [P, ctypes.POINTER(ctypes.c_int64), I32, P]
     lib.lmmse_fp64_count.restype = ctypes.c_int
     lib.nrx_status_string.argtypes = [ctypes.c_int]
     lib.nrx_status_string.restype = ctypes.c_char_p
     _lib = lib
     return lib
+
+
+def debug_counters(reset: bool = False) -> dict:
+    """Bounds-checked build only: {"violations", "site", "index", "extent"} of
+    the indices found outside their arrays since the last reset (see nrx.h)."""
+    n, site, idx, ext = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    st = load().nrx_debug_counters(ctypes.byref(n), ctypes.byref(site), ctypes.byref(idx), ctypes.byref(ext),
+                                   int(bool(reset)))
+    if st != NRX_OK:
+        raise NrxError(st, "nrx_debug_counters")
+    return {"violations": n.value, "site": site.value, "index": idx.value, "extent": ext.value}
 
 
 def _status_name(s: int) -> str:

@@ -364,6 +364,41 @@ def pack_weights(net: NetConfig, weights: Dict[str, np.ndarray]) -> bytes:
     return hdr + b"".join(a.tobytes() for a in arrs)
 
 
+def unpack_weights(blob: bytes) -> tuple:
+    """Inverse of ``pack_weights``: (NetConfig, weights) of a blob."""
+    hdr = struct.unpack("<8i", blob[:32])
+    if hdr[0] != WEIGHT_MAGIC or hdr[1] not in (WEIGHT_VERSION, WEIGHT_VERSION_VAR_IO):
+        raise ValueError("not an NRX weight blob")
+    net = NetConfig(num_rx_ant=hdr[2], channels=hdr[3], res_blocks=hdr[4], iterations=hdr[5], m_max=hdr[6],
+                    var_io=hdr[1] == WEIGHT_VERSION_VAR_IO)
+    flat = np.frombuffer(blob[32:], dtype=np.float32)
+    if flat.size != hdr[7]:
+        raise ValueError("blob size does not match its header")
+    out, o = {}, 0
+    for name, shape in weight_layout(net):
+        n = int(np.prod(shape))
+        out[name] = flat[o:o + n].reshape(shape).copy()
+        o += n
+    if o != flat.size:
+        raise ValueError("blob size does not match the layout")
+    return net, out
+
+
+def widen_readout(net: NetConfig, weights: Dict[str, np.ndarray], m_max: int) -> Dict[str, np.ndarray]:
+    """Weights of a single-head network with its ReadoutLLRs widened to m_max
+    outputs: the first rows keep the trained bit outputs, the added rows
+    (higher-order bits) start at zero."""
+    if net.var_io or m_max < net.m_max:
+        raise ValueError("only a single-head read-out can be widened")
+    out = {k: v.copy() for k, v in weights.items()}
+    w2 = np.zeros((m_max, net.channels), np.float32)
+    b2 = np.zeros((m_max,), np.float32)
+    w2[:net.m_max] = weights["ro2.w"]
+    b2[:net.m_max] = weights["ro2.b"]
+    out["ro2.w"], out["ro2.b"] = w2, b2
+    return out
+
+
 def zero_like_residual(net: NetConfig, weights: Dict[str, np.ndarray]) -> Dict[str, np.ndarray]:
     """Copy of ``weights`` with every message-MLP output layer, CNN-update input
     layer and residual branch output layer zeroed (used by composition tests)."""
@@ -465,6 +500,218 @@ def training_batch(slots: Sequence[Slot], m_max: int) -> TrainingBatch:
     return TrainingBatch(y=stack_batch(slots), dmrs=np.stack([s.dmrs for s in slots]), bits=bits, m_u=m_u, h=h,
                          dmrs_symbols=tuple(s0.dmrs_symbols),
                          noise_var=np.array([s.cfg.noise_var for s in slots]))
+
+
+# ----------------------------------------------------------------------------
+# 5G-structured quasi-cyclic LDPC code (transport-block decoding, Sec. II)
+# ----------------------------------------------------------------------------
+# TS 38.212 Sec. 5.3.2 structure: a base graph of mb rows and nb = kb + mb
+# columns whose nonzero entries are circulant shifts V; lifting by Z from the
+# set a 2^j (a in {2, 3, 5, 7, 9, 11, 13, 15}, Z <= 384) with shift V mod Z;
+# kb systematic columns, a 4 x 4 core parity block (first column of weight 3
+# with shifts 1, 0, 1 and a dual diagonal of identities, so the core parities
+# follow from the row sums in linear time) and one degree-1 parity column per
+# extension row; the first 2 Z systematic bits are punctured.  The standard's
+# shift tables are not reproduced here: this build's base graph draws the
+# systematic / extension connections and their shifts from a seeded rule
+# (BG2-like degrees, 4-cycles rejected at the lifting sizes used).
+
+LDPC_A = (2, 3, 5, 7, 9, 11, 13, 15)
+LDPC_ZMAX = 384
+
+
+def ldpc_lifting_sizes() -> List[int]:
+    """The lifting sizes a 2^j <= 384 of TS 38.212 Sec. 5.3.2, ascending."""
+    return sorted({a << j for a in LDPC_A for j in range(8) if (a << j) <= LDPC_ZMAX})
+
+
+@dataclasses.dataclass(frozen=True)
+class LdpcBaseGraph:
+    kb: int             # systematic columns
+    mb: int             # rows (4 core + extension)
+    V: np.ndarray       # int32 [mb, kb + mb]: shift in [0, 384), -1 where the block is zero
+
+    @property
+    def nb(self) -> int:
+        return self.kb + self.mb
+
+    def edges(self):
+        """Row-major edge list: (row_ptr int32 [mb+1], col int32 [nnz], shift int32 [nnz])."""
+        rows, cols = np.nonzero(self.V >= 0)
+        row_ptr = np.zeros(self.mb + 1, dtype=np.int32)
+        np.add.at(row_ptr, rows + 1, 1)
+        return np.cumsum(row_ptr).astype(np.int32), cols.astype(np.int32), self.V[rows, cols].astype(np.int32)
+
+
+def _four_cycles(V: np.ndarray, Z: int) -> int:
+    """Number of length-4 cycles of the lifted graph's base pattern at size Z
+    (row pairs x column pairs with V11 - V12 + V22 - V21 = 0 mod Z)."""
+    n = 0
+    nz = V >= 0
+    for r1 in range(V.shape[0]):
+        for r2 in range(r1 + 1, V.shape[0]):
+            cs = np.nonzero(nz[r1] & nz[r2])[0]
+            for a in range(len(cs)):
+                for b in range(a + 1, len(cs)):
+                    c1, c2 = cs[a], cs[b]
+                    if (V[r1, c1] - V[r1, c2] + V[r2, c2] - V[r2, c1]) % Z == 0:
+                        n += 1
+    return n
+
+
+def ldpc_base_graph(kb: int = 10, mb: int = 42, seed: int = 17, check_z=(96, 192, 384)) -> LdpcBaseGraph:
+    """BG2-like base graph (kb = 10, mb = 42 by default): core rows 0..3 on
+    every-few systematic columns plus the core parity block; extension row r
+    on 2..4 of the first kb + 4 columns plus its own parity column kb + r.
+    Shifts are redrawn (up to a bound) where they close a 4-cycle at the
+    lifting sizes ``check_z``."""
+    if kb < 2 or mb < 4:
+        raise ValueError("need kb >= 2 and the 4 core rows")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nb = kb + mb
+    V = -np.ones((mb, nb), dtype=np.int64)
+    # core rows: systematic connections (each column in at least two core rows)
+    deg = [max(2, kb - 3), max(2, kb - 4), max(2, kb - 3), max(2, kb - 4)]
+    for r in range(4):
+        V[r, rng.choice(kb, size=min(deg[r], kb), replace=False)] = 0
+    for c in range(kb):
+        while np.count_nonzero(V[:4, c] >= 0) < 2:
+            V[rng.integers(0, 4), c] = 0
+    # extension rows: a few of the systematic and core parity columns
+    for r in range(4, mb):
+        d = 4 if r < 12 else (3 if r < 28 else 2)
+        V[r, rng.choice(kb + 4, size=min(d, kb + 4), replace=False)] = 0
+    free = V >= 0  # entries whose shift is drawn
+    V[free] = rng.integers(0, LDPC_ZMAX, size=int(free.sum()))
+    # core parity block (fixed shifts) and the extension parities (identities)
+    core = {(0, kb): 1, (1, kb): 0, (3, kb): 1, (0, kb + 1): 0, (1, kb + 1): 0, (1, kb + 2): 0, (2, kb + 2): 0,
+            (2, kb + 3): 0, (3, kb + 3): 0}
+    for (r, c), v in core.items():
+        V[r, c] = v
+    for r in range(4, mb):
+        V[r, kb + r] = 0
+    fixed = np.zeros_like(free)
+    for (r, c) in core:
+        fixed[r, c] = True
+    for r in range(4, mb):
+        fixed[r, kb + r] = True
+    drawn = free & ~fixed
+    for _ in range(200):  # redraw shifts that close 4-cycles at the checked sizes
+        bad = [z for z in check_z if _four_cycles(V, z)]
+        if not bad:
+            break
+        z = bad[0]
+        for r1 in range(mb):
+            for r2 in range(r1 + 1, mb):
+                cs = np.nonzero((V[r1] >= 0) & (V[r2] >= 0))[0]
+                for a in range(len(cs)):
+                    for b in range(a + 1, len(cs)):
+                        c1, c2 = cs[a], cs[b]
+                        if (V[r1, c1] - V[r1, c2] + V[r2, c2] - V[r2, c1]) % z == 0:
+                            for (rr, cc) in ((r2, c2), (r2, c1), (r1, c2), (r1, c1)):
+                                if drawn[rr, cc]:
+                                    V[rr, cc] = rng.integers(0, LDPC_ZMAX)
+                                    break
+    return LdpcBaseGraph(kb=kb, mb=mb, V=V.astype(np.int32))
+
+
+def _circ(x: np.ndarray, v: int) -> np.ndarray:
+    """Circulant P^v applied to a length-Z block: (P^v x)[i] = x[(i + v) mod Z]."""
+    return np.roll(x, -v, axis=-1)
+
+
+def ldpc_encode(bg: LdpcBaseGraph, Z: int, info: np.ndarray) -> np.ndarray:
+    """Systematic encoding of info bits (uint8 [..., kb Z]) into the full
+    codeword (uint8 [..., nb Z]): core parities from the core row sums (the
+    weight-3 first parity column sums to the identity), then the dual
+    diagonal, then each extension parity from its row."""
+    info = np.asarray(info, dtype=np.uint8)
+    kb, mb, nb = bg.kb, bg.mb, bg.nb
+    lead = info.shape[:-1]
+    x = np.zeros(lead + (nb, Z), dtype=np.uint8)
+    x[..., :kb, :] = info.reshape(lead + (kb, Z))
+    V = bg.V % Z
+
+    def row_sum(r, cols):
+        acc = np.zeros(lead + (Z,), dtype=np.uint8)
+        for c in cols:
+            if bg.V[r, c] >= 0:
+                acc ^= _circ(x[..., c, :], int(V[r, c]))
+        return acc
+    sysc = range(kb)
+    s = [row_sum(r, sysc) for r in range(4)]
+    p0 = s[0] ^ s[1] ^ s[2] ^ s[3]
+    x[..., kb, :] = p0
+    x[..., kb + 1, :] = s[0] ^ _circ(p0, int(V[0, kb]))
+    x[..., kb + 2, :] = s[1] ^ p0 ^ x[..., kb + 1, :]
+    x[..., kb + 3, :] = s[2] ^ x[..., kb + 2, :]
+    for r in range(4, mb):
+        x[..., kb + r, :] = row_sum(r, range(kb + 4))
+    return x.reshape(lead + (nb * Z,))
+
+
+def ldpc_rate_match(bg: LdpcBaseGraph, Z: int, cw: np.ndarray, E: int, qm: int) -> np.ndarray:
+    """TS 38.212 Sec. 5.4.2 bit selection and interleaving (redundancy version
+    0, no filler bits): the circular buffer is the codeword without its first
+    2 Z bits; E bits are read from its start (wrapping), then written row-wise
+    into qm rows and read column-wise (bit i of modulation symbol j is
+    e[i E/qm + j])."""
+    if E % qm:
+        raise ValueError("E must be a multiple of the modulation order")
+    w = np.asarray(cw)[..., 2 * Z:]
+    e = w[..., np.arange(E) % w.shape[-1]]
+    return e.reshape(e.shape[:-1] + (qm, E // qm)).swapaxes(-1, -2).reshape(e.shape)
+
+
+def ldpc_params(n_bits: int, qm: int, rate: float = 0.5, kb: int = 10) -> tuple:
+    """Code blocks for a user stream of n_bits coded bits at modulation order
+    qm: (number of blocks C, lifting size Z, E bits per block), with C the
+    fewest blocks of at most kb * 384 information bits at the target rate and Z
+    the largest lifting size with kb Z <= rate * E."""
+    C = max(1, int(np.ceil(rate * n_bits / (kb * LDPC_ZMAX))))
+    E = qm * (n_bits // (C * qm))
+    zs = [z for z in ldpc_lifting_sizes() if kb * z <= rate * E]
+    if not zs:
+        raise ValueError("stream too short for a code block")
+    return C, zs[-1], E
+
+
+@dataclasses.dataclass
+class LdpcUser:
+    info: np.ndarray        # uint8 [C, kb Z]
+    Z: int
+    E: int
+
+
+def ldpc_coded_bits(bg: LdpcBaseGraph, n_bits: int, qm: int, rng: np.random.Generator, rate: float = 0.5):
+    """A user's bit stream of n_bits (the receivers' LLR order) filled with C
+    rate-matched code blocks back to back, random filler after them.  Returns
+    (bits uint8 [n_bits], LdpcUser)."""
+    C, Z, E = ldpc_params(n_bits, qm, rate, bg.kb)
+    info = rng.integers(0, 2, size=(C, bg.kb * Z), dtype=np.uint8)
+    stream = rng.integers(0, 2, size=n_bits, dtype=np.uint8)
+    stream[:C * E] = ldpc_rate_match(bg, Z, ldpc_encode(bg, Z, info), E, qm).reshape(-1)
+    return stream, LdpcUser(info=info, Z=Z, E=E)
+
+
+def make_ldpc_slot(cfg: SlotConfig, rng: np.random.Generator, bg: LdpcBaseGraph, rate: float = 0.5):
+    """A slot whose users carry LDPC code blocks (one transport block per user
+    and slot).  Returns (Slot, [LdpcUser per user])."""
+    S = cfg.num_subcarriers
+    n_data = cfg.num_data_symbols * S
+    users, bits = [], []
+    for m in cfg.bits_per_symbol:
+        stream, cu = ldpc_coded_bits(bg, n_data * m, m, rng, rate)
+        bits.append(stream.reshape(n_data, m))
+        users.append(cu)
+    dmrs = slot_dmrs(cfg, rng)
+    x = transmit_grid(cfg, dmrs, bits)
+    h = tdl_channel(cfg, rng)
+    n0 = cfg.noise_var
+    noise = np.sqrt(n0 / 2.0) * (rng.standard_normal((cfg.num_rx_ant, NUM_SYMBOLS, S))
+                                + 1j * rng.standard_normal((cfg.num_rx_ant, NUM_SYMBOLS, S)))
+    y = np.einsum("ubts,uts->bts", h, x) + noise
+    return Slot(cfg=cfg, y=y.astype(np.complex64), dmrs=dmrs, bits=bits, h=h, x=x), users
 
 
 # ----------------------------------------------------------------------------

@@ -698,14 +698,16 @@ def _make_batch(args):
 def fit(workload: synth.Workload, seconds: float, lr: float = 2e-3, lr_final: float = 5e-5, gamma: float = 1.0,
         seed: int = 1, resume: Optional[str] = None, workers: Optional[int] = None, log_every: int = 2000,
         trainer: Optional[Trainer] = None, precision: str = "fp32", simulator: str = "cpu",
-        recompute: Optional[bool] = None, active_users: bool = True) -> Trainer:
+        recompute: Optional[bool] = None, active_users: bool = True, init_blob: Optional[bytes] = None) -> Trainer:
     """Train for a wall-clock budget on fresh random batches of ``workload``
     (random MCS association and SNR offsets, Sec. IV-A; with ``active_users``
     the number of active users drawn per batch, Sec. II-B), with an exponential
     learning-rate decay from lr to lr_final over the budget.  Batches are
     generated by a pool of spawned CPU workers, at most 48 ahead of the GPU;
     each step is one CUDA-graph replay.  The read-out layers start at zero
-    (LLRs and channel estimates 0, i.e. BCE ln 2) unless resuming."""
+    (LLRs and channel estimates 0, i.e. BCE ln 2) unless resuming; with
+    ``init_blob`` the network starts from that inference blob instead (a
+    narrower single-head read-out widened with zero rows)."""
     import multiprocessing as mp
     import os
     import time
@@ -716,6 +718,12 @@ def fit(workload: synth.Workload, seconds: float, lr: float = 2e-3, lr_final: fl
         for k in ("ro2.w", "ro2.b"):
             W[k][...] = 0.0
         Wc["chest.2.w"][...] = 0.0
+        if init_blob is not None:
+            net0, W0 = synth.unpack_weights(init_blob)
+            if (net0.num_rx_ant, net0.channels, net0.res_blocks, net0.iterations, net0.var_io) != \
+                    (net.num_rx_ant, net.channels, net.res_blocks, net.iterations, net.var_io):
+                raise ValueError("the initial blob's network does not match the workload's")
+            W = synth.widen_readout(net0, W0, net.m_max) if net0.m_max != net.m_max else W0
         trainer = Trainer(net, W, Wc, lr=lr, gamma=gamma, precision=precision, recompute=recompute)
     if resume:
         trainer.restore(resume)
@@ -767,6 +775,8 @@ def main(argv=None):
     ap.add_argument("--lr-final", type=float, default=5e-5)
     ap.add_argument("--gamma", type=float, default=1.0)
     ap.add_argument("--resume", default=None)
+    ap.add_argument("--init-blob", default=None,
+                    help="start from this inference blob (its read-out widened to the workload's m_max)")
     ap.add_argument("--precision", default="fp32", choices=("fp32", "bf16"), help="GEMM compute of the passes")
     ap.add_argument("--simulator", default="cpu", choices=("cpu", "gpu"),
                     help="draw batches with CPU workers (synth) or on the GPU (nrx_train_simulate)")
@@ -783,7 +793,8 @@ def main(argv=None):
                              mcs_choices=tuple(int(v) for v in a.mcs.split(",")))
     tr = fit(wl, a.seconds, lr=a.lr, lr_final=a.lr_final, gamma=a.gamma, resume=a.resume, precision=a.precision,
              simulator=a.simulator, recompute={"auto": None, "on": True, "off": False}[a.recompute],
-             active_users=not a.all_users)
+             active_users=not a.all_users,
+             init_blob=open(a.init_blob, "rb").read() if a.init_blob else None)
     if a.checkpoint:
         tr.save(a.checkpoint)
     with open(a.out, "wb") as f:

@@ -177,3 +177,26 @@ def test_noalloc_rejects_nets_beyond_its_tables_without_a_gpu(lib, B, C, R, N_it
     bits = np.array([2, 4], dtype=np.int32)
     st = lib.nrx_detect_noalloc(hdr.ctypes.data, 0x20000, 0x30000, cfg, bits.ctypes.data, 0x40000, None)
     assert st == nrx.NRX_EINVAL
+
+
+def test_ldpc_decode_validates_without_a_gpu(lib):
+    """Host-side checks of nrx_ldpc_decode run before any launch."""
+    from paper_2409_02912_b300 import bler
+    el = bler.load()
+    bg = synth.ldpc_base_graph()
+    rp, col, sh = (np.ascontiguousarray(a, dtype=np.int32) for a in bg.edges())
+    args = lambda **k: dict(dict(n=1, E=64, qm=2, Z=16, kb=bg.kb, mb=bg.mb, rp=rp, col=col, sh=sh, it=10), **k)
+
+    def call(a):
+        return el.nrx_ldpc_decode(a["n"], None, None, a["E"], a["qm"], a["Z"], a["kb"], a["mb"], a["rp"].ctypes.data,
+                                  a["col"].ctypes.data, a["sh"].ctypes.data, a["it"], 0.75, 1, None, None, None)
+    assert call(args(n=0)) == nrx.NRX_OK                   # nothing to decode
+    assert call(args()) == nrx.NRX_EINVAL                  # null device buffers
+    assert call(args(n=0, Z=385)) == nrx.NRX_EINVAL        # lifting size
+    assert call(args(n=0, E=63)) == nrx.NRX_EINVAL         # E not a multiple of qm
+    assert call(args(n=0, it=0)) == nrx.NRX_EINVAL
+    bad = col.copy()
+    bad[0] = bg.nb
+    assert call(args(n=0, col=bad)) == nrx.NRX_EINVAL      # column out of range
+    dense = np.arange(bg.mb + 1, dtype=np.int32) * 17      # 17 edges per row
+    assert call(args(n=0, rp=dense)) == nrx.NRX_EINVAL

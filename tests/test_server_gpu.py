@@ -170,3 +170,39 @@ def test_short_load_run_completes_every_slot():
         assert r["latency_us"]["all_p50"] is not None and r["latency_us"]["all_p50"] > 0
     finally:
         srv.close()
+
+
+def test_served_mixed_prb_load_matches_oracle():
+    """Slots of 24, 51, 106 and 273 PRB with one to four users and mixed
+    QPSK / 16-QAM / 64-QAM, submitted together to a BF16 server with four
+    PRB buckets and a far deadline (so the NRX serves every slot): each
+    served slot's LLRs match the FP64 oracle within the BF16 bound."""
+    from oracle import nrx_oracle as O
+    from tests import helpers as H
+    net = synth.WORKLOADS["mu4_4rx_273prb"].net  # C=64, R=2, N_it=2, m_max=6
+    blob = synth.pack_weights(net, synth.make_weights(net))
+    W64 = H.weights64(net)
+    geoms = [(24, 4), (51, 3), (106, 2), (273, 4), (24, 1), (51, 4), (106, 3)]
+    slots = []
+    for i, (prb, U) in enumerate(geoms):
+        rng = np.random.Generator(np.random.PCG64(900 + i))
+        cfg = synth.SlotConfig(num_prb=prb, num_users=U, num_rx_ant=4, dmrs_symbols=(2, 11),
+                               bits_per_symbol=tuple(int(rng.choice([2, 4, 6])) for _ in range(U)),
+                               snr_db=float(rng.uniform(-2, 20)), num_taps=12,
+                               delay_spread_s=float(rng.uniform(10e-9, 300e-9)),
+                               doppler_hz=float(rng.uniform(0, 400)), ula=True)
+        slots.append(synth.make_slot(cfg, rng))
+    srv = server.Server(blob, 4, [24, 51, 106, 273], max_users=4, max_batch=8, precision="bf16",
+                        deadline_us=1e7, hbm_budget_bytes=24 << 30)
+    try:
+        out, comps = _serve(srv, slots)
+    finally:
+        srv.close()
+    assert len(comps) == len(slots) and all(c.receiver == 0 for c in comps)
+    for s, got in zip(slots, out):
+        ref = H.oracle_nrx([s], W64, net)
+        errs = H.rel_errors(got, ref, [s])
+        med, p99 = H.elementwise_rel(got, ref, [s])
+        print(f"served {s.cfg.num_prb} PRB x {s.cfg.num_users} users {s.cfg.bits_per_symbol}: "
+              f"worst {max(errs):.2e}, elementwise median {med:.2e} p99 {p99:.2e}")
+        assert max(errs) <= 2e-2, (s.cfg.num_prb, s.cfg.num_users, errs)
