@@ -273,7 +273,16 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl", device_id=dev)
     w = synth.WORKLOADS[WORKLOAD]
     net = w.net
-    blob = synth.pack_weights(net, synth.make_weights(net))
+    from paper_2409_02912_b300 import evaluate
+    if os.path.exists(evaluate.TRAINED_MU4):  # the trained network of this workload, else seeded weights
+        with open(evaluate.TRAINED_MU4, "rb") as f:
+            blob = f.read()
+        weights_name = os.path.basename(evaluate.TRAINED_MU4)
+        W_bench = synth.unpack_weights(blob)[1]
+    else:
+        W_bench = synth.make_weights(net)
+        blob = synth.pack_weights(net, W_bench)
+        weights_name = "seeded Gaussian init (PCG64(42))"
     batch = args.batch or w.batch
     slots = synth.workload_slots(w, batch, start=rank_slot_start(rank, batch))
     n = len(slots)
@@ -423,7 +432,6 @@ def run_ours(args, rank, world, local):
                          "d2h_bytes_per_step": int(n_llr * 4), "mode": "pipelined host calls",
                          "synchronous_value": res_step / sync_s}
         # matched BLER: the trained network on a coded sweep of the 24-PRB two-user workload
-        from paper_2409_02912_b300 import evaluate
         with open(evaluate.TRAINED_MU2, "rb") as f:
             q = evaluate.compare(f.read())
         snr10 = {k: v["snr_at_10pct"] for k, v in q.items() if not k.startswith("_")}
@@ -434,7 +442,27 @@ def run_ours(args, rank, world, local):
             "snr_db_at_10pct_bler": snr10,
             "delta_vs_fp32_db": {k: (None if v is None or ref10 is None else v - ref10) for k, v in snr10.items()},
             "bler": {k: v["bler"] for k, v in q.items() if not k.startswith("_")},
-            "snrs_db": q["_sweep"]["snrs"], "blocks_per_point": q["_sweep"]["blocks_per_point"]}
+            "snr_db_at_10pct_tbler_ldpc": {k: v.get("snr_at_10pct_tbler_ldpc") for k, v in q.items()
+                                           if not k.startswith("_")},
+            "tbler_ldpc": {k: v.get("tbler_ldpc") for k, v in q.items() if not k.startswith("_")},
+            "snrs_db": q["_sweep"]["snrs"], "blocks_per_point": q["_sweep"]["blocks_per_point"],
+            "ldpc": q["_sweep"].get("ldpc")}
+        if os.path.exists(evaluate.TRAINED_MU4):  # the benchmarked network on its own workload
+            q4 = evaluate.compare(blob, precisions=("fp32", "bf16", "fp16"), sw=evaluate.MU4_SWEEP,
+                                  early_exit=False)
+            s4 = {k: v["snr_at_10pct"] for k, v in q4.items() if not k.startswith("_")}
+            extras["quality"]["mu4_4rx_273prb"] = {
+                "workload": "8 x 273 PRB slots' geometry: 4 users x QPSK/16-QAM/64-QAM per user, 4 Rx; "
+                            "(133,171) code and LDPC transport blocks",
+                "weights": weights_name, "snr_db_at_10pct_bler": s4,
+                "delta_vs_fp32_db": {k: (None if v is None or s4.get("nrx_fp32") is None else v - s4["nrx_fp32"])
+                                     for k, v in s4.items()},
+                "bler": {k: v["bler"] for k, v in q4.items() if not k.startswith("_")},
+                "snr_db_at_10pct_tbler_ldpc": {k: v.get("snr_at_10pct_tbler_ldpc") for k, v in q4.items()
+                                               if not k.startswith("_")},
+                "tbler_ldpc": {k: v.get("tbler_ldpc") for k, v in q4.items() if not k.startswith("_")},
+                "snrs_db": q4["_sweep"]["snrs"], "blocks_per_point": q4["_sweep"]["blocks_per_point"],
+                "ldpc": q4["_sweep"].get("ldpc")}
         with open(evaluate.TRAINED_MU2_VAR_IO, "rb") as f:
             qv = evaluate.compare(f.read(), precisions=("fp32", "bf16"), early_exit=False)
         extras["quality"]["var_io"] = {
@@ -453,7 +481,7 @@ def run_ours(args, rank, world, local):
             srv.close()
         extras["serving"] = serving
         # CPU baseline: the FP64 oracle on one slot of the same workload
-        W64 = {k: v.astype(np.float64) for k, v in synth.make_weights(net).items()}
+        W64 = {k: v.astype(np.float64) for k, v in W_bench.items()}
         extras["cpu_baseline"] = oracle_cpu_baseline(
             slots[:1], W64, net, f"1 slot of {WORKLOAD} (45864 REs), FP64 numpy oracle, single-thread and all-core")
 

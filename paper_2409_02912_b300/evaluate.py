@@ -24,12 +24,20 @@ TRAINED_MU2 = os.path.join(WEIGHTS_DIR, "nrx_mu2_4rx_c64_r2_it2.bin")
 # (Var-IO, Sec. III; blob version 2), initialised from the masked network's
 # checkpoint and trained 135 k further steps on the GPU simulator.
 TRAINED_MU2_VAR_IO = os.path.join(WEIGHTS_DIR, "nrx_mu2_4rx_c64_r2_it2_varIO.bin")
+# The benchmarked network (mu4_4rx_273prb: C=64, R=2, N_it=2, m_max=6), trained
+# at config 4's shape: 51-PRB slots, up to four users with the number of active
+# users drawn per batch, QPSK / 16-QAM / 64-QAM, batches of 64, BF16 GEMMs with
+# FP32 master weights, on the GPU simulator; started from TRAINED_MU2 with its
+# read-out widened to six outputs.
+TRAINED_MU4 = os.path.join(WEIGHTS_DIR, "nrx_mu4_4rx_c64_r2_it2.bin")
 
 
 @dataclasses.dataclass(frozen=True)
 class Sweep:
-    """Coded-slot SNR sweep: geometry of the mu2_4rx_24prb workload, fixed
-    modulation order for both users, config-2 channel distributions."""
+    """Coded-slot SNR sweep: by default the geometry of the mu2_4rx_24prb
+    workload with one modulation order for both users; ``mcs`` draws each
+    user's order per slot instead (the mixed-MCS 273-PRB 4-user workload);
+    config-2 channel distributions."""
 
     num_prb: int = 24
     num_users: int = 2
@@ -41,6 +49,24 @@ class Sweep:
     n_info: int = 1024
     seed: int = 900
     ldpc_rate: float = 0.5
+    mcs: tuple = ()              # if given, each user's modulation order is drawn from it per slot
+    ldpc_slots_per_point: int = 0  # slots per point of the LDPC sweep (0: slots_per_point)
+
+
+# Coded sweep of the benchmarked workload: 273 PRB, four users, modulation order
+# drawn per user and slot; 4 slots (~1300 convolutional code blocks) per SNR
+# point, 32 slots (128 transport blocks, ~3000 LDPC code blocks) per point for
+# the LDPC curve.
+MU4_SWEEP = Sweep(num_prb=273, num_users=4, mcs=(2, 4, 6), snrs=(4.0, 8.0, 12.0, 16.0, 20.0, 24.0),
+                  slots_per_point=4, ldpc_slots_per_point=32)
+
+
+def _slot_cfg(sw: Sweep, snr: float, rng: np.random.Generator) -> synth.SlotConfig:
+    bits = tuple(int(rng.choice(sw.mcs)) for _ in range(sw.num_users)) if sw.mcs else (sw.bits,) * sw.num_users
+    return synth.SlotConfig(num_prb=sw.num_prb, num_users=sw.num_users, num_rx_ant=sw.num_rx_ant,
+                            dmrs_symbols=sw.dmrs_symbols, bits_per_symbol=bits, snr_db=float(snr), num_taps=12,
+                            delay_spread_s=float(rng.uniform(10e-9, 300e-9)),
+                            doppler_hz=float(rng.uniform(0.0, 400.0)), ula=True)
 
 
 def sweep_batches(sw: Sweep):
@@ -50,11 +76,7 @@ def sweep_batches(sw: Sweep):
         for i in range(sw.slots_per_point):
             seed = sw.seed * 100_000 + k * 1_000 + i
             rng = np.random.Generator(np.random.PCG64(seed))
-            cfgs.append(synth.SlotConfig(num_prb=sw.num_prb, num_users=sw.num_users, num_rx_ant=sw.num_rx_ant,
-                                         dmrs_symbols=sw.dmrs_symbols, bits_per_symbol=(sw.bits,) * sw.num_users,
-                                         snr_db=float(snr), num_taps=12,
-                                         delay_spread_s=float(rng.uniform(10e-9, 300e-9)),
-                                         doppler_hz=float(rng.uniform(0.0, 400.0)), ula=True))
+            cfgs.append(_slot_cfg(sw, snr, rng))
             seeds.append(seed + 7)
         out.append(bler.coded_batch(cfgs, seeds, n_info=sw.n_info))
     return out
@@ -67,14 +89,10 @@ def ldpc_sweep_batches(sw: Sweep, bg=None):
     out = []
     for k, snr in enumerate(sw.snrs):
         cfgs, seeds = [], []
-        for i in range(sw.slots_per_point):
+        for i in range(sw.ldpc_slots_per_point or sw.slots_per_point):
             seed = sw.seed * 100_000 + 50_000 + k * 1_000 + i
             rng = np.random.Generator(np.random.PCG64(seed))
-            cfgs.append(synth.SlotConfig(num_prb=sw.num_prb, num_users=sw.num_users, num_rx_ant=sw.num_rx_ant,
-                                         dmrs_symbols=sw.dmrs_symbols, bits_per_symbol=(sw.bits,) * sw.num_users,
-                                         snr_db=float(snr), num_taps=12,
-                                         delay_spread_s=float(rng.uniform(10e-9, 300e-9)),
-                                         doppler_hz=float(rng.uniform(0.0, 400.0)), ula=True))
+            cfgs.append(_slot_cfg(sw, snr, rng))
             seeds.append(seed + 7)
         out.append(bler.ldpc_batch(cfgs, seeds, bg, sw.ldpc_rate))
     return out
@@ -93,7 +111,7 @@ def compare(blob: bytes, precisions: Sequence[str] = ("fp32", "bf16", "fp16", "f
     batches = sweep_batches(sw) if batches is None else batches
     if ldpc and ldpc_batches is None:
         ldpc_batches = ldpc_sweep_batches(sw)
-    n = sw.slots_per_point
+    n = max(sw.slots_per_point, sw.ldpc_slots_per_point if ldpc else 0)
     dev = [(torch.from_numpy(synth.stack_batch(b.slots)).cuda(),
             torch.from_numpy(np.stack([s.dmrs for s in b.slots])).cuda()) for b in batches]
     ldev = [] if not ldpc else [(torch.from_numpy(synth.stack_batch(b.slots)).cuda(),
@@ -136,7 +154,8 @@ def compare(blob: bytes, precisions: Sequence[str] = ("fp32", "bf16", "fp16", "f
         run("nrx_untrained", rx, nrx_fn)
         rx.close()
     res["_sweep"] = {"snrs": list(sw.snrs), "blocks_per_point": int(batches[0].info.shape[0]),
-                     "slots_per_point": n, "num_prb": sw.num_prb, "bits": sw.bits}
+                     "slots_per_point": sw.slots_per_point, "num_prb": sw.num_prb, "num_users": sw.num_users,
+                     "bits": list(sw.mcs) if sw.mcs else sw.bits}
     if ldpc:
         b0 = ldpc_batches[0]
         res["_sweep"]["ldpc"] = {"transport_blocks_per_point": sum(len(u) for u in b0.users),

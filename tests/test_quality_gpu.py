@@ -99,3 +99,63 @@ def test_var_io_network_beats_lmmse():
         if snr < 12.0:
             assert q["nrx_fp32"]["bler"][i] < q["lmmse"]["bler"][i], snr
     assert abs(q["nrx_bf16"]["snr_at_10pct"] - q["nrx_fp32"]["snr_at_10pct"]) <= 0.2
+
+
+# ---- the benchmarked network on its own workload: 273 PRB, 4 users, QPSK / 16-QAM / 64-QAM ----
+
+@pytest.fixture(scope="module")
+def quality_mu4():
+    with open(evaluate.TRAINED_MU4, "rb") as f:
+        blob = f.read()
+    return blob, evaluate.compare(blob, precisions=("fp32", "bf16", "fp16"), sw=evaluate.MU4_SWEEP,
+                                  early_exit=False)
+
+
+def test_mu4_sweep_has_1000_blocks_per_point(quality_mu4):
+    _, q = quality_mu4
+    assert q["_sweep"]["blocks_per_point"] >= 1000
+    ld = q["_sweep"]["ldpc"]
+    assert ld["transport_blocks_per_point"] >= 100 and ld["transport_blocks_per_point"] * ld["code_blocks_per_tb"] >= 1000
+
+
+def test_mu4_bf16_and_fp16_within_0p2_db_of_fp32(quality_mu4):
+    """At the 10% operating point of both codes (block error rate with the
+    convolutional code, transport-block error rate with the LDPC code)."""
+    _, q = quality_mu4
+    for key in ("snr_at_10pct", "snr_at_10pct_tbler_ldpc"):
+        ref = q["nrx_fp32"][key]
+        assert ref is not None, key
+        for p in ("bf16", "fp16"):
+            assert abs(q[f"nrx_{p}"][key] - ref) <= 0.2, (key, p, q[f"nrx_{p}"][key], ref)
+
+
+def test_mu4_fp32_and_bf16_blocks_decode_like_the_fp64_oracle(quality_mu4):
+    """Two 273-PRB 4-user slots at the sweep point nearest the FP32 10% BLER
+    crossing: the FP64 oracle NRX's LLRs, the FP32 and the BF16 GPU receivers'
+    decode to nearly the same block-error pattern (conv. code, ~660 blocks)."""
+    import dataclasses
+    import numpy as np
+    from oracle import nrx_oracle as O
+    from paper_2409_02912_b300 import bler, nrx
+    blob, q = quality_mu4
+    sw = evaluate.MU4_SWEEP
+    s10 = q["nrx_fp32"]["snr_at_10pct"]
+    snr = min(sw.snrs, key=lambda s: abs(s - s10))
+    batch = evaluate.sweep_batches(dataclasses.replace(sw, snrs=(snr,), slots_per_point=2))[0]
+    net, W = synth.unpack_weights(blob)
+    W = {k: v.astype(np.float64) for k, v in W.items()}
+    ref = np.concatenate([O.nrx_forward(s.y, s.dmrs, 4, s.cfg.dmrs_symbols, s.cfg.bits_per_symbol, W, net.iterations,
+                                        net.res_blocks) for s in batch.slots]).astype(np.float32)
+    y = torch.from_numpy(synth.stack_batch(batch.slots)).cuda()
+    dm = torch.from_numpy(np.stack([s.dmrs for s in batch.slots])).cuda()
+    offs = torch.from_numpy(batch.offsets).cuda()
+    perm = torch.from_numpy(batch.perm).cuda()
+    err_ref = (bler.conv_decode(torch.from_numpy(ref).cuda(), offs, batch.n_info, perm).cpu().numpy()
+               != batch.info).any(axis=1)
+    assert err_ref.size > 500 and 0 < err_ref.sum() < err_ref.size
+    for p in ("fp32", "bf16"):
+        rx = nrx.Receiver(blob, 4, 4, 273, max_slots=2, precision=p)
+        gpu = rx.nrx_detect_batch(y, dm, sw.dmrs_symbols, batch.bits)
+        err = (bler.conv_decode(gpu, offs, batch.n_info, perm).cpu().numpy() != batch.info).any(axis=1)
+        rx.close()
+        assert np.sum(err != err_ref) <= max(2, err_ref.size // 200), (p, err.sum(), err_ref.sum())
