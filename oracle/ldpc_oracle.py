@@ -99,15 +99,22 @@ def sum_product(llr: np.ndarray, V: np.ndarray, Z: int, iterations: int = 30, st
 
 
 def layered_min_sum(llr: np.ndarray, V: np.ndarray, Z: int, iterations: int = 20, alpha: float = 0.75,
-                    stop_early: bool = False):
+                    stop_early: bool = False, dtype=np.float64):
     """Row-layered normalised min-sum: base rows in order; for row r and each
     of its Z checks, with t_e = post[v_e] - c2v_e over the row's edges e (in
     column order), the new message is alpha * (product of the other signs) *
     (the smallest other |t|), and post[v_e] = t_e + new message.  With
     stop_early, stops after an iteration whose hard decisions satisfy every
-    check.  Returns (hard bits uint8 [nb Z], posterior L [nb Z], iterations run)."""
+    check.  Returns (hard bits uint8 [nb Z], posterior L [nb Z], iterations run).
+
+    ``dtype`` is the arithmetic of the messages and posteriors.  The hard
+    decisions are integers decided by floating point, so a comparison with a
+    decoder that runs in FP32 takes them in FP32 (``np.float32``): each
+    message is then alpha * sign rounded once by the multiplication with the
+    magnitude, and each posterior once by the addition."""
     V = np.asarray(V)
-    L = -np.asarray(llr, dtype=np.float64)
+    L = -np.asarray(llr, dtype=np.float64).astype(dtype)
+    alpha = dtype(alpha)
     post = L.copy()
     mb = V.shape[0]
     i = np.arange(Z)
@@ -115,14 +122,14 @@ def layered_min_sum(llr: np.ndarray, V: np.ndarray, Z: int, iterations: int = 20
     for r in range(mb):
         cols = np.nonzero(V[r] >= 0)[0]
         row_vars.append(np.stack([c * Z + (i + V[r, c] % Z) % Z for c in cols]))  # [d, Z]
-    c2v = [np.zeros(rv.shape) for rv in row_vars]
+    c2v = [np.zeros(rv.shape, dtype=dtype) for rv in row_vars]
     it = 0
     for it in range(1, iterations + 1):
         for r in range(mb):
             vs = row_vars[r]
             t = post[vs] - c2v[r]
             a = np.abs(t)
-            sgn = np.where(t < 0, -1.0, 1.0)
+            sgn = np.where(t < 0, -1.0, 1.0).astype(dtype)
             tot = np.prod(sgn, axis=0)
             amin = np.argmin(a, axis=0)  # first minimum in edge order
             srt = np.sort(a, axis=0)

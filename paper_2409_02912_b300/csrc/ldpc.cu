@@ -94,9 +94,10 @@ __global__ void __launch_bounds__(kMaxZ) k_ldpc(LdpcGraph G, int Z, int kb, int 
         for (int q = 0; q < kMaxDeg; ++q) {
           if (q < d && !((skip >> q) & 1u)) {
             const float s = ((neg >> q) & 1u) ? -total : total;  // product of the other signs
-            const float nw = alpha * s * (q == amin ? m2 : m1);
+            // one rounding for the message and one for the posterior (never a fused multiply-add)
+            const float nw = __fmul_rn(alpha * s, q == amin ? m2 : m1);
             msg[(size_t)(e0 + q) * Z + i] = nw;
-            post[v[q]] = t[q] + nw;
+            post[v[q]] = __fadd_rn(t[q], nw);
           }
         }
       }

@@ -60,7 +60,8 @@ CHILD = textwrap.dedent('''
     got = bler.ldpc_decode(torch.from_numpy(llr.reshape(-1)).cuda(), torch.tensor([0, E]).cuda(), E, qm, Z, bg,
                            iterations=3, stop_early=False).cpu().numpy()
     for k in range(2):
-        hard, _, _ = LO.layered_min_sum(LO.rate_recover(llr[k].astype(np.float64), Z, bg.nb, qm), bg.V, Z, 3)
+        hard, _, _ = LO.layered_min_sum(LO.rate_recover(llr[k].astype(np.float64), Z, bg.nb, qm), bg.V, Z, 3,
+                                        dtype=np.float32)
         assert np.array_equal(got[k], hard[:bg.kb * Z])
     torch.cuda.synchronize()
     print("WORST", worst)

@@ -1,6 +1,7 @@
-"""The GPU LDPC decoder (nrx_ldpc_decode, through the C ABI) against the FP64
+"""The GPU LDPC decoder (nrx_ldpc_decode, through the C ABI) against the
 oracle decoders on the same received LLRs: the same layered normalised
-min-sum gives the same hard decisions after 1, 3 and 10 passes, and on
+min-sum, run in FP32 like the decoder, gives the same hard decisions after
+1, 3 and 10 passes, and on
 encoded QAM blocks over AWGN the GPU decodes every block the oracle's
 sum-product decodes, with the same rate recovery."""
 import numpy as np
@@ -35,8 +36,10 @@ def test_layered_min_sum_matches_oracle(iterations, Z, qm, E_factor):
     got = bler.ldpc_decode(_device(llr.reshape(-1), np.float32), _device(np.arange(n_blocks) * E, np.int64), E, qm,
                            Z, bg, iterations=iterations, alpha=0.75, stop_early=False).cpu().numpy()
     for b in range(n_blocks):
+        # decisions in the decoder's precision (FP32); no position is repeated at these E, so the
+        # recovered LLRs are the received ones exactly
         hard, _, _ = LO.layered_min_sum(LO.rate_recover(llr[b].astype(np.float64), Z, bg.nb, qm), bg.V, Z,
-                                        iterations=iterations, alpha=0.75)
+                                        iterations=iterations, alpha=0.75, dtype=np.float32)
         assert np.array_equal(got[b], hard[:bg.kb * Z]), (b, int(np.sum(got[b] != hard[:bg.kb * Z])))
 
 

@@ -107,6 +107,36 @@ def test_min_sum_single_check_closed_form():
         assert abs(post[k] - want) < 1e-12
 
 
+def test_min_sum_single_check_closed_form_fp32():
+    """The same check in FP32: each message is alpha * sign times the smallest
+    other magnitude, rounded once; each posterior is rounded once more."""
+    V = np.array([[0, 0, 0, 0, 0]])
+    llr = np.array([0.7, -2.0, 0.3, 1.5, -0.9], dtype=np.float32)
+    _, post, _ = LO.layered_min_sum(llr, V, 1, iterations=1, alpha=0.75, dtype=np.float32)
+    assert post.dtype == np.float32
+    L = -llr
+    for k in range(5):
+        others = np.delete(L, k)
+        msg = np.float32(0.75 * np.prod(np.sign(others))) * np.float32(np.min(np.abs(others)))
+        assert post[k] == np.float32(L[k] + msg)
+
+
+def test_min_sum_fp32_and_fp64_decode_the_same_block():
+    """On a block that decodes, the FP32 and FP64 min-sum return the sent word."""
+    bg = synth.ldpc_base_graph()
+    Z = 32
+    rng = _rng(5)
+    info = rng.integers(0, 2, size=bg.kb * Z, dtype=np.uint8)
+    cw = synth.ldpc_encode(bg, Z, info[None])[0]
+    E = 2 * bg.kb * Z
+    e = synth.ldpc_rate_match(bg, Z, cw[None], E, 1)[0]
+    llr = -4.0 * (1.0 - 2.0 * e) + 1.5 * rng.standard_normal(E)  # ln P(1)/P(0)
+    rec = LO.rate_recover(llr, Z, bg.nb, 1)
+    for dt in (np.float64, np.float32):
+        hard, _, _ = LO.layered_min_sum(rec, bg.V, Z, iterations=20, stop_early=True, dtype=dt)
+        assert np.array_equal(hard, cw), dt
+
+
 @pytest.mark.parametrize("E_mult", [0.4, 1.0, 1.7])
 def test_rate_recover_inverts_rate_matching(E_mult):
     bg = synth.ldpc_base_graph()
