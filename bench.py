@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--precision", choices=["auto", "fp32", "bf16", "fp16", "fp8"], default="auto")
     ap.add_argument("--no-extras", action="store_true", help="skip latency/compare/e2e/cpu legs")
     ap.add_argument("--batch", type=int, default=0, help="slots per step (0 = the workload's batch of 8)")
+    ap.add_argument("--oracle-child", type=int, default=0, help=argparse.SUPPRESS)  # internal: see below
     return ap.parse_args()
 
 
@@ -146,6 +147,44 @@ def oracle_slot_seconds(slots, W64, net):
     return time.perf_counter() - t0
 
 
+def bench_weights():
+    """(FP32 weights, name): the trained network of the workload when its blob
+    is present, else the seeded Gaussian initialisation."""
+    from paper_2409_02912_b300 import evaluate
+    net = synth.WORKLOADS[WORKLOAD].net
+    if os.path.exists(evaluate.TRAINED_MU4):
+        with open(evaluate.TRAINED_MU4, "rb") as f:
+            return synth.unpack_weights(f.read())[1], os.path.basename(evaluate.TRAINED_MU4)
+    return synth.make_weights(net), "seeded Gaussian init (PCG64(42))"
+
+
+def oracle_child(n_slots: int):
+    """Internal (--oracle-child N): time the oracle on the first N slots of
+    the workload in this process and print the seconds (the parent starts it
+    with one-thread BLAS / OpenMP pools)."""
+    w = synth.WORKLOADS[WORKLOAD]
+    W64 = {k: v.astype(np.float64) for k, v in bench_weights()[0].items()}
+    slots = synth.workload_slots(w, n_slots)
+    print(oracle_slot_seconds(slots, W64, w.net), flush=True)
+
+
+def oracle_single_thread_rate(n_slots: int):
+    """REs/s of the oracle on the first n_slots slots in a child process whose
+    BLAS and OpenMP pools are limited to one thread; None if it fails."""
+    import subprocess
+    import sys
+    one = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+                            "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS")}
+    env = dict(os.environ, **one, CUDA_VISIBLE_DEVICES="")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", str(n_slots)], env=env,
+                           capture_output=True, text=True, timeout=900, cwd=ROOT)
+        secs = float(r.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+    return n_slots * res_per_slot(synth.WORKLOADS[WORKLOAD]) / secs
+
+
 def blas_threads() -> int:
     try:
         from threadpoolctl import threadpool_info
@@ -156,18 +195,14 @@ def blas_threads() -> int:
 
 
 def oracle_cpu_baseline(slots, W64, net, sample: str) -> dict:
-    """The FP64 oracle timed on the host cores twice over the same slots: with
-    its BLAS pool limited to one thread and with the default pool (numpy's
-    matmuls are the only multi-threaded part).  `value` is the all-core rate;
-    `cores` the BLAS threads that run used; `nproc` the host's CPU count."""
+    """The FP64 oracle timed on the host cores twice over the same slots: in
+    a child process with one-thread BLAS / OpenMP pools, and here with the
+    default pools (numpy's matmuls are the only multi-threaded part).
+    `value` is the all-core rate; `cores` the BLAS threads that run used;
+    `nproc` the host's CPU count."""
     w = synth.WORKLOADS[WORKLOAD]
     n_res = len(slots) * res_per_slot(w)
-    try:
-        from threadpoolctl import threadpool_limits
-        with threadpool_limits(limits=1, user_api="blas"):
-            single = n_res / oracle_slot_seconds(slots, W64, net)
-    except ImportError:
-        single = None
+    single = oracle_single_thread_rate(len(slots))
     allc = n_res / oracle_slot_seconds(slots, W64, net)
     return {"value": allc, "unit": UNIT, "cores": blas_threads(), "nproc": os.cpu_count(), "kind": "oracle",
             "single_thread_value": single, "all_core_value": allc, "sample": sample}
@@ -205,7 +240,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     w = synth.WORKLOADS[WORKLOAD]
-    W64 = {k: v.astype(np.float64) for k, v in synth.make_weights(w.net).items()}
+    W64 = {k: v.astype(np.float64) for k, v in bench_weights()[0].items()}
     slots = synth.workload_slots(w, w.batch)
     for i in range(args.warmup):
         oracle_slot_seconds([slots[i % len(slots)]], W64, w.net)
@@ -213,12 +248,7 @@ def run_reference(args, rank, world):
     total = sum(secs)
     value = args.steps * res_per_slot(w) / total
     cores = blas_threads()
-    try:  # the same oracle with one BLAS thread, on one slot
-        from threadpoolctl import threadpool_limits
-        with threadpool_limits(limits=1, user_api="blas"):
-            single = res_per_slot(w) / oracle_slot_seconds([slots[0]], W64, w.net)
-    except ImportError:
-        single = None
+    single = oracle_single_thread_rate(1)  # the same oracle with one-thread pools, on one slot
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
@@ -229,7 +259,7 @@ def run_reference(args, rank, world):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "nproc": os.cpu_count(), "kind": "oracle",
                          "single_thread_value": single, "all_core_value": value,
                          "sample": f"{args.steps} slots of {WORKLOAD}, one per step, FP64 numpy oracle "
-                                   "(single-thread figure: one more slot with one BLAS thread)"},
+                                   "(single-thread figure: one more slot in a process with one-thread BLAS / OpenMP pools)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -274,15 +304,8 @@ def run_ours(args, rank, world, local):
     w = synth.WORKLOADS[WORKLOAD]
     net = w.net
     from paper_2409_02912_b300 import evaluate
-    if os.path.exists(evaluate.TRAINED_MU4):  # the trained network of this workload, else seeded weights
-        with open(evaluate.TRAINED_MU4, "rb") as f:
-            blob = f.read()
-        weights_name = os.path.basename(evaluate.TRAINED_MU4)
-        W_bench = synth.unpack_weights(blob)[1]
-    else:
-        W_bench = synth.make_weights(net)
-        blob = synth.pack_weights(net, W_bench)
-        weights_name = "seeded Gaussian init (PCG64(42))"
+    W_bench, weights_name = bench_weights()  # the trained network of this workload, else seeded weights
+    blob = synth.pack_weights(net, W_bench)
     batch = args.batch or w.batch
     slots = synth.workload_slots(w, batch, start=rank_slot_start(rank, batch))
     n = len(slots)
@@ -536,6 +559,9 @@ def run_ours(args, rank, world, local):
 
 def main():
     args = parse()
+    if args.oracle_child:
+        oracle_child(args.oracle_child)
+        return
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
