@@ -9,23 +9,28 @@
 // the 16 input columns c (subcarrier s0 - 2 + c, a halo of two on each side),
 // in the 128-byte-swizzle K-major layout of the MMA; the MMAs cover it as two
 // M = 128 tiles starting at rows 0 and 96.  Per tile:
-//   1. TMA: input box [14][16][64] -> IN (zero outside the grid).
-//   2. MMA: D2 = IN x I + 1 b2^T (identity weights: the residual lands in the
-//      PW2 accumulator exactly, since I is exact in 16 bits).
-//   3. DW1 (columns 1..14) from IN -> A.  MMA: D1 = 1 b1^T + A W1^T.
+//   1. TMA: input box [14][16][64] -> IN (zero outside the grid), loaded
+//      during the previous tile (three buffers rotate through the roles IN,
+//      A and free; the last block of an iteration, whose third buffer holds
+//      the state tile ST, keeps fixed roles).
+//   2. DW1 (columns 1..14) from IN -> A, while the leader issues
+//      D2 = IN x I + 1 b2^T (identity weights: the residual lands in the PW2
+//      accumulator exactly, since I is exact in 16 bits) and D1 = 1 b1^T.
+//   3. MMA: D1 += A W1^T.
 //   4. Epilogue 1: P1 = ReLU(D1), zero outside the grid, over IN.
 //   5. DW2 + ReLU (columns 2..13) from P1 -> A.  MMA: D2 += A W2^T
 //      (+ ST x I: the state tile, last block).
-//   6. Epilogue 2: D2 -> OUT (rows t * 12 + c - 2) -> TMA store.
+//   6. Epilogue 2: D2 -> OUT (in A; rows t * 12 + c - 2) -> TMA store.
 // The biases enter the accumulators through one K = 16 MMA of an all-ones
 // tile with a tile holding [b_hi, b_lo], b_hi the 16-bit rounding of b and
 // b_lo that of the remainder.
-// A CTA of 16 warps holds one copy of the weights and runs two independent
-// 8-warp tile pipelines (own buffers, barriers and 256 TMEM columns each), so
-// one group's depthwise work overlaps the other's copies, MMAs and waits.
+// A CTA of 16 warps holds one copy of the weights and runs two 8-warp tile
+// pipelines (own buffers, barriers and 256 TMEM columns each) whose
+// depthwise phases take turns: while one group runs its taps on the CUDA
+// cores, the other waits for its MMAs and runs its epilogues and copies.
 // All waits are bounded (the waiting thread sleeps in hardware); on a timeout
-// the context's error word is set and the CTA drains its asynchronous work
-// and exits.
+// the context's error word is set and the group stops working but keeps
+// taking its turns, and the CTA drains its asynchronous work and exits.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -172,36 +177,32 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, uint64_
 // of one channel pair (2 cp, 2 cp + 1).  in_addr[k] (k < 4) addresses this
 // lane's word of input column k on symbol 0 (one symbol = 16 rows = 2048
 // bytes further); out_addr[o] likewise for output column o.  Zero padding in
-// time; kRelu applies max(., 0).  BF16: scalar FP32 FMAs; FP16: packed FP16
-// FMAs.  The words of symbol ti + 2 are requested before symbol ti is
-// computed.  Symbols 0..11 run as a loop over blocks of three (the period of
-// the register window), 12 and 13 after it: a small loop body keeps the
-// kernel's code within the instruction caches.
+// time; kRelu applies max(., 0).  BF16: FP32 FMAs; FP16: packed FP16 FMAs.  The words of symbol ti + 2 are requested before
+// symbol ti is computed.  Symbols 0..11 run as a loop over blocks of three
+// (the period of the register window), 12 and 13 after it: a small loop body
+// keeps the kernel's code within the instruction caches.
 template <typename T, bool kRelu>
 __device__ __forceinline__ void dw_pair(const float* __restrict__ taps, int cp, const uint32_t (&in_addr)[4],
                                         const uint32_t (&out_addr)[2]) {
   constexpr bool kBf16 = std::is_same<T, __nv_bfloat16>::value;
-  constexpr int NA = kBf16 ? 4 : 2;  // accumulators per tap row (two columns x two channels, or two packed)
-  using Acc = typename std::conditional<kBf16, float, __half2>::type;
-  Acc kk[kBf16 ? 18 : 9];  // taps: BF16 [i] channel 2cp, [9 + i] channel 2cp + 1; FP16 packed pairs
+  using Acc = typename std::conditional<kBf16, float2, __half2>::type;  // (channel 2 cp, channel 2 cp + 1)
+  Acc kk[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const float a = taps[(2 * cp) * 9 + i], b = taps[(2 * cp + 1) * 9 + i];
-    if constexpr (kBf16) {
-      kk[i] = a;
-      kk[9 + i] = b;
-    } else {
+    if constexpr (kBf16)
+      kk[i] = make_float2(a, b);
+    else
       kk[i] = __floats2half2_rn(a, b);
-    }
   }
   Acc zero;
   if constexpr (kBf16)
-    zero = 0.f;
+    zero = make_float2(0.f, 0.f);
   else
     zero = __float2half2_rn(0.f);
-  Acc am[NA], a0[NA], ap[NA];
+  Acc am[2], a0[2], ap[2];  // per output column: outputs of symbols ti - 1, ti, ti + 1
 #pragma unroll
-  for (int j = 0; j < NA; ++j) am[j] = a0[j] = ap[j] = zero;
+  for (int j = 0; j < 2; ++j) am[j] = a0[j] = ap[j] = zero;
   uint32_t w0[4], w1[4], w2[4];  // words of symbols ti, ti + 1, ti + 2
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -211,7 +212,7 @@ __device__ __forceinline__ void dw_pair(const float* __restrict__ taps, int cp, 
   auto put = [&](int t, int o) {
     uint32_t word;
     if constexpr (kBf16) {
-      word = kRelu ? tc::pack_relu_bf16x2(am[2 * o], am[2 * o + 1]) : tc::pack_bf16x2(am[2 * o], am[2 * o + 1]);
+      word = kRelu ? tc::pack_relu_bf16x2(am[o].x, am[o].y) : tc::pack_bf16x2(am[o].x, am[o].y);
     } else {
       __half2 v = am[o];
       if (kRelu) v = __hmax2(v, zero);
@@ -223,43 +224,34 @@ __device__ __forceinline__ void dw_pair(const float* __restrict__ taps, int cp, 
     if (prefetch)
 #pragma unroll
       for (int k = 0; k < 4; ++k) w2[k] = lds32(in_addr[k] + (ti + 2) * 2048);
-    if constexpr (kBf16) {
-      float xl[4], xh[4];
+    Acc x[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        xl[k] = __uint_as_float(w0[k] << 16);
-        xh[k] = __uint_as_float(w0[k] & 0xFFFF0000u);
-      }
+    for (int k = 0; k < 4; ++k) {
+      if constexpr (kBf16)
+        x[k] = make_float2(__uint_as_float(w0[k] << 16), __uint_as_float(w0[k] & 0xFFFF0000u));
+      else
+        x[k] = *reinterpret_cast<const __half2*>(&w0[k]);
+    }
 #pragma unroll
-      for (int o = 0; o < 2; ++o)
+    for (int o = 0; o < 2; ++o)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          am[2 * o] = fmaf(kk[6 + k], xl[o + k], am[2 * o]);
-          am[2 * o + 1] = fmaf(kk[15 + k], xh[o + k], am[2 * o + 1]);
-          a0[2 * o] = fmaf(kk[3 + k], xl[o + k], a0[2 * o]);
-          a0[2 * o + 1] = fmaf(kk[12 + k], xh[o + k], a0[2 * o + 1]);
-          ap[2 * o] = fmaf(kk[k], xl[o + k], ap[2 * o]);
-          ap[2 * o + 1] = fmaf(kk[9 + k], xh[o + k], ap[2 * o + 1]);
-        }
-    } else {
-      __half2 x[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) x[k] = *reinterpret_cast<const __half2*>(&w0[k]);
-#pragma unroll
-      for (int o = 0; o < 2; ++o)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < 3; ++k) {
+        if constexpr (kBf16) {  // scalar FMAs: measured faster here than the packed f32x2 form
+          am[o] = make_float2(fmaf(kk[6 + k].x, x[o + k].x, am[o].x), fmaf(kk[6 + k].y, x[o + k].y, am[o].y));
+          a0[o] = make_float2(fmaf(kk[3 + k].x, x[o + k].x, a0[o].x), fmaf(kk[3 + k].y, x[o + k].y, a0[o].y));
+          ap[o] = make_float2(fmaf(kk[k].x, x[o + k].x, ap[o].x), fmaf(kk[k].y, x[o + k].y, ap[o].y));
+        } else {
           am[o] = __hfma2(kk[6 + k], x[o + k], am[o]);
           a0[o] = __hfma2(kk[3 + k], x[o + k], a0[o]);
           ap[o] = __hfma2(kk[k], x[o + k], ap[o]);
         }
-    }
+      }
     if (ti >= 1) {
       put(ti - 1, 0);
       put(ti - 1, 1);
     }
 #pragma unroll
-    for (int j = 0; j < NA; ++j) {
+    for (int j = 0; j < 2; ++j) {
       am[j] = a0[j];
       a0[j] = ap[j];
       ap[j] = zero;
@@ -383,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::BAR + 64);
   if (tid == 0) {
-    for (int i = 0; i < 6; ++i) tc::mbar_init(reinterpret_cast<uint64_t*>(sm + L::BAR + (i / 3) * 32 + (i % 3) * 8), 1);
+    for (int i = 0; i < 8; ++i) tc::mbar_init(reinterpret_cast<uint64_t*>(sm + L::BAR + i * 8), 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tslot, 512);
@@ -396,14 +388,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   // ---- this group's pipeline ----
   const int grp = warp >> 3, gw = warp & 7, gtid = tid & (kGroupThreads - 1);
   const uint32_t bar_id = 1 + grp;
-  const bool leader = gtid == 0;
-  uint64_t* in_bar = reinterpret_cast<uint64_t*>(sm + L::BAR + grp * 32);
-  uint64_t* st_bar = in_bar + 1;
-  uint64_t* mma_bar = in_bar + 2;
-  unsigned char* g_in = sm + L::GRP + grp * L::GSTRIDE;  // IN, later P1
-  unsigned char* g_a = g_in + kBuf;                        // A1, later A2
-  unsigned char* g_so = g_a + kBuf;                        // ST (last block), later OUT
-  const uint32_t in_s = tc::smem_u32(g_in), a_s = tc::smem_u32(g_a), so_s = tc::smem_u32(g_so);
+  // the group's leader (TMA, MMA issue, waits) is lane 0 of warp 7, which has no depthwise
+  // columns in DW1: it issues the residual and bias MMAs while the other warps run DW1
+  const bool leader = gtid == 7 * 32;
+  uint64_t* in_bar = reinterpret_cast<uint64_t*>(sm + L::BAR + grp * 32);  // [i]: copy into buffer i
+  uint64_t* mma_bar = in_bar + 3;
+  unsigned char* g_buf0 = sm + L::GRP + grp * L::GSTRIDE;  // three operand buffers of kBuf bytes
+  const uint32_t buf0_s = tc::smem_u32(g_buf0), st_s = buf0_s + 2 * kBuf;
   const uint32_t w1_s = tc::smem_u32(sm + L::W1), w2_s = tc::smem_u32(sm + L::W2), id_s = tc::smem_u32(sm + L::ID),
                  ones_s = tc::smem_u32(sm + L::ONES), bi1_s = tc::smem_u32(sm + L::BI1),
                  bi2_s = tc::smem_u32(sm + L::BI2);
@@ -417,60 +408,99 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int e_r = e_mt ? kM1Row + e_row : e_row;
   const int e_c = e_r & 15, e_t = e_r >> 4;
   const uint32_t e_lane = (uint32_t)((gw & 3) * 32) << 16;
+  // Buffer roles.  The last block of an iteration: IN = 0, A = 1, ST = 2; the
+  // next tile's input is loaded into buffer 0 once DW2 is done with P1, and
+  // DW1 waits until the previous tile's store has read OUT (in A).  The other
+  // blocks rotate the three buffers: tile j has IN = j % 3 and A = (j + 2) % 3,
+  // which was the IN of tile j - 1 (P1 no longer read), so DW1 never waits for
+  // a store; tile j + 1's input is loaded during tile j's PW1 into buffer
+  // (j + 1) % 3, the A of tile j - 1, once that tile's store has read it.
+  const bool rot = !last;
 
-  uint32_t in_ph = 0, st_ph = 0, mma_ph = 0;
-  bool in_pending = false, st_pending = false, mma_pending = false;
+  uint32_t in_ph = 0, in_pending = 0;  // bit i: parity / copy in flight of buffer i
+  uint32_t st_ph = 0, mma_ph = 0;
+  bool st_pending = false, mma_pending = false;
   const int vt0 = blockIdx.x * 2 + grp, vstride = gridDim.x * 2;
+  // both groups run the same number of iterations, so that the turns below pair up
+  const int n_grp0 = blockIdx.x * 2 < n_tiles ? (n_tiles - blockIdx.x * 2 + vstride - 1) / vstride : 0;
+  const int n_grp1 = blockIdx.x * 2 + 1 < n_tiles ? (n_tiles - blockIdx.x * 2 - 1 + vstride - 1) / vstride : 0;
+  const int n_iter = n_grp0 > n_grp1 ? n_grp0 : n_grp1;
   tc::pdl_wait();  // from here on the previous kernel's output is read
   if (leader && vt0 < n_tiles) {
     NRX_IN(vt0 / tps, n_tiles / tps, 404);
     tc::mbar_arrive_expect_tx(in_bar, kInBytes);
-    tc::tma_load_3d(g_in, &in_map, 0, (vt0 % tps) * kTW - 2, (vt0 / tps) * NRX_SYMBOLS, in_bar);
-    in_pending = true;
+    tc::tma_load_3d(g_buf0, &in_map, 0, (vt0 % tps) * kTW - 2, (vt0 / tps) * NRX_SYMBOLS, in_bar);
+    in_pending = 1u;
   }
-  for (int tile = vt0; tile < n_tiles; tile += vstride) {
+  // The depthwise phases of the two groups take turns (group 0 first): while
+  // one group runs its depthwise taps on the CUDA cores, the other waits for
+  // its MMAs, runs its epilogues and copies.  Named barrier 3 + g is group g's
+  // turn: the group syncs on it before a depthwise phase, and the other group
+  // arrives on it after each of its own (group 1 skips its very last arrival,
+  // which no phase of group 0 would consume).
+  const uint32_t my_turn = 3 + grp, other_turn = 4 - grp;
+  auto take_turn = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(my_turn), "n"(kThreads) : "memory"); };
+  auto pass_turn = [&](bool final_phase) {
+    if (!(grp == 1 && final_phase)) asm volatile("bar.arrive %0, %1;" ::"r"(other_turn), "n"(kThreads) : "memory");
+  };
+  if (grp == 1 && n_iter > 0) pass_turn(false);
+  bool dead = false;  // a wait gave up: the group only keeps taking and passing its turns
+  int b = 0;           // IN buffer of this tile
+  for (int it = 0; it < n_iter; ++it) {
+    const int tile = vt0 + it * vstride;
+    const bool final_it = it + 1 == n_iter;
+    bool work = !dead && tile < n_tiles;
+    const int ba = rot ? (b == 0 ? 2 : b - 1) : 1;  // A buffer
+    const int bn = rot ? (b == 2 ? 0 : b + 1) : 0;  // next tile's IN buffer
+    const uint32_t in_s = buf0_s + b * kBuf, a_s = buf0_s + ba * kBuf;
     const int su = tile / tps, s0 = (tile % tps) * kTW;
-    // 1-2: input tile; residual and b2 into D2, b1 into D1
-    {
+    // 1: input tile; OUT (in A) read by the previous store
+    if (work) {
       bool ok = true;
       if (leader) {
-        ok = wait_bar(in_bar, in_ph);
+        ok = wait_bar(in_bar + b, (in_ph >> b) & 1u);
         if (ok) {
-          in_pending = false;
-          tc::tc_fence_after();
-          tc::mma_k64(d2, in_s, id_s, idesc16<T>(), false);
-          tc::mma_k64(d2 + 64, in_s + kM1Row * 128, id_s, idesc16<T>(), false);
-          mma_bias<T>(d2, ones_s, bi2_s, true);
-          mma_bias<T>(d2 + 64, ones_s, bi2_s, true);
-          mma_bias<T>(d1, ones_s, bi1_s, false);
-          mma_bias<T>(d1 + 64, ones_s, bi1_s, false);
+          in_pending &= ~(1u << b);
+          if (!rot) tc::bulk_wait_read_all();  // OUT (in A) read by the previous store
         }
       }
-      in_ph ^= 1u;
+      in_ph ^= 1u << b;
       if (group_any(bar_id, !ok)) {
         if (leader) atomicExch(err, 1);
-        break;
+        dead = true;
+        work = false;
       }
     }
-    // 3: DW1, output columns 1..14 (warp gw: columns 2 gw + 1, 2 gw + 2)
-    if (gw < 7) {
+    // 2-3: DW1, output columns 1..14 (warp gw: columns 2 gw + 1, 2 gw + 2); meanwhile the
+    // leader issues D2 = IN x I + 1 b2^T (the residual, exact: I is exact in 16 bits) and
+    // D1 = 1 b1^T, which the PW1 commit below covers
+    take_turn();
+    if (work && gw < 7) {
       uint32_t ia[4], oa[2];
 #pragma unroll
       for (int k = 0; k < 4; ++k) ia[k] = col_word(in_s, 2 * gw + k, cp);
 #pragma unroll
       for (int o = 0; o < 2; ++o) oa[o] = col_word(a_s, 2 * gw + 1 + o, cp);
       dw_pair<T, false>(sk1, cp, ia, oa);
+    } else if (work && leader) {
+      tc::tc_fence_after();
+      tc::mma_k64(d2, in_s, id_s, idesc16<T>(), false);
+      tc::mma_k64(d2 + 64, in_s + kM1Row * 128, id_s, idesc16<T>(), false);
+      mma_bias<T>(d2, ones_s, bi2_s, true);
+      mma_bias<T>(d2 + 64, ones_s, bi2_s, true);
+      mma_bias<T>(d1, ones_s, bi1_s, false);
+      mma_bias<T>(d1 + 64, ones_s, bi1_s, false);
     }
-    tc::fence_async_smem();
-    if (leader && last) {  // state tile for the last block; OUT (same buffer) was read by the previous store
-      tc::bulk_wait_read_all();
-      tc::mbar_arrive_expect_tx(st_bar, kInBytes);
-      NRX_IN(s0 + kTW - 1, S, 405);
-      tc::tma_load_3d(g_so, &st_map, 0, s0 - 2, su * NRX_SYMBOLS, st_bar);
-      st_pending = true;
-    }
-    group_sync(bar_id);
-    {
+    pass_turn(false);
+    if (work) {
+      tc::fence_async_smem();
+      if (leader && last) {  // state tile for the last block (buffer 2: its previous tile's MMAs are done)
+        tc::mbar_arrive_expect_tx(in_bar + 2, kInBytes);
+        NRX_IN(s0 + kTW - 1, S, 405);
+        tc::tma_load_3d(g_buf0 + 2 * kBuf, &st_map, 0, s0 - 2, su * NRX_SYMBOLS, in_bar + 2);
+        st_pending = true;
+      }
+      group_sync(bar_id);
       bool ok = true;
       if (leader) {
         tc::tc_fence_after();
@@ -478,29 +508,42 @@ __global__ void __launch_bounds__(kThreads, 1)
         mma_w<T>(d1 + 64, a_s + kM1Row * 128, w1_s, true);
         tc::mma_commit(mma_bar);
         mma_pending = true;
+        const int nt = tile + vstride;
+        if (rot && nt < n_tiles) {  // next tile's input into the previous tile's A, once its store has read it
+          tc::bulk_wait_read_all();
+          NRX_IN(nt / tps, n_tiles / tps, 406);
+          tc::mbar_arrive_expect_tx(in_bar + bn, kInBytes);
+          tc::tma_load_3d(g_buf0 + bn * kBuf, &in_map, 0, (nt % tps) * kTW - 2, (nt / tps) * NRX_SYMBOLS,
+                          in_bar + bn);
+          in_pending |= 1u << bn;
+        }
         ok = wait_bar(mma_bar, mma_ph);
         if (ok) mma_pending = false;
       }
       mma_ph ^= 1u;
       if (group_any(bar_id, !ok)) {
         if (leader) atomicExch(err, 1);
-        break;
+        dead = true;
+        work = false;
       }
     }
-    tc::tc_fence_after();
-    // 4: epilogue 1 -> P1 (over IN: the residual MMA and DW1 are done with it)
-    if (gw != 4) {
-      float v[64];
-      tc::tmem_row64(d1 + e_mt * 64 + e_lane, v);
-      if (e_c >= 1 && e_c <= 14) {
-        const int s = s0 - 2 + e_c;
-        store_row<T, true>(in_s + e_r * 128, e_r, v, s < 0 || s >= S);
+    if (work) {
+      tc::tc_fence_after();
+      // 4: epilogue 1 -> P1 (over IN: the residual MMA and DW1 are done with it)
+      if (gw != 4) {
+        float v[64];
+        tc::tmem_row64(d1 + e_mt * 64 + e_lane, v);
+        if (e_c >= 1 && e_c <= 14) {
+          const int s = s0 - 2 + e_c;
+          store_row<T, true>(in_s + e_r * 128, e_r, v, s < 0 || s >= S);
+        }
       }
+      tc::tc_fence_before();
+      group_sync(bar_id);
     }
-    tc::tc_fence_before();
-    group_sync(bar_id);
     // 5: DW2 + ReLU, output columns 2..13 (warp gw: columns 2 gw + 2, 2 gw + 3)
-    if (gw < 6) {
+    take_turn();
+    if (work && gw < 6) {
       uint32_t ia[4], oa[2];
 #pragma unroll
       for (int k = 0; k < 4; ++k) ia[k] = col_word(in_s, 2 * gw + 1 + k, cp);
@@ -508,14 +551,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int o = 0; o < 2; ++o) oa[o] = col_word(a_s, 2 * gw + 2 + o, cp);
       dw_pair<T, true>(sk2, cp, ia, oa);
     }
-    tc::fence_async_smem();
-    if (leader && !last) tc::bulk_wait_read_all();  // the previous store has read OUT
-    group_sync(bar_id);
-    {
+    pass_turn(final_it);
+    if (work) {
+      tc::fence_async_smem();
+      group_sync(bar_id);
       bool ok = true;
       if (leader) {
         if (last) {
-          ok = wait_bar(st_bar, st_ph);
+          ok = wait_bar(in_bar + 2, st_ph);
           if (ok) st_pending = false;
         }
         if (ok) {
@@ -523,18 +566,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           mma_w<T>(d2, a_s, w2_s, true);
           mma_w<T>(d2 + 64, a_s + kM1Row * 128, w2_s, true);
           if (last) {
-            tc::mma_k64(d2, so_s, id_s, idesc16<T>(), true);
-            tc::mma_k64(d2 + 64, so_s + kM1Row * 128, id_s, idesc16<T>(), true);
+            tc::mma_k64(d2, st_s, id_s, idesc16<T>(), true);
+            tc::mma_k64(d2 + 64, st_s + kM1Row * 128, id_s, idesc16<T>(), true);
           }
           tc::mma_commit(mma_bar);
           mma_pending = true;
-          // the next tile's input: IN / P1 is free (DW2 is past the barrier)
+          // last block: the next tile's input into IN, whose P1 DW2 no longer reads
           const int nt = tile + vstride;
-          if (nt < n_tiles) {
+          if (!rot && nt < n_tiles) {
             NRX_IN(nt / tps, n_tiles / tps, 406);
             tc::mbar_arrive_expect_tx(in_bar, kInBytes);
-            tc::tma_load_3d(g_in, &in_map, 0, (nt % tps) * kTW - 2, (nt / tps) * NRX_SYMBOLS, in_bar);
-            in_pending = true;
+            tc::tma_load_3d(g_buf0, &in_map, 0, (nt % tps) * kTW - 2, (nt / tps) * NRX_SYMBOLS, in_bar);
+            in_pending |= 1u;
           }
           ok = wait_bar(mma_bar, mma_ph);
           if (ok) mma_pending = false;
@@ -544,31 +587,37 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_ph ^= 1u;
       if (group_any(bar_id, !ok)) {
         if (leader) atomicExch(err, 1);
-        break;
+        dead = true;
+        work = false;
       }
     }
-    tc::tc_fence_after();
-    // 6: epilogue 2 -> OUT rows t * 12 + c - 2, then one bulk tensor store
-    if (gw != 4) {
-      float v[64];
-      tc::tmem_row64(d2 + e_mt * 64 + e_lane, v);
-      if (e_c >= 2 && e_c <= 13) {
-        const int ro = e_t * kTW + e_c - 2;
-        store_row<T, false>(so_s + ro * 128, ro, v, false);
+    if (work) {
+      tc::tc_fence_after();
+      // 6: epilogue 2 -> OUT (in A, whose A2 rows the PW2 MMAs have read), rows t * 12 + c - 2,
+      // then one bulk tensor store
+      if (gw != 4) {
+        float v[64];
+        tc::tmem_row64(d2 + e_mt * 64 + e_lane, v);
+        if (e_c >= 2 && e_c <= 13) {
+          const int ro = e_t * kTW + e_c - 2;
+          store_row<T, false>(a_s + ro * 128, ro, v, false);
+        }
+      }
+      tc::fence_async_smem();
+      tc::tc_fence_before();
+      group_sync(bar_id);
+      if (leader && NRX_IN(s0 + kTW - 1, S, 407) && NRX_IN(su, n_tiles / tps, 407)) {
+        tc::tma_store_3d(&out_map, 0, s0, su * NRX_SYMBOLS, g_buf0 + ba * kBuf);
+        tc::bulk_commit();
       }
     }
-    tc::fence_async_smem();
-    tc::tc_fence_before();
-    group_sync(bar_id);
-    if (leader && NRX_IN(s0 + kTW - 1, S, 407) && NRX_IN(su, n_tiles / tps, 407)) {
-      tc::tma_store_3d(&out_map, 0, s0, su * NRX_SYMBOLS, g_so);
-      tc::bulk_commit();
-    }
+    b = bn;
   }
   // ---- teardown: let asynchronous work in flight land, then free TMEM ----
   if (leader) {
-    if (in_pending) wait_bar(in_bar, in_ph, kDrainNs);
-    if (st_pending) wait_bar(st_bar, st_ph, kDrainNs);
+    for (int j = 0; j < 3; ++j)
+      if ((in_pending >> j) & 1u) wait_bar(in_bar + j, (in_ph >> j) & 1u, kDrainNs);
+    if (st_pending) wait_bar(in_bar + 2, st_ph, kDrainNs);
     if (mma_pending) wait_bar(mma_bar, mma_ph, kDrainNs);
     tc::bulk_wait_all();
   }
