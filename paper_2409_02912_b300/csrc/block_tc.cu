@@ -15,11 +15,13 @@
 //      the state tile ST, keeps fixed roles).
 //   2. DW1 (columns 1..14) from IN -> A, while the leader issues
 //      D2 = IN x I + 1 b2^T (identity weights: the residual lands in the PW2
-//      accumulator exactly, since I is exact in 16 bits) and D1 = 1 b1^T.
-//   3. MMA: D1 += A W1^T.
+//      accumulator exactly, since I is exact in 16 bits), D1 = 1 b1^T and,
+//      once DW1 has stored symbols 0..7, D1 += A W1^T on the first M tile.
+//   3. MMA: D1 += A W1^T on the second M tile.
 //   4. Epilogue 1: P1 = ReLU(D1), zero outside the grid, over IN.
-//   5. DW2 + ReLU (columns 2..13) from P1 -> A.  MMA: D2 += A W2^T
-//      (+ ST x I: the state tile, last block).
+//   5. DW2 + ReLU (columns 2..13) from P1 -> A.  MMA: D2 += A W2^T (the
+//      first M tile during DW2, as in 2) (+ ST x I: the state tile, last
+//      block).
 //   6. Epilogue 2: D2 -> OUT (in A; rows t * 12 + c - 2) -> TMA store.
 // The biases enter the accumulators through one K = 16 MMA of an all-ones
 // tile with a tile holding [b_hi, b_lo], b_hi the 16-bit rounding of b and
@@ -94,7 +96,7 @@ struct Lay {
   static constexpr int BI2 = BI1 + 2048;
   static constexpr int K1 = BI2 + 2048;       // DW1 taps [64][9] FP32
   static constexpr int K2 = K1 + 64 * 9 * 4;
-  static constexpr int BAR = K2 + 64 * 9 * 4; // per group: in, st, mma mbarriers (32 B); TMEM slot at +64
+  static constexpr int BAR = K2 + 64 * 9 * 4; // per group: six mbarriers (48 B); TMEM slot at +96
   static constexpr int GRP = ((BAR + 128 + 1023) / 1024) * 1024;
   static constexpr int GSTRIDE = 3 * kBuf;    // per group: IN/P1, A, ST/OUT
   static constexpr int TOTAL = GRP + 2 * GSTRIDE;
@@ -173,6 +175,11 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, uint64_
   return false;
 }
 
+// Plain arrive (count 1) on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
 // Sliding 3x3 depthwise over the 14 symbols for two adjacent output columns
 // of one channel pair (2 cp, 2 cp + 1).  in_addr[k] (k < 4) addresses this
 // lane's word of input column k on symbol 0 (one symbol = 16 rows = 2048
@@ -183,7 +190,7 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, uint64_
 // keeps the kernel's code within the instruction caches.
 template <typename T, bool kRelu>
 __device__ __forceinline__ void dw_pair(const float* __restrict__ taps, int cp, const uint32_t (&in_addr)[4],
-                                        const uint32_t (&out_addr)[2]) {
+                                        const uint32_t (&out_addr)[2], uint64_t* half_bar) {
   constexpr bool kBf16 = std::is_same<T, __nv_bfloat16>::value;
   using Acc = typename std::conditional<kBf16, float2, __half2>::type;  // (channel 2 cp, channel 2 cp + 1)
   Acc kk[9];
@@ -267,6 +274,11 @@ __device__ __forceinline__ void dw_pair(const float* __restrict__ taps, int cp, 
     step(tb, true);
     step(tb + 1, true);
     step(tb + 2, true);
+    if (tb == 6) {  // symbols 0..7 stored: the rows of the first M tile are complete
+      tc::fence_async_smem();
+      __syncwarp();
+      if (cp == 0) mbar_arrive(half_bar);
+    }
   }
   step(12, false);
   step(13, false);
@@ -373,9 +385,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     *reinterpret_cast<uint16_t*>(sm + L::ONES + plain_offset(tid, 0)) = Ops<T>::one;
     *reinterpret_cast<uint16_t*>(sm + L::ONES + plain_offset(tid, 1)) = Ops<T>::one;
   }
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::BAR + 64);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::BAR + 96);
   if (tid == 0) {
-    for (int i = 0; i < 8; ++i) tc::mbar_init(reinterpret_cast<uint64_t*>(sm + L::BAR + i * 8), 1);
+    // per group (48 bytes): copies into buffers 0..2, MMA commits, the depthwise half-way arrivals (7 warps)
+    for (int i = 0; i < 12; ++i) tc::mbar_init(reinterpret_cast<uint64_t*>(sm + L::BAR + i * 8), i % 6 == 4 ? 7 : 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tslot, 512);
@@ -391,8 +404,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   // the group's leader (TMA, MMA issue, waits) is lane 0 of warp 7, which has no depthwise
   // columns in DW1: it issues the residual and bias MMAs while the other warps run DW1
   const bool leader = gtid == 7 * 32;
-  uint64_t* in_bar = reinterpret_cast<uint64_t*>(sm + L::BAR + grp * 32);  // [i]: copy into buffer i
+  uint64_t* in_bar = reinterpret_cast<uint64_t*>(sm + L::BAR + grp * 48);  // [i]: copy into buffer i
   uint64_t* mma_bar = in_bar + 3;
+  uint64_t* half_bar = in_bar + 4;  // the depthwise warps have stored symbols 0..7 (the first M tile's rows)
   unsigned char* g_buf0 = sm + L::GRP + grp * L::GSTRIDE;  // three operand buffers of kBuf bytes
   const uint32_t buf0_s = tc::smem_u32(g_buf0), st_s = buf0_s + 2 * kBuf;
   const uint32_t w1_s = tc::smem_u32(sm + L::W1), w2_s = tc::smem_u32(sm + L::W2), id_s = tc::smem_u32(sm + L::ID),
@@ -418,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const bool rot = !last;
 
   uint32_t in_ph = 0, in_pending = 0;  // bit i: parity / copy in flight of buffer i
-  uint32_t st_ph = 0, mma_ph = 0;
+  uint32_t st_ph = 0, mma_ph = 0, half_ph = 0;
   bool st_pending = false, mma_pending = false;
   const int vt0 = blockIdx.x * 2 + grp, vstride = gridDim.x * 2;
   // both groups run the same number of iterations, so that the turns below pair up
@@ -475,13 +489,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     // leader issues D2 = IN x I + 1 b2^T (the residual, exact: I is exact in 16 bits) and
     // D1 = 1 b1^T, which the PW1 commit below covers
     take_turn();
+    bool ok_half = true;
     if (work && gw < 7) {
       uint32_t ia[4], oa[2];
 #pragma unroll
       for (int k = 0; k < 4; ++k) ia[k] = col_word(in_s, 2 * gw + k, cp);
 #pragma unroll
       for (int o = 0; o < 2; ++o) oa[o] = col_word(a_s, 2 * gw + 1 + o, cp);
-      dw_pair<T, false>(sk1, cp, ia, oa);
+      dw_pair<T, false>(sk1, cp, ia, oa, half_bar);
     } else if (work && leader) {
       tc::tc_fence_after();
       tc::mma_k64(d2, in_s, id_s, idesc16<T>(), false);
@@ -490,7 +505,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_bias<T>(d2 + 64, ones_s, bi2_s, true);
       mma_bias<T>(d1, ones_s, bi1_s, false);
       mma_bias<T>(d1 + 64, ones_s, bi1_s, false);
+      // PW1 of the first M tile while DW1 finishes the second
+      ok_half = wait_bar(half_bar, half_ph);
+      if (ok_half) {
+        tc::tc_fence_after();
+        mma_w<T>(d1, a_s, w1_s, true);
+      }
     }
+    if (work) half_ph ^= 1u;
     pass_turn(false);
     if (work) {
       tc::fence_async_smem();
@@ -501,10 +523,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         st_pending = true;
       }
       group_sync(bar_id);
-      bool ok = true;
-      if (leader) {
+      bool ok = ok_half;
+      if (leader && ok) {
         tc::tc_fence_after();
-        mma_w<T>(d1, a_s, w1_s, true);
         mma_w<T>(d1 + 64, a_s + kM1Row * 128, w1_s, true);
         tc::mma_commit(mma_bar);
         mma_pending = true;
@@ -543,27 +564,36 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     // 5: DW2 + ReLU, output columns 2..13 (warp gw: columns 2 gw + 2, 2 gw + 3)
     take_turn();
+    bool ok_half2 = true;
     if (work && gw < 6) {
       uint32_t ia[4], oa[2];
 #pragma unroll
       for (int k = 0; k < 4; ++k) ia[k] = col_word(in_s, 2 * gw + 1 + k, cp);
 #pragma unroll
       for (int o = 0; o < 2; ++o) oa[o] = col_word(a_s, 2 * gw + 2 + o, cp);
-      dw_pair<T, true>(sk2, cp, ia, oa);
+      dw_pair<T, true>(sk2, cp, ia, oa, half_bar);
+    } else if (work && gw == 6) {
+      if (lane == 0) mbar_arrive(half_bar);  // the seventh arrival: warp 6 has no DW2 columns
+    } else if (work && leader) {  // PW2 of the first M tile while DW2 finishes the second
+      ok_half2 = wait_bar(half_bar, half_ph);
+      if (ok_half2) {
+        tc::tc_fence_after();
+        mma_w<T>(d2, a_s, w2_s, true);
+      }
     }
+    if (work) half_ph ^= 1u;
     pass_turn(final_it);
     if (work) {
       tc::fence_async_smem();
       group_sync(bar_id);
-      bool ok = true;
-      if (leader) {
+      bool ok = ok_half2;
+      if (leader && ok) {
         if (last) {
           ok = wait_bar(in_bar + 2, st_ph);
           if (ok) st_pending = false;
         }
         if (ok) {
           tc::tc_fence_after();
-          mma_w<T>(d2, a_s, w2_s, true);
           mma_w<T>(d2 + 64, a_s + kM1Row * 128, w2_s, true);
           if (last) {
             tc::mma_k64(d2, st_s, id_s, idesc16<T>(), true);
