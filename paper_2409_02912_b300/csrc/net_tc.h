@@ -92,10 +92,11 @@ cudaError_t launch_readout_tc(const Geometry& g, const SlotTable& tab, const Rea
 template <typename T>
 cudaError_t launch_to_f32(const T* in, float* out, size_t n, cudaStream_t st);
 
-// Residual block for 16-bit operands (block_tc.cu): warp-specialised,
-// 12-subcarrier tiles, the residual and state added by identity-weight MMAs,
-// input / state / output tiles moved by bulk tensor copies; requires
-// S % 12 == 0 (always true: S = 12 N_PRB) and 16-byte aligned activations.
+// Residual block for 16-bit operands (block_tc.cu): two tile pipelines per
+// SM whose depthwise phases take turns, 12-subcarrier tiles, the residual and
+// state added by identity-weight MMAs, input / state / output tiles moved by
+// bulk tensor copies; requires S % 12 == 0 (always true: S = 12 N_PRB) and
+// 16-byte aligned activations.
 template <typename T>
 cudaError_t launch_block16_tc(const Geometry& g, const IterWeightsTC& w, int r, const T* z_in, T* z_out, T* state,
                              bool last, cudaStream_t st);
