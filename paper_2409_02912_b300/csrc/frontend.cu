@@ -7,12 +7,14 @@
 
 // ---------------------------------------------------------------------------
 // StateInit (Sec. II-A): S0 = ReLU(DW(PW(x_u))), x_u = [y, h_u, PE].
-// One CTA per (subcarrier tile of TW, user, slot), all 14 symbols.  The PW
-// output is formed on the tile plus a one-subcarrier halo (zero outside the
-// grid, i.e. the depthwise input's zero padding), then the 3x3 depthwise and
-// ReLU produce the tile.  FP32 CUDA-core arithmetic (each thread accumulates
-// 4 REs x 4 channels of the input layer; the depthwise slides over the
-// symbols for one channel pair); output FP32, BF16 or FP16.
+// Persistent CTAs (as many per SM as registers and shared memory allow:
+// three with the register bound of 80) loop over tiles of TW subcarriers of
+// one (slot, user), all 14 symbols.  The PW output is formed on the tile plus
+// a one-subcarrier halo (zero outside the grid, i.e. the depthwise input's
+// zero padding), then the 3x3 depthwise and ReLU produce the tile.  FP32
+// CUDA-core arithmetic (each thread computes the input layer of one RE, four
+// channels at a time; the depthwise slides over the symbols for one channel
+// pair); output FP32, BF16 or FP16.
 // ---------------------------------------------------------------------------
 template <typename OutT>
 __device__ __forceinline__ void store_pair(OutT* p, float a, float b);
@@ -30,7 +32,7 @@ __device__ __forceinline__ void store_pair<__half>(__half* p, float a, float b) 
 }
 
 template <int C, int B, typename OutT>
-__global__ void __launch_bounds__(256) k_state_init(Geometry g, SlotTable tab, const float2* __restrict__ y,
+__global__ void __launch_bounds__(256, 3) k_state_init(Geometry g, SlotTable tab, const float2* __restrict__ y,
                                                     InitWeights wts, OutT* __restrict__ s_out) {
   constexpr int F = 4 * B + 2;
   constexpr int TW = kStateInitTile;
@@ -176,9 +178,14 @@ cudaError_t launch_si(const Geometry& g, const SlotTable& tab, const float2* y, 
                       cudaStream_t st) {
   const size_t smem = state_init_smem_bytes(C, B);
   ensure_smem<k_state_init<C, B, OutT>>((int)smem);
-  int per_sm = (int)((228 * 1024) / (smem + 1024));
-  if (per_sm > 4) per_sm = 4;
-  if (per_sm < 1) per_sm = 1;
+  // resident CTAs per SM (registers and shared memory), so that the grid is one wave
+  static const int per_sm = [smem] {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_state_init<C, B, OutT>, 256, smem) != cudaSuccess ||
+        n < 1)
+      n = 1;
+    return n;
+  }();
   const int tiles = g.n_slots * g.U * ((g.S + kStateInitTile - 1) / kStateInitTile);
   const int grid = tiles < per_sm * sm_count() ? tiles : per_sm * sm_count();
   return launch_pdl(k_state_init<C, B, OutT>, grid, 256, smem, st, g, tab, y, w, s_out);
