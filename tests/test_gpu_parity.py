@@ -106,14 +106,21 @@ def test_lmmse_fp64_redo_pivot_spread(num_users):
 
 
 @pytest.mark.parametrize("workload", ["su_2rx_4prb", "mu2_4rx_24prb", "mu4_4rx_273prb"])
-def test_nrx_fp32_parity(workload):
+def test_nrx_fp32_parity(workload, record_property):
+    """Per (slot, user) within 1e-4; the elementwise relative error (floor
+    1.0, so that small LLRs count in absolute terms) is reported and held to
+    the same bound at its 99th percentile."""
     w, slots = H.slots_for(workload)
     rx = _receiver(w.net, slots)
     y, dmrs, bits, _ = H.device_inputs(slots)
     llr = rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits).cpu().numpy()
     assert rx.last_launch_count() == 2 + w.net.iterations * (1 + w.net.res_blocks)
-    errs = H.rel_errors(llr, H.oracle_nrx(slots, H.weights64(w.net), w.net), slots)
+    refs = H.oracle_nrx(slots, H.weights64(w.net), w.net)
+    errs = H.rel_errors(llr, refs, slots)
+    med, p99 = H.elementwise_rel(llr, refs, slots)
+    record_property("elementwise_rel_median_p99", (med, p99))
     assert max(errs) <= TOL_FP32, errs
+    assert p99 <= TOL_FP32, (med, p99)
 
 
 EDGE = [
@@ -246,17 +253,23 @@ TC_MODES = ["bf16", "fp16"]
 
 @pytest.mark.parametrize("prec", TC_MODES)
 @pytest.mark.parametrize("workload", ["mu2_4rx_24prb", "mu4_4rx_273prb"])
-def test_nrx_tc_parity(workload, prec):
+def test_nrx_tc_parity(workload, prec, record_property):
     """Tensor-core path (tcgen05 GEMMs on 16-bit operands, 16-bit activations)
-    vs the FP64 oracle."""
+    vs the FP64 oracle; the elementwise relative error (floor 1.0) is
+    reported and its median held to the same bound."""
     w, slots = H.slots_for(workload)
     rx = _receiver(w.net, slots, prec)
     y, dmrs, bits, _ = H.device_inputs(slots)
     llr = rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits).cpu().numpy()
     rx.nrx_check()
     assert rx.last_launch_count() == 2 + w.net.iterations * (1 + w.net.res_blocks)
-    errs = H.rel_errors(llr, H.oracle_nrx(slots, H.weights64(w.net), w.net), slots)
+    refs = H.oracle_nrx(slots, H.weights64(w.net), w.net)
+    errs = H.rel_errors(llr, refs, slots)
+    med, p99 = H.elementwise_rel(llr, refs, slots)
+    record_property("elementwise_rel_median_p99", (med, p99))
+    print(prec, workload, "worst", max(errs), "elementwise median", med, "p99", p99)
     assert max(errs) <= TOL_TC, errs
+    assert med <= TOL_TC, (med, p99)
 
 
 def test_trained_network_parity():
