@@ -53,6 +53,7 @@ cudaError_t debug_read_frontend(unsigned long long* out, bool reset);
 cudaError_t debug_read_net_f32(unsigned long long* out, bool reset);
 cudaError_t debug_read_net_tc(unsigned long long* out, bool reset);
 cudaError_t debug_read_block_tc(unsigned long long* out, bool reset);
+cudaError_t debug_read_mp_tc(unsigned long long* out, bool reset);
 cudaError_t debug_read_ldpc(unsigned long long* out, bool reset);
 cudaError_t debug_read_train(unsigned long long* out, bool reset);
 

@@ -1380,6 +1380,7 @@ cudaError_t state_rows_map(CUtensorMap* map, const T* base, int planes, int n_re
 template <typename P>
 cudaError_t launch_mp_tc(const Geometry& g, const IterWeightsTC& w, const typename P::T* state, typename P::T* z,
                          cudaStream_t st) {
+  if constexpr (!P::fp8) return launch_mp16_tc<typename P::T>(g, w, state, z, st);
   if (g.C != 64) return cudaErrorInvalidValue;
   const int nre = g.U == 4 ? 32 : g.U == 3 ? 40 : g.U == 2 ? 64 : 128;
   const int tps = (NRX_SYMBOLS * g.S + nre - 1) / nre;
@@ -1452,6 +1453,9 @@ cudaError_t state_rows_map(CUtensorMap* map, const T* base, int planes, int n_re
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
+
+template cudaError_t state_rows_map<__nv_bfloat16>(CUtensorMap*, const __nv_bfloat16*, int, int, int, int);
+template cudaError_t state_rows_map<__half>(CUtensorMap*, const __half*, int, int, int, int);
 
 template <typename P>
 cudaError_t launch_block_tc(const Geometry& g, const IterWeightsTC& w, int r, const typename P::T* z_in,

@@ -101,6 +101,15 @@ template <typename T>
 cudaError_t launch_block16_tc(const Geometry& g, const IterWeightsTC& w, int r, const T* z_in, T* z_out, T* state,
                              bool last, cudaStream_t st);
 
+// Message passing + CNN-update input layer for 16-bit operands (mp_tc.cu):
+// eight worker warps and one issuer warp that runs the bulk tensor copies and
+// the MMAs a tile ahead; requires 16-byte aligned activations.
+template <typename T>
+cudaError_t launch_mp16_tc(const Geometry& g, const IterWeightsTC& w, const T* state, T* z, cudaStream_t st);
+
+// Number of SMs of the current device (cached).
+int block_sms();
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (null if
 // the driver does not provide it).
 #include <cudaTypedefs.h>

@@ -734,7 +734,8 @@ nrx_status nrx_debug_counters(int64_t* violations, int32_t* first_site, int64_t*
   if (!violations) return NRX_EINVAL;
   cudaError_t (*const readers[])(unsigned long long*, bool) = {debug_read_frontend, debug_read_net_f32,
                                                                debug_read_net_tc,   debug_read_block_tc,
-                                                               debug_read_ldpc,     debug_read_train};
+                                                               debug_read_mp_tc,    debug_read_ldpc,
+                                                               debug_read_train};
   int64_t total = 0;
   bool have_first = false;
   for (auto rd : readers) {
