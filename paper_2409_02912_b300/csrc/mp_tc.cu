@@ -381,6 +381,15 @@ __global__ void __launch_bounds__(kThreads, 2)
       tc::fence_async_smem();
       workers_sync();
       if (tid == 0) mbar_arrive1(bars + kGReady);
+      // PE of this thread's row, computed while the G part of GEMM2 runs
+      float pt = 0.f, pf = 0.f;
+      {
+        const int u = r / nre, j = r % nre, re = re0 + j;
+        if (u < U && re < n_re) {
+          pt = pe_time(g, re / S);
+          pf = pe_freq(u, re % S);
+        }
+      }
       {
         bool ok = true;
         if (tid == 0) ok = mp_wait(bars + kZFull, ph_z);
@@ -405,12 +414,6 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int e = 0; e < 16; ++e) {
           acc[e] = __uint_as_float(a[e]);
           acc[16 + e] = __uint_as_float(b[e]);
-        }
-        const int u = r / nre, j = r % nre, re = re0 + j;
-        float pt = 0.f, pf = 0.f;
-        if (u < U && re < n_re) {
-          pt = pe_time(g, re / S);
-          pf = pe_freq(u, re % S);
         }
         const float* bb = vec + 64 + 32 * hc;
         const float* wt = vec + 128 + 32 * hc;
