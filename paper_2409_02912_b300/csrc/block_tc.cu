@@ -15,9 +15,10 @@
 //      the state tile ST, keeps fixed roles).
 //   2. DW1 (columns 1..14) from IN -> A, while the leader issues
 //      D2 = IN x I + 1 b2^T (identity weights: the residual lands in the PW2
-//      accumulator exactly, since I is exact in 16 bits), D1 = 1 b1^T and,
-//      once DW1 has stored symbols 0..7, D1 += A W1^T on the first M tile.
-//   3. MMA: D1 += A W1^T on the second M tile.
+//      accumulator exactly, since I is exact in 16 bits), D1 = 1 b1^T and
+//      (BF16) once DW1 has stored symbols 0..7, D1 += A W1^T on the first
+//      M tile.
+//   3. MMA: D1 += A W1^T on the second M tile (FP16: on both).
 //   4. Epilogue 1: P1 = ReLU(D1), zero outside the grid, over IN.
 //   5. DW2 + ReLU (columns 2..13) from P1 -> A.  MMA: D2 += A W2^T (the
 //      first M tile during DW2, as in 2) (+ ST x I: the state tile, last
@@ -63,6 +64,8 @@ struct Ops<__nv_bfloat16> {
   static constexpr uint32_t fmt = 1;
   static constexpr uint16_t one = 0x3F80;
   static constexpr bool split = true;
+  // each PW's first M tile issued once the depthwise warps have stored its rows
+  static constexpr bool early_pw = true;
   __device__ static __forceinline__ uint32_t pack(float a, float b) { return tc::pack_bf16x2(a, b); }
   __device__ static __forceinline__ uint32_t pack_relu(float a, float b) { return tc::pack_relu_bf16x2(a, b); }
 };
@@ -71,6 +74,9 @@ struct Ops<__half> {
   static constexpr uint32_t fmt = 0;
   static constexpr uint16_t one = 0x3C00;
   static constexpr bool split = false;
+  // PWs issued after the depthwise phase: with packed FP16 taps the depthwise
+  // phases lost more to the early MMAs' shared-memory reads than the overlap gained
+  static constexpr bool early_pw = false;
   __device__ static __forceinline__ uint32_t pack(float a, float b) {
     __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
@@ -274,7 +280,7 @@ __device__ __forceinline__ void dw_pair(const float* __restrict__ taps, int cp, 
     step(tb, true);
     step(tb + 1, true);
     step(tb + 2, true);
-    if (tb == 6) {  // symbols 0..7 stored: the rows of the first M tile are complete
+    if (Ops<T>::early_pw && tb == 6) {  // symbols 0..7 stored: the rows of the first M tile are complete
       tc::fence_async_smem();
       __syncwarp();
       if (cp == 0) mbar_arrive(half_bar);
@@ -505,11 +511,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_bias<T>(d2 + 64, ones_s, bi2_s, true);
       mma_bias<T>(d1, ones_s, bi1_s, false);
       mma_bias<T>(d1 + 64, ones_s, bi1_s, false);
-      // PW1 of the first M tile while DW1 finishes the second
-      ok_half = wait_bar(half_bar, half_ph);
-      if (ok_half) {
-        tc::tc_fence_after();
-        mma_w<T>(d1, a_s, w1_s, true);
+      if constexpr (Ops<T>::early_pw) {  // PW1 of the first M tile while DW1 finishes the second
+        ok_half = wait_bar(half_bar, half_ph);
+        if (ok_half) {
+          tc::tc_fence_after();
+          mma_w<T>(d1, a_s, w1_s, true);
+        }
       }
     }
     if (work) half_ph ^= 1u;
@@ -526,6 +533,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = ok_half;
       if (leader && ok) {
         tc::tc_fence_after();
+        if constexpr (!Ops<T>::early_pw) mma_w<T>(d1, a_s, w1_s, true);
         mma_w<T>(d1 + 64, a_s + kM1Row * 128, w1_s, true);
         tc::mma_commit(mma_bar);
         mma_pending = true;
@@ -573,12 +581,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int o = 0; o < 2; ++o) oa[o] = col_word(a_s, 2 * gw + 2 + o, cp);
       dw_pair<T, true>(sk2, cp, ia, oa, half_bar);
     } else if (work && gw == 6) {
-      if (lane == 0) mbar_arrive(half_bar);  // the seventh arrival: warp 6 has no DW2 columns
+      if (Ops<T>::early_pw && lane == 0) mbar_arrive(half_bar);  // the seventh arrival: warp 6 has no DW2 columns
     } else if (work && leader) {  // PW2 of the first M tile while DW2 finishes the second
-      ok_half2 = wait_bar(half_bar, half_ph);
-      if (ok_half2) {
-        tc::tc_fence_after();
-        mma_w<T>(d2, a_s, w2_s, true);
+      if constexpr (Ops<T>::early_pw) {
+        ok_half2 = wait_bar(half_bar, half_ph);
+        if (ok_half2) {
+          tc::tc_fence_after();
+          mma_w<T>(d2, a_s, w2_s, true);
+        }
       }
     }
     if (work) half_ph ^= 1u;
@@ -594,6 +604,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (ok) {
           tc::tc_fence_after();
+          if constexpr (!Ops<T>::early_pw) mma_w<T>(d2, a_s, w2_s, true);
           mma_w<T>(d2 + 64, a_s + kM1Row * 128, w2_s, true);
           if (last) {
             tc::mma_k64(d2, st_s, id_s, idesc16<T>(), true);
