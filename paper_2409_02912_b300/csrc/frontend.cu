@@ -46,7 +46,9 @@ __global__ void __launch_bounds__(256, 3) k_state_init(Geometry g, SlotTable tab
   float* wt = reinterpret_cast<float*>(hf + 2 * B * EW);  // [F][C]
   float* kd = wt + F * C;                                // [C][9]
   float* bias = kd + 9 * C;                              // [C]
-  float* h = bias + C;  // [NRE][C], float4 chunk q of row r stored at q ^ (r & (NQ - 1))
+  // [NRE][C]: float4 chunk q of row r = t * EW + e stored at q ^ (e & (NQ - 1)), so a
+  // depthwise column's addresses step by a constant over the symbols
+  float* h = bias + C;
 
   const int tid = threadIdx.x;
   int loaded = -1;  // head whose weights are in shared memory
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(256, 3) k_state_init(Geometry g, SlotTable tab
             a01 = tc::ffma2(make_float2(w.x, w.y), xk, a01);
             a23 = tc::ffma2(make_float2(w.z, w.w), xk, a23);
           }
-          hrow[q ^ (tid & (NQ - 1))] = make_float4(a01.x, a01.y, a23.x, a23.y);
+          hrow[q ^ (e & (NQ - 1))] = make_float4(a01.x, a01.y, a23.x, a23.y);
         }
       }
     }
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(256, 3) k_state_init(Geometry g, SlotTable tab
             kk,
             [&](int ti, int k) {
               const int r = ti * EW + xc + k;
-              const int hi = r * C + (((cp >> 1) ^ (r & (NQ - 1))) << 2) + (cp & 1) * 2;
+              const int hi = r * C + (((cp >> 1) ^ ((xc + k) & (NQ - 1))) << 2) + (cp & 1) * 2;
               return NRX_IN(hi + 1, NRE * C, 104) ? *reinterpret_cast<const float2*>(h + hi) : make_float2(0.f, 0.f);
             },
             [&](int t, float2 v) {

@@ -1029,6 +1029,17 @@ struct RoLayout {
   static constexpr int DYN = TOTAL + 1024;
 };
 
+// The read-out's last layer on 32 of the 64 hidden values of one RE: outputs
+// 0..M-1 (M = m rounded up to even; an extra output is computed and not stored),
+// M independent FMA chains.  w2 points at column 0 of the half: [8][64] FP32.
+template <int M>
+__device__ __forceinline__ void ro_accumulate(const float* w2, const float (&h)[32], float (&a)[8]) {
+#pragma unroll
+  for (int k = 0; k < 32; ++k)
+#pragma unroll
+    for (int o = 0; o < M; ++o) a[o] = fmaf(w2[o * 64 + k], h[k], a[o]);
+}
+
 template <typename P>
 __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, ReadoutWeightsTC w,
                                                     const typename P::T* __restrict__ state, float* __restrict__ llr,
@@ -1160,25 +1171,40 @@ __global__ void __launch_bounds__(128) k_readout_tc(Geometry g, SlotTable tab, R
         tma_pending = true;
       }
     }
-    float h[64];
-    tc::tmem_row64(c.tmem + ((uint32_t)(warp * 32) << 16), h);
+    // h = ReLU(D + b1) in two halves of 32 columns, each half's products added to the
+    // outputs' FMA chains (one chain per output, over k = 0..63 in order) before the next
+    // half is read, so only 32 hidden values are live at a time
     const int rd = dsym * S + s0 + row;  // data RE index
-    if (s0 + row < S) {
+    const int m = tab.bits[sl][u];       // uniform over the tile
+    float a[8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) a[o] = sb2[o];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      float h[32];
+      tc::tmem_row32(c.tmem + ((uint32_t)(warp * 32) << 16) + 32 * half, h);
       if constexpr (P::fp8) {
         const float rs = ssc[64 + row];
 #pragma unroll
-        for (int k = 0; k < 64; ++k) h[k] *= rs * ssc[k];
+        for (int k = 0; k < 32; ++k) h[k] *= rs * ssc[32 * half + k];
       }
 #pragma unroll
-      for (int k = 0; k < 64; ++k) h[k] = fmaxf(h[k] + sb1[k], 0.f);
-      const int m = tab.bits[sl][u];
+      for (int k = 0; k < 32; ++k) h[k] = fmaxf(h[k] + sb1[32 * half + k], 0.f);
+      if (m <= 2)
+        ro_accumulate<2>(w2 + 32 * half, h, a);
+      else if (m <= 4)
+        ro_accumulate<4>(w2 + 32 * half, h, a);
+      else if (m <= 6)
+        ro_accumulate<6>(w2 + 32 * half, h, a);
+      else
+        ro_accumulate<8>(w2 + 32 * half, h, a);
+    }
+    if (s0 + row < S) {
       float* dst = llr + tab.llr_off[sl][u] + (size_t)rd * m;
-      for (int o = 0; o < m; ++o) {
-        if (!NRX_IN(tab.llr_off[sl][u] + (long long)rd * m + o, tab.llr_total, 312)) break;
-        float a = sb2[o];
 #pragma unroll
-        for (int k = 0; k < 64; ++k) a = fmaf(w2[o * 64 + k], h[k], a);
-        dst[o] = a;
+      for (int o = 0; o < 8; ++o) {
+        if (o >= m || !NRX_IN(tab.llr_off[sl][u] + (long long)rd * m + o, tab.llr_total, 312)) break;
+        dst[o] = a[o];
       }
     }
     tc::tc_fence_before();
@@ -1508,7 +1534,18 @@ cudaError_t launch_readout_tc(const Geometry& g, const SlotTable& tab, const Rea
     const cudaError_t e = readout_rows_map(&rmap, state, g.n_slots * g.U, g.S);
     if (e != cudaSuccess) return e;
   }
-  const int grid = grid_for(smem, 8, tiles);  // 8 x 64 TMEM columns per SM
+  // resident CTAs per SM from the kernel's registers (allocated per warp in units of
+  // 256) and shared memory, at most 8 x 64 TMEM columns, so that the grid is one wave
+  // (a grid of 1.5 waves measured 12-23% slower)
+  static const int per_sm = [smem] {
+    int n = 8;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k_readout_tc<P>) == cudaSuccess && fa.numRegs > 0)
+      n = std::min(n, 65536 / (((fa.numRegs * 32 + 255) / 256) * 256 * 4));
+    n = std::min(n, (228 * 1024) / (smem + 1024));
+    return std::max(n, 1);
+  }();
+  const int grid = tiles < per_sm * num_sms() ? tiles : per_sm * num_sms();
   return launch_pdl(k_readout_tc<P>, grid, 128, smem, st, g, tab, w, state, llr, tpsu, rmap);
 }
 

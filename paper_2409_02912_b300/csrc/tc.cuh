@@ -213,6 +213,20 @@ __device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16]) {
                : "memory");
 }
 
+// 32 FP32 columns of this thread's lane (row) into v.
+__device__ __forceinline__ void tmem_row32(uint32_t taddr, float (&v)[32]) {
+  uint32_t a[16], b[16];
+  tmem_ld16(taddr, a);
+  tmem_ld16(taddr + 16, b);
+  tmem_wait16(a);
+  tmem_wait16(b);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    v[i] = __uint_as_float(a[i]);
+    v[16 + i] = __uint_as_float(b[i]);
+  }
+}
+
 // 64 FP32 columns of this thread's lane (row) into v.
 __device__ __forceinline__ void tmem_row64(uint32_t taddr, float (&v)[64]) {
   uint32_t a[16], b[16], c[16], d[16];
