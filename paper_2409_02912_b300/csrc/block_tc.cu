@@ -1,8 +1,13 @@
 // Residual block of the CNN update (Sec. II-A) on the tensor cores, 16-bit
-// operands (BF16 with split weights, or FP16):
+// activations (BF16 or FP16) in and out:
 //   z_out = z_in + PW2(ReLU(DW2(ReLU(PW1(DW1(z_in))))))     (+ S, last block)
 // with 3x3 depthwise taps DW on the CUDA cores and the 1x1 layers PW as
-// tcgen05 MMAs with FP32 accumulators in TMEM.
+// tcgen05 MMAs with FP32 accumulators in TMEM.  The block's intermediates
+// (the depthwise outputs, which are the PW operands, and P1) are FP16, the
+// taps run as packed FP16 FMAs and the PW weights are FP16 in both modes:
+// FP16 carries three more mantissa bits than BF16, so the BF16 mode needs no
+// split (hi + lo) weights here; the input, the residual, the biases and the
+// output stay in the activation type.
 //
 // Tiles: 12 subcarriers x 14 symbols of one (slot, user); since S = 12 N_PRB
 // no tile is ragged.  Every operand tile has 224 rows, row = t * 16 + c, over
@@ -15,14 +20,11 @@
 //      the state tile ST, keeps fixed roles).
 //   2. DW1 (columns 1..14) from IN -> A, while the leader issues
 //      D2 = IN x I + 1 b2^T (identity weights: the residual lands in the PW2
-//      accumulator exactly, since I is exact in 16 bits), D1 = 1 b1^T and
-//      (BF16) once DW1 has stored symbols 0..7, D1 += A W1^T on the first
-//      M tile.
-//   3. MMA: D1 += A W1^T on the second M tile (FP16: on both).
+//      accumulator exactly, since I is exact in 16 bits) and D1 = 1 b1^T.
+//   3. MMA: D1 += A W1^T on both M tiles.
 //   4. Epilogue 1: P1 = ReLU(D1), zero outside the grid, over IN.
-//   5. DW2 + ReLU (columns 2..13) from P1 -> A.  MMA: D2 += A W2^T (the
-//      first M tile during DW2, as in 2) (+ ST x I: the state tile, last
-//      block).
+//   5. DW2 + ReLU (columns 2..13) from P1 -> A.  MMA: D2 += A W2^T (+ ST x I:
+//      the state tile, last block).
 //   6. Epilogue 2: D2 -> OUT (in A; rows t * 12 + c - 2) -> TMA store.
 // The biases enter the accumulators through one K = 16 MMA of an all-ones
 // tile with a tile holding [b_hi, b_lo], b_hi the 16-bit rounding of b and
@@ -63,9 +65,6 @@ template <>
 struct Ops<__nv_bfloat16> {
   static constexpr uint32_t fmt = 1;
   static constexpr uint16_t one = 0x3F80;
-  static constexpr bool split = true;
-  // each PW's first M tile issued once the depthwise warps have stored its rows
-  static constexpr bool early_pw = true;
   __device__ static __forceinline__ uint32_t pack(float a, float b) { return tc::pack_bf16x2(a, b); }
   __device__ static __forceinline__ uint32_t pack_relu(float a, float b) { return tc::pack_relu_bf16x2(a, b); }
 };
@@ -73,10 +72,6 @@ template <>
 struct Ops<__half> {
   static constexpr uint32_t fmt = 0;
   static constexpr uint16_t one = 0x3C00;
-  static constexpr bool split = false;
-  // PWs issued after the depthwise phase: with packed FP16 taps the depthwise
-  // phases lost more to the early MMAs' shared-memory reads than the overlap gained
-  static constexpr bool early_pw = false;
   __device__ static __forceinline__ uint32_t pack(float a, float b) {
     __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
@@ -93,7 +88,7 @@ constexpr uint32_t idesc16() {  // kind::f16, M = 128, N = 64, FP32 accumulate, 
 // Shared-memory layout (offsets from the 1024-byte-aligned base).
 template <typename T>
 struct Lay {
-  static constexpr int WB = Ops<T>::split ? 16384 : 8192;  // one packed 64 x 64 weight (hi [+ lo])
+  static constexpr int WB = 8192;             // one packed 64 x 64 FP16 weight (both modes)
   static constexpr int W1 = 0;
   static constexpr int W2 = W1 + WB;
   static constexpr int ID = W2 + WB;          // 64 x 64 identity, SW128
@@ -181,39 +176,24 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, uint64_
   return false;
 }
 
-// Plain arrive (count 1) on an mbarrier.
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
-}
-
 // Sliding 3x3 depthwise over the 14 symbols for two adjacent output columns
-// of one channel pair (2 cp, 2 cp + 1).  in_addr[k] (k < 4) addresses this
-// lane's word of input column k on symbol 0 (one symbol = 16 rows = 2048
-// bytes further); out_addr[o] likewise for output column o.  Zero padding in
-// time; kRelu applies max(., 0).  BF16: FP32 FMAs; FP16: packed FP16 FMAs.  The words of symbol ti + 2 are requested before
-// symbol ti is computed.  Symbols 0..11 run as a loop over blocks of three
-// (the period of the register window), 12 and 13 after it: a small loop body
-// keeps the kernel's code within the instruction caches.
-template <typename T, bool kRelu>
+// of one channel pair (2 cp, 2 cp + 1), packed FP16 FMAs with FP16 taps.
+// in_addr[k] (k < 4) addresses this lane's word of input column k on symbol 0
+// (one symbol = 16 rows = 2048 bytes further); out_addr[o] likewise for
+// output column o.  Inputs Tin (a BF16 pair is rounded to an FP16 pair on
+// load), FP16 outputs; zero padding in time; kRelu applies max(., 0).  The
+// words of symbol ti + 2 are requested before symbol ti is computed.  Symbols
+// 0..11 run as a loop over blocks of three (the period of the register
+// window), 12 and 13 after it: a small loop body keeps the kernel's code
+// within the instruction caches.
+template <typename Tin, bool kRelu>
 __device__ __forceinline__ void dw_pair(const float* __restrict__ taps, int cp, const uint32_t (&in_addr)[4],
-                                        const uint32_t (&out_addr)[2], uint64_t* half_bar) {
-  constexpr bool kBf16 = std::is_same<T, __nv_bfloat16>::value;
-  using Acc = typename std::conditional<kBf16, float2, __half2>::type;  // (channel 2 cp, channel 2 cp + 1)
-  Acc kk[9];
+                                        const uint32_t (&out_addr)[2]) {
+  __half2 kk[9];  // (channel 2 cp, channel 2 cp + 1)
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const float a = taps[(2 * cp) * 9 + i], b = taps[(2 * cp + 1) * 9 + i];
-    if constexpr (kBf16)
-      kk[i] = make_float2(a, b);
-    else
-      kk[i] = __floats2half2_rn(a, b);
-  }
-  Acc zero;
-  if constexpr (kBf16)
-    zero = make_float2(0.f, 0.f);
-  else
-    zero = __float2half2_rn(0.f);
-  Acc am[2], a0[2], ap[2];  // per output column: outputs of symbols ti - 1, ti, ti + 1
+  for (int i = 0; i < 9; ++i) kk[i] = __floats2half2_rn(taps[(2 * cp) * 9 + i], taps[(2 * cp + 1) * 9 + i]);
+  const __half2 zero = __float2half2_rn(0.f);
+  __half2 am[2], a0[2], ap[2];  // per output column: outputs of symbols ti - 1, ti, ti + 1
 #pragma unroll
   for (int j = 0; j < 2; ++j) am[j] = a0[j] = ap[j] = zero;
   uint32_t w0[4], w1[4], w2[4];  // words of symbols ti, ti + 1, ti + 2
@@ -223,25 +203,19 @@ __device__ __forceinline__ void dw_pair(const float* __restrict__ taps, int cp, 
     w1[k] = lds32(in_addr[k] + 2048);
   }
   auto put = [&](int t, int o) {
-    uint32_t word;
-    if constexpr (kBf16) {
-      word = kRelu ? tc::pack_relu_bf16x2(am[o].x, am[o].y) : tc::pack_bf16x2(am[o].x, am[o].y);
-    } else {
-      __half2 v = am[o];
-      if (kRelu) v = __hmax2(v, zero);
-      word = *reinterpret_cast<uint32_t*>(&v);
-    }
-    sts32c(out_addr[o] + t * 2048, word);
+    __half2 v = am[o];
+    if (kRelu) v = __hmax2(v, zero);
+    sts32c(out_addr[o] + t * 2048, *reinterpret_cast<uint32_t*>(&v));
   };
   auto step = [&](int ti, bool prefetch) {
     if (prefetch)
 #pragma unroll
       for (int k = 0; k < 4; ++k) w2[k] = lds32(in_addr[k] + (ti + 2) * 2048);
-    Acc x[4];
+    __half2 x[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      if constexpr (kBf16)
-        x[k] = make_float2(__uint_as_float(w0[k] << 16), __uint_as_float(w0[k] & 0xFFFF0000u));
+      if constexpr (std::is_same<Tin, __nv_bfloat16>::value)
+        x[k] = __floats2half2_rn(__uint_as_float(w0[k] << 16), __uint_as_float(w0[k] & 0xFFFF0000u));
       else
         x[k] = *reinterpret_cast<const __half2*>(&w0[k]);
     }
@@ -249,15 +223,9 @@ __device__ __forceinline__ void dw_pair(const float* __restrict__ taps, int cp, 
     for (int o = 0; o < 2; ++o)
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        if constexpr (kBf16) {  // scalar FMAs: measured faster here than the packed f32x2 form
-          am[o] = make_float2(fmaf(kk[6 + k].x, x[o + k].x, am[o].x), fmaf(kk[6 + k].y, x[o + k].y, am[o].y));
-          a0[o] = make_float2(fmaf(kk[3 + k].x, x[o + k].x, a0[o].x), fmaf(kk[3 + k].y, x[o + k].y, a0[o].y));
-          ap[o] = make_float2(fmaf(kk[k].x, x[o + k].x, ap[o].x), fmaf(kk[k].y, x[o + k].y, ap[o].y));
-        } else {
-          am[o] = __hfma2(kk[6 + k], x[o + k], am[o]);
-          a0[o] = __hfma2(kk[3 + k], x[o + k], a0[o]);
-          ap[o] = __hfma2(kk[k], x[o + k], ap[o]);
-        }
+        am[o] = __hfma2(kk[6 + k], x[o + k], am[o]);
+        a0[o] = __hfma2(kk[3 + k], x[o + k], a0[o]);
+        ap[o] = __hfma2(kk[k], x[o + k], ap[o]);
       }
     if (ti >= 1) {
       put(ti - 1, 0);
@@ -280,11 +248,6 @@ __device__ __forceinline__ void dw_pair(const float* __restrict__ taps, int cp, 
     step(tb, true);
     step(tb + 1, true);
     step(tb + 2, true);
-    if (Ops<T>::early_pw && tb == 6) {  // symbols 0..7 stored: the rows of the first M tile are complete
-      tc::fence_async_smem();
-      __syncwarp();
-      if (cp == 0) mbar_arrive(half_bar);
-    }
   }
   step(12, false);
   step(13, false);
@@ -315,11 +278,10 @@ __device__ __forceinline__ void store_row(uint32_t row_addr, int row, const floa
   }
 }
 
-// K = 64 product of one M tile with a packed weight (hi, then lo if split).
+// K = 64 product of one M tile with a packed 64 x 64 weight.
 template <typename T>
 __device__ __forceinline__ void mma_w(uint32_t d, uint32_t a, uint32_t w, bool acc) {
   tc::mma_k64(d, a, w, idesc16<T>(), acc);
-  if constexpr (Ops<T>::split) tc::mma_k64(d, a, w + 8192, idesc16<T>(), true);
 }
 
 // Shared-memory descriptor of a K-major tile without swizzle: 8-row x 16-byte
@@ -349,6 +311,10 @@ __global__ void __launch_bounds__(kThreads, 1)
              const float* __restrict__ k2g, int last, int* err, const __grid_constant__ CUtensorMap in_map,
              const __grid_constant__ CUtensorMap st_map, const __grid_constant__ CUtensorMap out_map) {
   using L = Lay<T>;
+  // Inside the block the depthwise outputs (PW operands) and P1 are FP16, the taps
+  // packed FP16 FMAs and the PW weights FP16 in both modes; the input, the residual,
+  // the biases and the output keep T.
+  using TI = __half;
   tc::pdl_launch_dependents();
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -393,8 +359,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::BAR + 96);
   if (tid == 0) {
-    // per group (48 bytes): copies into buffers 0..2, MMA commits, the depthwise half-way arrivals (7 warps)
-    for (int i = 0; i < 12; ++i) tc::mbar_init(reinterpret_cast<uint64_t*>(sm + L::BAR + i * 8), i % 6 == 4 ? 7 : 1);
+    // per group (48 bytes): copies into buffers 0..2, MMA commits (two slots unused)
+    for (int i = 0; i < 12; ++i) tc::mbar_init(reinterpret_cast<uint64_t*>(sm + L::BAR + i * 8), 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tslot, 512);
@@ -412,7 +378,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const bool leader = gtid == 7 * 32;
   uint64_t* in_bar = reinterpret_cast<uint64_t*>(sm + L::BAR + grp * 48);  // [i]: copy into buffer i
   uint64_t* mma_bar = in_bar + 3;
-  uint64_t* half_bar = in_bar + 4;  // the depthwise warps have stored symbols 0..7 (the first M tile's rows)
   unsigned char* g_buf0 = sm + L::GRP + grp * L::GSTRIDE;  // three operand buffers of kBuf bytes
   const uint32_t buf0_s = tc::smem_u32(g_buf0), st_s = buf0_s + 2 * kBuf;
   const uint32_t w1_s = tc::smem_u32(sm + L::W1), w2_s = tc::smem_u32(sm + L::W2), id_s = tc::smem_u32(sm + L::ID),
@@ -438,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const bool rot = !last;
 
   uint32_t in_ph = 0, in_pending = 0;  // bit i: parity / copy in flight of buffer i
-  uint32_t st_ph = 0, mma_ph = 0, half_ph = 0;
+  uint32_t st_ph = 0, mma_ph = 0;
   bool st_pending = false, mma_pending = false;
   const int vt0 = blockIdx.x * 2 + grp, vstride = gridDim.x * 2;
   // both groups run the same number of iterations, so that the turns below pair up
@@ -495,14 +460,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     // leader issues D2 = IN x I + 1 b2^T (the residual, exact: I is exact in 16 bits) and
     // D1 = 1 b1^T, which the PW1 commit below covers
     take_turn();
-    bool ok_half = true;
     if (work && gw < 7) {
       uint32_t ia[4], oa[2];
 #pragma unroll
       for (int k = 0; k < 4; ++k) ia[k] = col_word(in_s, 2 * gw + k, cp);
 #pragma unroll
       for (int o = 0; o < 2; ++o) oa[o] = col_word(a_s, 2 * gw + 1 + o, cp);
-      dw_pair<T, false>(sk1, cp, ia, oa, half_bar);
+      dw_pair<T, false>(sk1, cp, ia, oa);
     } else if (work && leader) {
       tc::tc_fence_after();
       tc::mma_k64(d2, in_s, id_s, idesc16<T>(), false);
@@ -511,15 +475,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_bias<T>(d2 + 64, ones_s, bi2_s, true);
       mma_bias<T>(d1, ones_s, bi1_s, false);
       mma_bias<T>(d1 + 64, ones_s, bi1_s, false);
-      if constexpr (Ops<T>::early_pw) {  // PW1 of the first M tile while DW1 finishes the second
-        ok_half = wait_bar(half_bar, half_ph);
-        if (ok_half) {
-          tc::tc_fence_after();
-          mma_w<T>(d1, a_s, w1_s, true);
-        }
-      }
     }
-    if (work) half_ph ^= 1u;
     pass_turn(false);
     if (work) {
       tc::fence_async_smem();
@@ -530,11 +486,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         st_pending = true;
       }
       group_sync(bar_id);
-      bool ok = ok_half;
-      if (leader && ok) {
+      bool ok = true;
+      if (leader) {
         tc::tc_fence_after();
-        if constexpr (!Ops<T>::early_pw) mma_w<T>(d1, a_s, w1_s, true);
-        mma_w<T>(d1 + 64, a_s + kM1Row * 128, w1_s, true);
+        mma_w<TI>(d1, a_s, w1_s, true);
+        mma_w<TI>(d1 + 64, a_s + kM1Row * 128, w1_s, true);
         tc::mma_commit(mma_bar);
         mma_pending = true;
         const int nt = tile + vstride;
@@ -564,7 +520,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::tmem_row64(d1 + e_mt * 64 + e_lane, v);
         if (e_c >= 1 && e_c <= 14) {
           const int s = s0 - 2 + e_c;
-          store_row<T, true>(in_s + e_r * 128, e_r, v, s < 0 || s >= S);
+          store_row<TI, true>(in_s + e_r * 128, e_r, v, s < 0 || s >= S);
         }
       }
       tc::tc_fence_before();
@@ -572,40 +528,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     // 5: DW2 + ReLU, output columns 2..13 (warp gw: columns 2 gw + 2, 2 gw + 3)
     take_turn();
-    bool ok_half2 = true;
     if (work && gw < 6) {
       uint32_t ia[4], oa[2];
 #pragma unroll
       for (int k = 0; k < 4; ++k) ia[k] = col_word(in_s, 2 * gw + 1 + k, cp);
 #pragma unroll
       for (int o = 0; o < 2; ++o) oa[o] = col_word(a_s, 2 * gw + 2 + o, cp);
-      dw_pair<T, true>(sk2, cp, ia, oa, half_bar);
-    } else if (work && gw == 6) {
-      if (Ops<T>::early_pw && lane == 0) mbar_arrive(half_bar);  // the seventh arrival: warp 6 has no DW2 columns
-    } else if (work && leader) {  // PW2 of the first M tile while DW2 finishes the second
-      if constexpr (Ops<T>::early_pw) {
-        ok_half2 = wait_bar(half_bar, half_ph);
-        if (ok_half2) {
-          tc::tc_fence_after();
-          mma_w<T>(d2, a_s, w2_s, true);
-        }
-      }
+      dw_pair<TI, true>(sk2, cp, ia, oa);
     }
-    if (work) half_ph ^= 1u;
     pass_turn(final_it);
     if (work) {
       tc::fence_async_smem();
       group_sync(bar_id);
-      bool ok = ok_half2;
-      if (leader && ok) {
+      bool ok = true;
+      if (leader) {
         if (last) {
           ok = wait_bar(in_bar + 2, st_ph);
           if (ok) st_pending = false;
         }
         if (ok) {
           tc::tc_fence_after();
-          if constexpr (!Ops<T>::early_pw) mma_w<T>(d2, a_s, w2_s, true);
-          mma_w<T>(d2 + 64, a_s + kM1Row * 128, w2_s, true);
+          mma_w<TI>(d2, a_s, w2_s, true);
+          mma_w<TI>(d2 + 64, a_s + kM1Row * 128, w2_s, true);
           if (last) {
             tc::mma_k64(d2, st_s, id_s, idesc16<T>(), true);
             tc::mma_k64(d2 + 64, st_s + kM1Row * 128, id_s, idesc16<T>(), true);

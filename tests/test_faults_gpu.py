@@ -92,20 +92,27 @@ def test_latency_is_linear_in_the_iterations():
     slots = synth.workload_slots(synth.dataclasses.replace(w, num_prb=106, net=net), 4)
     rx = _receiver(net, slots, "bf16")
     y, dmrs, bits, _ = H.device_inputs(slots)
-    ts = []
     its = list(range(1, 9))
-    for n in its:
-        for _ in range(3):
-            rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits, iterations=n)
-        samples = []
-        for _ in range(7):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits, iterations=n)
-            b.record()
-            torch.cuda.synchronize()
-            samples.append(a.elapsed_time(b))
-        ts.append(float(np.median(samples)))
+
+    def sweep():
+        ts = []
+        for n in its:
+            for _ in range(3):
+                rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits, iterations=n)
+            samples = []
+            for _ in range(7):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits, iterations=n)
+                b.record()
+                torch.cuda.synchronize()
+                samples.append(a.elapsed_time(b))
+            ts.append(float(np.median(samples)))
+        return ts
+
+    # the lower of two sweeps' medians per depth: one sweep on a shared GPU machine was once
+    # disturbed at a single depth (R^2 0.963)
+    ts = [min(a, b) for a, b in zip(sweep(), sweep())]
     rx.nrx_check()
     A = np.stack([np.ones(len(its)), np.asarray(its, dtype=np.float64)], axis=1)
     coef, *_ = np.linalg.lstsq(A, np.asarray(ts), rcond=None)
