@@ -265,6 +265,16 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# what each mode computes in, beyond its activation type
+PRECISION_NOTE = {
+    "bf16": "BF16 activations in HBM; BF16 MMAs with split (hi + lo) weights in message passing and the "
+            "read-out; FP16 weights, taps and intermediates inside the residual blocks; FP32 accumulation",
+    "fp16": "FP16 activations, weights and depthwise taps; FP32 MMA accumulation",
+    "fp8": "E4M3 MMA operands with per-channel weight and per-row activation scales; FP16 activations in HBM",
+    "fp32": "FP32 CUDA-core arithmetic",
+}
+
+
 def traffic_for(kernel: str, precision: str):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if
     neither the kernel source nor a header of the CUDA sources has changed
@@ -544,7 +554,8 @@ def run_ours(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": precision, "data": "synthetic",
             "config": {"workload": WORKLOAD, "batch": n, "users": w.num_users, "num_rx_ant": w.num_rx_ant,
                        "num_prb": w.num_prb, "net": "C64 R2 N_it2 m_max6", "l2": "flushed before each step",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "precision": PRECISION_NOTE.get(precision, precision)},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
             "roofline": roofline,
