@@ -1,5 +1,8 @@
 // Message passing + CNN-update input layer of one CGNN iteration (Sec. II-A)
-// on the tensor cores, 16-bit operands (BF16 with split weights, or FP16).
+// on the tensor cores, 16-bit operands: S and the products with it in the
+// activation type (BF16 with split hi + lo weights, or FP16); g and the G part
+// of GEMM2 in FP16 in both modes (FP16 g and weights are more precise than
+// BF16 ones, and one MMA pass).
 // One M tile = 128 rows = nre REs x U users (row = u nre + j):
 //   GEMM1: h = ReLU(S W1^T + b1)
 //   g_u = sum over the other active users v of h_v (FP32, through shared memory)
@@ -40,7 +43,7 @@ struct MpOps;
 template <>
 struct MpOps<__nv_bfloat16> {
   static constexpr uint32_t fmt = 1;
-  static constexpr bool split = true;  // two-pass weights; h exchanged one column half at a time
+  static constexpr bool split = true;  // two-pass weights
   __device__ static __forceinline__ uint32_t pack(float a, float b) { return tc::pack_bf16x2(a, b); }
 };
 template <>
@@ -59,19 +62,18 @@ constexpr uint32_t mp_idesc() {  // kind::f16, M = 128, N = 64, FP32 accumulate,
          ((uint32_t)(128 >> 4) << 24);
 }
 
-// Shared-memory layout (offsets from the 1024-byte-aligned base).  With the
-// split BF16 weights the FP32 exchange of h holds one column half (16 KB),
-// which keeps two CTAs per SM; FP16 exchanges whole rows (32 KB).
+// Shared-memory layout (offsets from the 1024-byte-aligned base): the FP32
+// exchange of h holds whole rows (32 KB); W1 and WS are packed in the
+// activation type (hi + lo for BF16), WC in FP16.
 template <typename T>
 struct MpLay {
-  static constexpr bool kHalfX = MpOps<T>::split;
-  static constexpr int WB = MpOps<T>::split ? 2 * 8192 : 8192;  // one packed 64 x 64 weight (hi [+ lo])
+  static constexpr int WB = MpOps<T>::split ? 2 * 8192 : 8192;  // W1, WS: one packed 64 x 64 weight (hi [+ lo])
   static constexpr int BUF = 0;                                  // two operand buffers (S / G / z staging)
   static constexpr int XCH = BUF + 2 * kTile;
-  static constexpr int W1 = XCH + (kHalfX ? 16384 : 32768);
+  static constexpr int W1 = XCH + 32768;
   static constexpr int WS = W1 + WB;
-  static constexpr int WC = WS + WB;
-  static constexpr int VEC = WC + WB;    // b1, b_in + (U-1) Win_a b2, PE weights (t, f): 4 x 64 FP32
+  static constexpr int WC = WS + WB;     // FP16 image (8 KB)
+  static constexpr int VEC = WC + 8192;  // b1, b_in + (U-1) Win_a b2, PE weights (t, f): 4 x 64 FP32
   static constexpr int BAR = VEC + 1024; // 8 mbarriers; TMEM slot at +64
   static constexpr int TOTAL = BAR + 128;
   static constexpr int DYN = TOTAL + 1024;
@@ -153,8 +155,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int i = tid; i < L::WB / 16; i += kThreads) {
       d1[i] = __ldg(w.mp1 + i);
       ds[i] = __ldg(w.in_s + i);
-      dc[i] = __ldg(w.in_c + i);
     }
+    for (int i = tid; i < 8192 / 16; i += kThreads) dc[i] = __ldg(w.in_c + i);
     float* vec = reinterpret_cast<float*>(sm + L::VEC);
     if (tid < 64) {
       vec[tid] = __ldg(w.mp1_b + tid);
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         ph_g ^= 1u;
         if (!ok) break;
         tc::tc_fence_after();
-        mp_gemm<T>(tmem + 128 * p + 64, buf_s + gb * kTile, wc_s, true);
+        mp_gemm<__half>(tmem + 128 * p + 64, buf_s + gb * kTile, wc_s, true);  // G part: FP16
         tc::mma_commit(bars + kZFull);
         ok = mp_wait(bars + kZFull, ph_z);  // GEMM2 has read S and G
         ph_z ^= 1u;
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 2)
               }
             const int row = u * nre + j;
             *reinterpret_cast<uint2*>(g_buf + tc::sw128_offset(row, 4 * cq)) =
-                make_uint2(MpOps<T>::pack(s4.x, s4.y), MpOps<T>::pack(s4.z, s4.w));
+                make_uint2(MpOps<__half>::pack(s4.x, s4.y), MpOps<__half>::pack(s4.z, s4.w));
           }
         }
       };
@@ -316,67 +318,32 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         return workers_any(!ok);  // also the barrier after the exchange writes
       };
-      if constexpr (L::kHalfX) {
-        // h = ReLU(acc + b1) of row r, columns [32 hc, 32 hc + 32), in registers;
-        // per column half, its writer warps store it to the exchange (float4
-        // chunk c of a row at c ^ (r & 7)), then g_u of that half
-        float hval[32];
-        {
-          uint32_t a[16], b[16];
-          tc::tmem_ld16(dh + 32 * hc, a);
-          tc::tmem_ld16(dh + 32 * hc + 16, b);
-          tc::tmem_wait16(a);
-          tc::tmem_wait16(b);
-          const float* b1 = vec + 32 * hc;
+      // h = ReLU(acc + b1) of row r, columns [32 hc, 32 hc + 32), into the exchange
+      // (float4 chunk k of a row at k ^ (r & 7)), then g_u
+      {
+        uint32_t a[16], b[16];
+        tc::tmem_ld16(dh + 32 * hc, a);
+        tc::tmem_ld16(dh + 32 * hc + 16, b);
+        tc::tmem_wait16(a);
+        tc::tmem_wait16(b);
+        const float* b1 = vec + 32 * hc;
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            hval[e] = fmaxf(__uint_as_float(a[e]) + b1[e], 0.f);
-            hval[16 + e] = fmaxf(__uint_as_float(b[e]) + b1[16 + e], 0.f);
-          }
+        for (int c = 0; c < 8; ++c) {
+          const uint32_t* src = c < 4 ? a + 4 * c : b + 4 * (c - 4);
+          const int kk = 8 * hc + c;
+          *reinterpret_cast<float4*>(xch + r * 64 + ((kk ^ (r & 7)) << 2)) =
+              make_float4(fmaxf(__uint_as_float(src[0]) + b1[4 * c], 0.f),
+                          fmaxf(__uint_as_float(src[1]) + b1[4 * c + 1], 0.f),
+                          fmaxf(__uint_as_float(src[2]) + b1[4 * c + 2], 0.f),
+                          fmaxf(__uint_as_float(src[3]) + b1[4 * c + 3], 0.f));
         }
-        tc::tc_fence_before();
-        auto write_half = [&]() {
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            *reinterpret_cast<float4*>(xch + r * 32 + ((c ^ (r & 7)) << 2)) =
-                make_float4(hval[4 * c], hval[4 * c + 1], hval[4 * c + 2], hval[4 * c + 3]);
-        };
-        if (hc == 0) write_half();
-        if (wait_free()) {
-          if (tid == 0) atomicExch(w.err, 1);
-          break;
-        }
-        aggregate(32, 0, 8);
-        workers_sync();  // the second half overwrites the exchange
-        if (hc == 1) write_half();
-        workers_sync();
-        aggregate(32, 8, 8);
-      } else {
-        {
-          uint32_t a[16], b[16];
-          tc::tmem_ld16(dh + 32 * hc, a);
-          tc::tmem_ld16(dh + 32 * hc + 16, b);
-          tc::tmem_wait16(a);
-          tc::tmem_wait16(b);
-          const float* b1 = vec + 32 * hc;
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const uint32_t* src = c < 4 ? a + 4 * c : b + 4 * (c - 4);
-            const int kk = 8 * hc + c;
-            *reinterpret_cast<float4*>(xch + r * 64 + ((kk ^ (r & 7)) << 2)) =
-                make_float4(fmaxf(__uint_as_float(src[0]) + b1[4 * c], 0.f),
-                            fmaxf(__uint_as_float(src[1]) + b1[4 * c + 1], 0.f),
-                            fmaxf(__uint_as_float(src[2]) + b1[4 * c + 2], 0.f),
-                            fmaxf(__uint_as_float(src[3]) + b1[4 * c + 3], 0.f));
-          }
-        }
-        tc::tc_fence_before();
-        if (wait_free()) {
-          if (tid == 0) atomicExch(w.err, 1);
-          break;
-        }
-        aggregate(64, 0, 16);
       }
+      tc::tc_fence_before();
+      if (wait_free()) {
+        if (tid == 0) atomicExch(w.err, 1);
+        break;
+      }
+      aggregate(64, 0, 16);
       // rows of G not covered by (u < U, j < nre) only feed rows that are never stored
       tc::fence_async_smem();
       workers_sync();

@@ -1318,9 +1318,9 @@ nrx_status upload_tc_weights(int mode, int C, int R, int N_it, const std::vector
     pack_weight(W, ld, col0, host.data() + t * wb, m < 0 ? mode : m, sc_host + t * 64);
     ++t;
   };
-  // the residual block's PW weights: FP16 images in both 16-bit modes (its operands
-  // are FP16 there), E4M3 in FP8 mode
-  const int blk_mode = mode == 2 ? 2 : 0;
+  // the residual block's PW weights and Win_a W2 (acting on g): FP16 images in both
+  // 16-bit modes (those operands are FP16 there), E4M3 in FP8 mode
+  const int f16_mode = mode == 2 ? 2 : 0;
   const size_t per_blob = 6 + 6 * R;
   for (int k = 0; k < N_it; ++k) {
     const float* const* b = blob_it.data() + k * per_blob;  // mp1w, mp1b, mp2w, mp2b, inw, inb, blocks
@@ -1339,11 +1339,11 @@ nrx_status upload_tc_weights(int mode, int C, int R, int N_it, const std::vector
       }
       cb2_host[(size_t)k * C + n] = (float)cb;
     }
-    put(wc.data(), C, 0);  // in_c
+    put(wc.data(), C, 0, f16_mode);  // in_c
     for (int r = 0; r < R; ++r) {
       const float* const* blk = b + 6 + 6 * r;
-      put(blk[1], C, 0, blk_mode);  // pw1
-      put(blk[4], C, 0, blk_mode);  // pw2
+      put(blk[1], C, 0, f16_mode);  // pw1
+      put(blk[4], C, 0, f16_mode);  // pw2
     }
   }
   for (const float* ro1w : ro1w_heads) put(ro1w, C, 0);
