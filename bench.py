@@ -267,9 +267,9 @@ def run_reference(args, rank, world):
 
 # what each mode computes in, beyond its activation type
 PRECISION_NOTE = {
-    "bf16": "BF16 activations in HBM; BF16 MMAs with split (hi + lo) weights on the state (message passing "
-            "GEMM 1 and S part of GEMM 2, read-out); FP16 cross-user sum g and its weights; FP16 weights, taps "
-            "and intermediates inside the residual blocks; FP32 accumulation",
+    "bf16": "BF16 activations in HBM; BF16 MMAs on the state (split hi + lo weights in message passing, "
+            "BF16 weights in the read-out); FP16 cross-user sum g and its weights; FP16 weights, taps and "
+            "intermediates inside the residual blocks; FP32 accumulation",
     "fp16": "FP16 activations, weights and depthwise taps; FP32 MMA accumulation",
     "fp8": "E4M3 MMA operands with per-channel weight and per-row activation scales; FP16 activations in HBM",
     "fp32": "FP32 CUDA-core arithmetic",
