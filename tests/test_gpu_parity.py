@@ -272,6 +272,38 @@ def test_nrx_tc_parity(workload, prec, record_property):
     assert med <= TOL_TC, (med, p99)
 
 
+# Deep network: per-(slot, user) error of the 16-bit modes against the FP32 path, which the
+# other tests hold to the oracle.  Errors compound over eight CGNN iterations; measured on a
+# B300: BF16 3.0e-2, FP16 6.0e-3 (24 PRB), 2.1e-2 / 5.6e-3 (106 PRB).
+TOL_DEEP = {"bf16": 5e-2, "fp16": 2e-2}
+
+
+@pytest.mark.parametrize("num_prb", [24, 106])
+def test_deep_network_16bit_modes(num_prb):
+    """A seeded N_it = 8 network (the deepest tested: its activations reach about 1.5e4
+    inside the residual blocks, where both 16-bit modes keep FP16 intermediates, so this
+    checks that they stay in FP16's range): BF16 and FP16 LLRs are finite and near FP32's."""
+    net = synth.NetConfig(num_rx_ant=4, channels=64, res_blocks=2, iterations=8, m_max=4)
+    w = synth.WORKLOADS["mu2_4rx_24prb"]
+    slots = synth.workload_slots(synth.dataclasses.replace(w, num_prb=num_prb, net=net), 2)
+    y, dmrs, bits, _ = H.device_inputs(slots)
+    c = slots[0].cfg
+    blob = synth.pack_weights(net, synth.make_weights(net))
+    out = {}
+    for prec in ("fp32", "bf16", "fp16"):
+        rx = nrx.Receiver(blob, net.num_rx_ant, c.num_users, c.num_prb, len(slots), prec)
+        out[prec] = rx.nrx_detect_batch(y, dmrs, w.dmrs_symbols, bits).cpu().numpy()
+        rx.nrx_check()
+        rx.close()
+    per, _ = H.split(out["fp32"], slots)
+    refs = [np.concatenate(p) for p in per]
+    for prec in ("bf16", "fp16"):
+        assert np.isfinite(out[prec]).all(), prec
+        errs = H.rel_errors(out[prec], refs, slots)
+        print(prec, num_prb, "worst vs FP32", max(errs))
+        assert max(errs) <= TOL_DEEP[prec], (prec, errs)
+
+
 def test_trained_network_parity():
     """The trained 4-user network (m_max = 6) on two 273-PRB slots against the
     FP64 oracle: FP32 within 1e-4 and FP16 within 2e-2 per (slot, user).  BF16
