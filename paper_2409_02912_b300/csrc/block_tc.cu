@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!rot) tc::bulk_wait_read_all();  // OUT (in A) read by the previous store
         }
       }
-      in_ph ^= 1u << b;
+      if (ok) in_ph ^= 1u << b;  // after a failed wait the bit keeps the pending phase (teardown drain)
       if (group_any(bar_id, !ok)) {
         if (leader) atomicExch(err, 1);
         dead = true;
@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = wait_bar(mma_bar, mma_ph);
         if (ok) mma_pending = false;
       }
-      mma_ph ^= 1u;
+      if (!mma_pending) mma_ph ^= 1u;
       if (group_any(bar_id, !ok)) {
         if (leader) atomicExch(err, 1);
         dead = true;
@@ -568,8 +568,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (ok) mma_pending = false;
         }
       }
-      if (last) st_ph ^= 1u;
-      mma_ph ^= 1u;
+      if (last && !st_pending) st_ph ^= 1u;
+      if (!mma_pending) mma_ph ^= 1u;
       if (group_any(bar_id, !ok)) {
         if (leader) atomicExch(err, 1);
         dead = true;
@@ -598,7 +598,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     b = bn;
   }
-  // ---- teardown: let asynchronous work in flight land, then free TMEM ----
+  // ---- teardown: let asynchronous work in flight land, then free TMEM (a phase
+  // variable advances only past a successful wait, so it names the pending phase) ----
   if (leader) {
     for (int j = 0; j < 3; ++j)
       if ((in_pending >> j) & 1u) wait_bar(in_bar + j, (in_ph >> j) & 1u, kDrainNs);

@@ -201,8 +201,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       // GEMM1 and the S part of GEMM2 of the tile whose S rows land in buffer `buf`
       auto front = [&](int parity, int buf) {
         ok = mp_wait(bars + kSFull, ph_s);
+        if (!ok) return;  // ph_s keeps the pending phase for the teardown drain
         ph_s ^= 1u;
-        if (!ok) return;
         s_pending = false;
         tc::tc_fence_after();
         const uint32_t d = tmem + 128 * parity, a = buf_s + buf * kTile;
