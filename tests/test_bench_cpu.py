@@ -50,3 +50,14 @@ def test_roofline_numerators_of_the_workload():
     assert act == 187_858_944
     assert b["residual_block"] == (2 * (2 - 1) + 3) * act / 2  # non-last: z in, z out; last: + state
     assert b["message_passing"] == 2 * act
+
+
+def test_traffic_record_matches_the_kernel_source():
+    """The committed DRAM traffic of the dominant kernel is keyed to the hash of its
+    source and the CUDA headers; the bench reports null once they change, so a
+    kernel edit without a new capture (or a stated re-keying) fails here first."""
+    for prec in ("bf16", "fp16"):
+        t = bench.traffic_for("residual_block", prec)
+        assert t is not None, prec
+        # between 50% and 150% of the algorithmic bytes of one launch (2.5 tensors of 188 MB)
+        assert 0.5 * 2.5 * 187_858_944 < t < 1.5 * 2.5 * 187_858_944
