@@ -277,9 +277,10 @@ PRECISION_NOTE = {
 
 
 def traffic_for(kernel: str, precision: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if
-    neither the kernel source nor a header of the CUDA sources has changed
-    since the capture."""
+    """Per-launch DRAM bytes of `kernel` at the 8-slot batch from the committed
+    ncu summary, if neither the kernel source nor a header of the CUDA sources
+    has changed since the capture (the caller scales it to its batch: the
+    traffic grows with the number of tiles)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))[f"{kernel}/{precision}"]
@@ -547,7 +548,7 @@ def run_ours(args, rank, world, local):
             peak_desc = "measured sustained dense BF16 tensor rate (FP16 has the same rate)"
     roofline = {"bound": bound, "kernel": kern, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "peak_source": f"{src}: {peak_desc}",
-                "traffic": traffic_for(kern, precision),
+                "traffic": (lambda t: None if t is None else t * n / 8)(traffic_for(kern, precision)),
                 "flop_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
                 "intensity_flop_per_byte": flops / nbytes, "launch_ms": per_launch_ms,
                 "kernel_share": {k: prof[k][0] / max(sum(v[0] for v in prof.values()), 1e-12) for k in prof
